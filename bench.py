@@ -1,0 +1,280 @@
+#!/usr/bin/env python3
+"""Benchmark: image-series registration (preprocessing + prefix scan of the
+registration operator) on a synthetic 400 x 1024^2 series, 5-level pyramid.
+
+One step = one full series registration on a handle whose frames and pyramid
+are resident in HBM: all A(f_e, f_{e+1}) applications in one batch, then every
+level of the scan schedule as one batch.  value = operator applications per
+second (A + B) over the whole job; ms_per_step = series time.
+
+Prints one JSON line on rank 0.  Multi-GPU (torchrun): every rank registers
+its own series (independent problems, weak scaling, no collective on the data
+path); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="c3_400x1024", seed=3, n_frames=400, side=1024, spacing=16.0, sigma=2.0, peak=5.0,
+                drift_sd=1.0, dist_amp=2.0, n_levels=5, iter_max=50, lam=10.0)
+METRIC = "operator applications/s and series scan time at 400x1024^2; % of HBM roofline"
+UNIT = "op-apps/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kind", default="sklansky",
+                    choices=["serial", "sklansky", "kogge_stone", "brent_kung", "blelloch", "chunked", "chunked_alt"])
+    ap.add_argument("--chunks", type=int, default=16)
+    ap.add_argument("--frames", type=int, default=WORKLOAD["n_frames"])
+    ap.add_argument("--side", type=int, default=WORKLOAD["side"])
+    ap.add_argument("--levels", type=int, default=WORKLOAD["n_levels"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(frames, cfg, n_ops=None, budget_s=30.0):
+    """The FP64 oracle as it stands, on a bounded sample: A(f_e, f_{e+1}) ops of
+    the same series and parameters, run in parallel over the host cores."""
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    n = n_ops or min(cores, 16)
+    p = oracle.params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"])
+    g = [oracle.embed(frames[e]) for e in range(n + 1)]
+    t = time.time()
+    oracle.apply_batch([dict(R=g[e], T=g[e + 1]) for e in range(n)], p)
+    dt = time.time() - t
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} A operator applications (frame pairs 0..{n}) of the {cfg['name']} series, "
+                      f"{cfg['side']}^2, {cfg['n_levels']} levels, iter_max {cfg['iter_max']}, "
+                      f"run in parallel over {cores} host threads; {dt:.1f} s"}
+
+
+def main():
+    a = _args()
+    import numpy as np
+
+    cfg = dict(WORKLOAD)
+    cfg["n_frames"], cfg["side"], cfg["n_levels"] = a.frames, a.side, a.levels
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if a.impl == "reference":
+        if rank != 0:
+            return 0
+        import synth
+        frames = synth.series(cfg["seed"], 17, cfg["side"], spacing=cfg["spacing"], sigma=cfg["sigma"],
+                              peak=cfg["peak"], drift_sd=cfg["drift_sd"], dist_amp=cfg["dist_amp"])
+        vals = []
+        for _ in range(max(1, a.steps)):
+            cb = cpu_baseline(frames, cfg)
+            vals.append(cb["value"])
+        v = float(np.median(vals))
+        cb["value"] = v
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+               "steps": a.steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": cfg["name"], "frames": cfg["n_frames"], "side": cfg["side"],
+                          "levels": cfg["n_levels"], "note": "FP64 CPU oracle on a bounded sample of the workload"},
+               "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return 0
+
+    import torch
+    import synth
+    import paper_1712_02533_gb300 as reg
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    kind = {v: k for k, v in reg.SCAN_NAMES.items()}[a.kind]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # each rank registers its own series (independent problems)
+    t0 = time.time()
+    frames = synth.series(cfg["seed"] + 1000 * rank, cfg["n_frames"], cfg["side"], spacing=cfg["spacing"],
+                          sigma=cfg["sigma"], peak=cfg["peak"], drift_sd=cfg["drift_sd"], dist_amp=cfg["dist_amp"])
+    gen_s = time.time() - t0
+    params = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"],
+                                flags=reg.FLAG_PROFILE)
+    fd = torch.from_numpy(frames).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    s = reg.Series([fd], params)
+    torch.cuda.synchronize()
+    create_s = time.time() - t0
+
+    for _ in range(a.warmup):
+        s.prefix_scan(kind, a.chunks, reg.KOGGE_STONE)
+    s.reset_kernel_stats()
+    sampler = ClockSampler(dev)
+    barrier()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    reports = []
+    for _ in range(a.steps):
+        reports.append(s.prefix_scan(kind, a.chunks, reg.KOGGE_STONE))
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    stats = s.kernel_stats()
+    ops_per_step = reports[-1]["ops"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / a.steps
+    value = world * ops_per_step / (ms_step / 1e3)
+
+    # dominant kernel and its roofline
+    peak, peak_kind = _peaks()
+    fams = {k: v for k, v in stats.items() if k in ("grad", "trial", "prolong")}
+    dom = max(fams, key=lambda k: fams[k]["ms"])
+    dk = fams[dom]
+    launches = max(1, dk["launches"])
+    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": None, "bytes_per_launch": dk["bytes"] / launches,
+                "ms_per_launch": dk["ms"] / launches,
+                "kernels": {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
+                                "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+                            for k, v in stats.items()}}
+    gpu_launches = int(sum(v["launches"] for v in stats.values()))
+
+    # end to end through the C-ABI with host buffers (upload, pyramid, scan, download)
+    e2e = None
+    if not a.no_e2e:
+        host = torch.from_numpy(frames).pin_memory()
+        out = torch.empty((cfg["n_frames"], 2, cfg["side"], cfg["side"]), dtype=torch.float32).pin_memory()
+        p2 = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"])
+        e2e_steps = max(1, min(a.steps, 2))
+        barrier()
+        t = time.time()
+        for _ in range(e2e_steps):
+            with reg.Series([host], p2) as s2:
+                r2 = s2.prefix_scan(kind, a.chunks, reg.KOGGE_STONE)
+                s2.get_deformations(out=out)
+        barrier()
+        e2e_s = (time.time() - t) / e2e_steps
+        e2e = {"value": world * r2["ops"] / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(out.numel() * 4),
+               "ms_per_step": round(e2e_s * 1e3, 2)}
+    s.close()
+
+    if rank == 0:
+        cb = None
+        if not a.no_cpu and world == 1:
+            cb = cpu_baseline(frames, cfg)
+        rep = reports[-1]
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms_step, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 global sums)", "data": "synthetic",
+            "config": {"workload": cfg["name"], "frames": cfg["n_frames"], "side": cfg["side"],
+                       "levels": cfg["n_levels"], "iter_max": cfg["iter_max"], "lambda": cfg["lam"],
+                       "schedule": a.kind, "chunks": a.chunks if "chunked" in a.kind else None,
+                       "ops_per_step": ops_per_step, "preprocessing_ops": rep["preprocessing_ops"],
+                       "scan_ops": rep["scan_ops"], "scan_batches": rep["scan_batches"],
+                       "iters_per_step": rep["iters"], "l2": "working set (GBs) larger than L2; no flush",
+                       "generator_s": round(gen_s, 1), "create_ms": round(create_s * 1e3, 1)},
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

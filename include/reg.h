@@ -1,0 +1,244 @@
+/*
+ * libreg -- GB300 (sm_103a) registration prefix scan for long electron
+ * micrograph series.
+ *
+ * The method is the one of "Parallel Prefix Algorithms for the Registration of
+ * Arbitrarily Long Electron Micrograph Series" (arXiv 1712.02533):
+ *   - function A (Algorithm "Multilevel gradient flow for image registration"):
+ *     register frame f_k to frame f_i by a multilevel L2 gradient flow on
+ *     E[phi] = -NCC[f_i, f_k o phi] + lambda/2 int |D(phi - id)|^2
+ *     (Section "Image registration for electron microscopy"), forward Euler
+ *     steps with the Armijo rule with widening (Section "Gradient flow");
+ *   - function B(phi_ij, phi_jk) = A(f_i, f_k, phi_jk o phi_ij) (Section
+ *     "Registration for series of images");
+ *   - image series registration (Definition "Image series registration"):
+ *     preprocessing x_e = A(f_e, f_{e+1}, I), then the inclusive prefix scan
+ *     phi_{0,e+1} = x_0 (.)_B ... (.)_B x_e (Section "Prefix sum for
+ *     registration problem") with one of the paper's scan schedules.
+ * All independent operator applications of one scan level run in one batched
+ * device loop; every arithmetic step runs in this library's CUDA kernels.
+ *
+ * Units and layout.  A frame is side x side pixels, side = 2^L (32 <= side <=
+ * 4096), row-major, row = x_1, column = x_0.  Level l of the pyramid is the
+ * vertex grid of (2^l + 1)^2 nodes on Omega = [0,1]^2; the frame is embedded
+ * on level L by repeating its last row and column.  Deformations are returned
+ * as displacements u(x) = phi(x) - x in pixels, channel 0 along columns (x_0),
+ * channel 1 along rows (x_1), with f_k(x + u(x)) ~ f_0(x).
+ *
+ * Errors.  Every call returns a reg_status; no C++ exception crosses the ABI.
+ * A handle is not thread-safe: calls on one handle must be serialised by the
+ * caller.  Work is enqueued on the stream given at creation; every call is
+ * synchronous on return unless stated otherwise.
+ */
+#ifndef REG_H
+#define REG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reg_series *reg_series_t;
+
+typedef enum reg_status {
+    REG_OK = 0,
+    REG_EINVAL = 1,   /* bad argument: size, index, chain mismatch, null pointer */
+    REG_ENOMEM = 2,   /* device or host allocation failed */
+    REG_ECUDA = 3,    /* a CUDA runtime call failed (message in reg_last_error) */
+    REG_ESTATE = 4,   /* call not valid in the handle's current state */
+    REG_ETIMEOUT = 5, /* a bounded device loop gave up (step budget exhausted) */
+    REG_EKERNEL = 6   /* a kernel reported an internal error */
+} reg_status;
+
+/* Per-operator outcome (not a call error). */
+typedef enum reg_op_status {
+    REG_OP_CONVERGED = 0,     /* energy decrease below epsilon * max(1, |E|) */
+    REG_OP_MAXITER = 1,       /* iter_max gradient steps on the finest level */
+    REG_OP_LS_STALLED = 2,    /* Armijo search found no step >= tau_min */
+    REG_OP_NONFINITE = 3,     /* an energy or slope was not finite on some level */
+    REG_OP_ZERO_GRADIENT = 4  /* the slope g^T d was exactly zero */
+} reg_op_status;
+
+typedef enum reg_storage { REG_STORAGE_F32 = 0, REG_STORAGE_BF16 = 1 } reg_storage;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  When
+ * alloc is NULL the library uses cudaMallocAsync/cudaFreeAsync on its stream. */
+typedef struct reg_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} reg_allocator;
+
+/* Method parameters.  n_levels: pyramid depth m1 - m0 + 1 with m1 = L
+ * (Algorithm "Multilevel gradient flow"); iter_max and epsilon: stopping
+ * criteria per level; lambda: regulariser weight; armijo_sigma, tau_*: step
+ * rule (Section "Gradient flow").  trials_per_pass (1..8): how many step
+ * sizes of the Armijo sequence one energy pass evaluates at once (does not
+ * change the accepted step).  storage: pyramid storage precision. */
+typedef struct reg_params {
+    int32_t n_levels;
+    int32_t iter_max;
+    double epsilon;
+    double lambda;
+    double armijo_sigma;
+    double tau_init;
+    double tau_max;
+    double tau_min;
+    int32_t storage;
+    int32_t trials_per_pass;
+    int32_t max_steps;        /* device step budget per batch; <= 0: automatic */
+    int32_t flags;            /* REG_FLAG_* */
+    reg_allocator allocator;
+} reg_params;
+
+#define REG_FLAG_PROFILE 1    /* time kernel families with CUDA events */
+
+/* Fills *p with the defaults: n_levels 3, iter_max 50, epsilon 1e-7,
+ * lambda 10, sigma 0.5, tau_init 1, tau_max 1e4, tau_min 1e-12, F32 storage,
+ * 4 trials per pass. */
+void reg_default_params(reg_params *p);
+
+/* One operator application (Section "Registration for series of images").
+ * Registers frame_k (template) to frame_i (reference) of series `series`:
+ *   left >= 0, right >= 0 : B = A(f_i, f_k, right o left)  (slots' fields)
+ *   left >= 0, right <  0 : A(f_i, f_k, left)
+ *   left <  0, right <  0 : A(f_i, f_k, I)
+ * The result is written to slot dst of the same series.  All ops of one call
+ * read their slots before any op writes (level-synchronous semantics). */
+typedef struct reg_op_desc {
+    int32_t series;
+    int32_t left_slot;
+    int32_t right_slot;
+    int32_t dst_slot;
+    int32_t frame_i;
+    int32_t frame_k;
+} reg_op_desc;
+
+typedef enum reg_scan_kind {
+    REG_SCAN_SERIAL = 0,      /* Algorithm "serial prefix sum" */
+    REG_SCAN_SKLANSKY = 1,    /* Algorithm "Sklansky" (Ladner-Fischer) */
+    REG_SCAN_KOGGE_STONE = 2, /* Algorithm "Kogge-Stone" (double-buffered) */
+    REG_SCAN_BRENT_KUNG = 3,  /* Algorithm "Brent-Kung" */
+    REG_SCAN_BLELLOCH = 4,    /* Algorithm "Blelloch" (exclusive, shifted) */
+    REG_SCAN_CHUNKED = 5,     /* general strategy, Algorithm "Distributed parallel prefix sum" */
+    REG_SCAN_CHUNKED_ALT = 6  /* alternative strategy (reduce-then-scan) */
+} reg_scan_kind;
+
+/* Create a handle holding `n_series` series (one segmented scan).
+ * frames: the frames of all series back to back, series s holding
+ *   frames_per_series[s] frames of side_px[s]^2 pixels with row pitch
+ *   pitch_elems (>= max side; elements), float32.  Host memory unless
+ *   frames_on_device != 0 (then a device pointer; it is only read).
+ * The library copies the frames, builds each frame's pyramid (restriction
+ * with the 1/16 [1 2 1; 2 4 2; 1 2 1] stencil, Section "Multilevel") and
+ * keeps it until reg_destroy_series.  cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream).  Errors: REG_EINVAL for a side that is not a power
+ * of two in [32, 4096], fewer than 2 frames, or n_levels outside [1, L-3]. */
+reg_status reg_create_series(const float *frames, int32_t n_series, const int32_t *frames_per_series,
+                             const int32_t *side_px, int64_t pitch_elems, int32_t frames_on_device,
+                             const reg_params *p, void *cuda_stream, reg_series_t *out);
+
+/* Run a batch of independent operator applications in one device loop.
+ * op_status_out, iters_out (nullable, n_ops entries, host memory): per-op
+ * reg_op_status and total gradient steps over all levels.
+ * Errors: REG_EINVAL for an out-of-range series/slot/frame, an identity slot
+ * used as an operand, or a chain mismatch (left ends where right starts is
+ * required: the slot holding phi_{a,b} and the one holding phi_{b,c}). */
+reg_status reg_apply_operator_batch(reg_series_t s, int32_t n_ops, const reg_op_desc *ops,
+                                    int32_t *op_status_out, int32_t *iters_out);
+
+/* Image series registration: preprocessing (all A ops of all series in one
+ * batch) followed by the prefix scan with the chosen schedule; each scan level
+ * is one reg_apply_operator_batch over all series (segmented scan).  chunks
+ * and global_kind are used by the chunked strategies only.  report_json_buf
+ * (nullable): receives a NUL-terminated JSON summary (levels, op counts,
+ * iterations, per-kernel timings when REG_FLAG_PROFILE is set). */
+reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, reg_scan_kind global_kind,
+                           char *report_json_buf, size_t buf_len);
+
+/* Copy deformations phi_{0,k} - id, k = first .. first+count-1, of series
+ * `series` into out (count x 2 x side x side float32, pixels; host memory
+ * unless out_on_device).  phi_{0,0} is the identity (zeros).  Valid after
+ * reg_prefix_scan. */
+reg_status reg_get_deformations(reg_series_t s, int32_t series, int32_t first, int32_t count, float *out,
+                                int32_t out_on_device);
+
+/* Copy the finest-level field held in a slot and its (start, end) frame pair;
+ * end < 0 marks the identity (zeros are written).  out: 2 x (side+1) x (side+1)
+ * float32, pixels, the full vertex grid of level L (host unless
+ * out_on_device).  Used by tests and by callers that drive
+ * reg_apply_operator_batch themselves. */
+reg_status reg_get_slot(reg_series_t s, int32_t series, int32_t slot, float *out, int32_t out_on_device,
+                        int32_t *start_end);
+
+/* Set a slot to phi_{start,end} given as a displacement field on the vertex
+ * grid (2 x (side+1) x (side+1) float32, pixels, host or device) -- e.g. to
+ * seed a scan with known neighbour deformations.  end < 0 marks the slot as
+ * the identity (field ignored). */
+reg_status reg_set_slot(reg_series_t s, int32_t series, int32_t slot, const float *field, int32_t on_device,
+                        int32_t start, int32_t end);
+
+/* Number of slots of a series (N-1 data slots for N frames plus the
+ * auxiliary slots the largest schedule needs). */
+reg_status reg_num_slots(reg_series_t s, int32_t series, int32_t *n_slots);
+
+/* Diagnostic evaluation of the discrete energy of one frame pair at one level
+ * for a given displacement (2 x n x n, grid units of that level, host memory):
+ * fills parts[0..4] = {E, NCC, regulariser, T_bar, sigma_T}.  Used to check
+ * the kernels against an independent implementation. */
+reg_status reg_eval_energy(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                           const float *u_grid, double *parts);
+
+/* Diagnostic evaluation of the gradient-flow direction d = -g / w (grid units)
+ * and slope g^T d at a displacement (same conventions as reg_eval_energy). */
+reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                              const float *u_grid, float *d_out, double *slope);
+
+/* Schedule export (host only, no GPU work): writes the op list of a schedule
+ * over n elements as reg_schedule_op records (level index, kind, slots) into
+ * buf (up to buf_len records), the total count into *n_out (call with buf NULL
+ * to size) and the auxiliary slot count into *n_aux_slots.  Ops of one level
+ * read the slots as they were before the level. */
+typedef struct reg_schedule_op {
+    int32_t level;
+    int32_t kind;   /* 0 combine dst = a (.) b, 1 copy dst = a, 2 identity dst */
+    int32_t dst;
+    int32_t a;
+    int32_t b;
+} reg_schedule_op;
+reg_status reg_schedule(reg_scan_kind kind, int32_t n, int32_t chunks, reg_scan_kind global_kind,
+                        reg_schedule_op *buf, int64_t buf_len, int64_t *n_out, int32_t *n_aux_slots);
+
+/* Per-kernel-family statistics accumulated since creation (or the last reset):
+ * launches, device time (ms, CUDA events, only with REG_FLAG_PROFILE) and
+ * algorithmic bytes (counted on the device per processed node). */
+typedef struct reg_kernel_stats {
+    char name[24];
+    int64_t launches;
+    double ms;
+    double bytes;
+    int64_t items;
+} reg_kernel_stats;
+reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t buf_len, int32_t *n_out);
+reg_status reg_reset_kernel_stats(reg_series_t s);
+
+/* Diagnostic trace of every Armijo trial the device state machine decides:
+ * reg_set_trace allocates room for `capacity` records (0 disables);
+ * reg_get_trace copies up to cap records of 7 doubles
+ * {op index in its batch, nodes per side of the level, iteration, tau,
+ *  E(u + tau d) - E(u), sigma tau g^T d, accepted} and returns the number
+ * recorded.  Records of one op appear in decision order. */
+reg_status reg_set_trace(reg_series_t s, int64_t capacity);
+reg_status reg_get_trace(reg_series_t s, double *out, int64_t cap, int64_t *n_out);
+
+reg_status reg_destroy_series(reg_series_t s);
+const char *reg_status_string(reg_status st);
+/* Message of the last error on this thread (empty if none). */
+const char *reg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REG_H */

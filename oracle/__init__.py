@@ -89,6 +89,8 @@ def _load():
         "orc_register": ([vp, vp, i, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(LevelStats)], i),
         "orc_compose": ([vp, vp, i, vp], None),
         "orc_apply_batch": ([i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp], None),
+        "orc_set_trace": ([vp, ctypes.c_long], None),
+        "orc_trace_len": ([], ctypes.c_long),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -203,6 +205,24 @@ def register(R, T, p: Params, u_init=None):
     s = _load().orc_register(R.ctypes.data, T.ctypes.data, L, _ptr(ui), ctypes.byref(p),
                              out.ctypes.data, st)
     return out, s, [st[i] for i in range(p.n_levels)]
+
+
+class trace:
+    """Context manager recording every Armijo trial of the (single-threaded)
+    level solves run inside it: rows (n, iteration, tau, dE, sigma tau slope,
+    accepted)."""
+
+    def __init__(self, cap=1 << 20):
+        self.buf = np.zeros((cap, 6))
+
+    def __enter__(self):
+        _load().orc_set_trace(self.buf.ctypes.data, self.buf.shape[0])
+        return self
+
+    def __exit__(self, *a):
+        lib = _load()
+        self.rows = self.buf[:lib.orc_trace_len()].copy()
+        lib.orc_set_trace(None, 0)
 
 
 def compose(u_ij, u_jk):

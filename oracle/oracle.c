@@ -34,6 +34,33 @@
 
 static double *dalloc(size_t n) { return (double *)calloc(n, sizeof(double)); }
 
+/* Optional trace of every Armijo trial of orc_solve_level (for comparing
+ * decision sequences in tests): records of 6 doubles
+ * {n, iteration, tau, E(u + tau d) - E(u), sigma tau g^T d, accepted}. */
+static double *g_trace = NULL;
+static long g_trace_cap = 0, g_trace_len = 0;
+
+void orc_set_trace(double *buf, long cap)
+{
+    g_trace = buf;
+    g_trace_cap = cap;
+    g_trace_len = 0;
+}
+
+long orc_trace_len(void) { return g_trace_len; }
+
+static void trace(int n, int it, double tau, double dE, double rhs, int acc)
+{
+    if (!g_trace || g_trace_len >= g_trace_cap) return;
+    double *r = g_trace + 6 * g_trace_len++;
+    r[0] = n;
+    r[1] = it;
+    r[2] = tau;
+    r[3] = dE;
+    r[4] = rhs;
+    r[5] = acc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Grids, embedding, restriction and prolongation (Section "Multilevel")     */
 /* ------------------------------------------------------------------------- */
@@ -357,12 +384,16 @@ int orc_solve_level(const double *R, const double *T, int n, double *u, const or
         double E1;
         int stalled = 0;
         TRIAL(tau, E1);
-        if (E1 - E0 <= p->armijo_sigma * tau * slope) {
+        int ok = E1 - E0 <= p->armijo_sigma * tau * slope;
+        trace(n, it, tau, E1 - E0, p->armijo_sigma * tau * slope, ok);
+        if (ok) {
             for (;;) {
                 double t2 = 2.0 * tau, Et;
                 if (t2 > p->tau_max) break;
                 TRIAL(t2, Et);
-                if (Et - E0 <= p->armijo_sigma * t2 * slope) {
+                int ok2 = Et - E0 <= p->armijo_sigma * t2 * slope;
+                trace(n, it, t2, Et - E0, p->armijo_sigma * t2 * slope, ok2);
+                if (ok2) {
                     tau = t2;
                     E1 = Et;
                 } else {
@@ -377,7 +408,9 @@ int orc_solve_level(const double *R, const double *T, int n, double *u, const or
                     break;
                 }
                 TRIAL(tau, E1);
-                if (E1 - E0 <= p->armijo_sigma * tau * slope) break;
+                int ok3 = E1 - E0 <= p->armijo_sigma * tau * slope;
+                trace(n, it, tau, E1 - E0, p->armijo_sigma * tau * slope, ok3);
+                if (ok3) break;
             }
         }
 #undef TRIAL

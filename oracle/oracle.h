@@ -26,6 +26,8 @@ typedef struct orc_level_stats {
     double tau;
 } orc_level_stats;
 
+void orc_set_trace(double *buf, long cap);
+long orc_trace_len(void);
 void orc_embed(const float *frame, int side, double *out);
 void orc_restrict(const double *fine, int nf, double *coarse);
 void orc_prolong(const double *coarse, int nc, double *fine);

@@ -1,0 +1,1147 @@
+// Host side of libreg: series handles, pyramid construction, the batched
+// operator loop (a device-resident Armijo state machine stepped by a captured
+// CUDA graph), the scan driver and the C-ABI entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/reg.h"
+#include "reg_common.cuh"
+#include "schedule.h"
+
+// kernels (kernels.cu)
+__global__ void k_embed(const float *, int64_t, int64_t, int, float *, int64_t, int);
+__global__ void k_restrict_img(const float *, int64_t, int, int, float *, int64_t, int);
+__global__ void k_image_stats(const float *, int64_t, int, int, double *);
+__global__ void k_normalize(const float *, int64_t, int, int, const double *, void *, int64_t, int, int);
+__global__ void k_compose(BatchDev);
+__global__ void k_restrict_u(BatchDev, int);
+__global__ void k_zero_u(BatchDev);
+__global__ void k_init_state(BatchDev, int);
+__global__ void k_plan(BatchDev);
+__global__ void k_prolong(BatchDev);
+void launch_grad(int bf16, int grid, cudaStream_t st, const BatchDev &b);
+void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b);
+int trial_blocks_per_sm(int J);
+__global__ void k_control(BatchDev);
+__global__ void k_slot_to_planes(const float2 *, int, int, float *);
+__global__ void k_planes_to_slot(const float *, int, float2 *, int);
+
+#define PT_STRIDE (3 * REG_MAX_TRIALS + 3)
+
+namespace {
+
+thread_local std::string g_err;
+
+reg_status fail(reg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(x)                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) return fail(REG_ECUDA, "%s: %s", #x, cudaGetErrorString(e_));    \
+    } while (0)
+
+#define RET(x)                                  \
+    do {                                        \
+        reg_status r_ = (x);                    \
+        if (r_ != REG_OK) return r_;            \
+    } while (0)
+
+int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+struct SlotMeta {
+    int start = -1, end = -1;  // end < 0: identity / empty
+};
+
+struct SeriesInfo {
+    int n_frames = 0, side = 0, L = 0, m0 = 0, nl = 0, frame_base = 0;
+    int n_data = 0, n_slots = 0;
+    std::vector<int> n, pitch;            // per level index k (0 = coarsest)
+    std::vector<size_t> img_off;          // element offset of level k inside a frame's pyramid block
+    size_t frame_block = 0;               // elements per frame pyramid
+    void *pyr = nullptr;                  // n_frames * frame_block elements (float or bf16)
+    float2 *slots = nullptr;              // n_slots * slot_elems
+    size_t slot_elems = 0;
+    std::vector<SlotMeta> meta;
+    std::vector<size_t> ws_off;           // per level: offset (bytes) of U0 within an op workspace
+    size_t ws_bytes = 0;                  // per op
+    size_t field_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(float2); }
+    size_t ufield_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(float4); }
+};
+
+struct FamilyStats {
+    const char *name;
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes_per_unit = 0.0;
+};
+
+struct OpReq {
+    int series, frame_i, frame_k, init;
+    int left, right, dst;  // slot indices (-1 none)
+};
+
+constexpr int GRAPH_STEPS = 8;
+constexpr int NFAM = 6;  // P, G, T, C, plan, setup
+enum { F_P = 0, F_G, F_T, F_C, F_PLAN, F_SETUP };
+
+}  // namespace
+
+struct reg_series {
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    reg_params p{};
+    int bf16 = 0;
+    int nsm = 0;
+    int grid_work = 0;
+    std::vector<SeriesInfo> S;
+    std::vector<void *> allocs;
+    // batch buffers
+    int cap_ops = 0;
+    int64_t cap_items = 0;
+    size_t cap_ws = 0;
+    OpDesc *d_ops = nullptr;
+    OpState *d_st = nullptr;
+    int *d_lists = nullptr;  // listP, listG, listT, prefP, prefG, prefT
+    int *d_ctr = nullptr;
+    double *d_partG = nullptr, *d_partT = nullptr;
+    unsigned long long *d_work = nullptr;
+    char *d_ws = nullptr;
+    double *d_scratch = nullptr;
+    OpDesc *h_ops = nullptr;
+    int *h_ctr = nullptr;
+    OpState *h_st = nullptr;
+    int h_st_cap = 0;
+    // graph of GRAPH_STEPS steps
+    cudaGraphExec_t gexec = nullptr;
+    int graph_gen = -1, buf_gen = 0;
+    // profiling
+    cudaEvent_t ev[GRAPH_STEPS][NFAM];
+    cudaEvent_t ev_end[GRAPH_STEPS];
+    bool ev_ok = false;
+    FamilyStats fam[NFAM] = {{"prolong"}, {"grad"}, {"trial"}, {"control"}, {"plan"}, {"setup"}};
+    unsigned long long work_prev[16] = {0};
+    double *d_trace = nullptr;
+    unsigned long long *d_trace_len = nullptr;
+    long long trace_cap = 0;
+    // totals for reports
+    int64_t tot_steps = 0, tot_ops = 0, tot_iters = 0, tot_trials = 0, tot_evals = 0;
+};
+
+namespace {
+
+reg_status dalloc(reg_series *s, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) return REG_OK;
+    if (s->p.allocator.alloc) {
+        *ptr = s->p.allocator.alloc(bytes, (void *)s->stream, s->p.allocator.ctx);
+        if (!*ptr) return fail(REG_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(ptr, bytes, s->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(REG_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    return REG_OK;
+}
+
+void dfree(reg_series *s, void *ptr, size_t bytes)
+{
+    if (!ptr) return;
+    if (s->p.allocator.alloc) {
+        if (s->p.allocator.free) s->p.allocator.free(ptr, bytes, (void *)s->stream, s->p.allocator.ctx);
+    } else {
+        cudaFreeAsync(ptr, s->stream);
+    }
+}
+
+}  // namespace
+
+namespace {
+
+reg_status track(reg_series *s, void **ptr, size_t bytes)
+{
+    RET(dalloc(s, ptr, bytes));
+    s->allocs.push_back(*ptr);
+    s->allocs.push_back(reinterpret_cast<void *>(bytes));
+    return REG_OK;
+}
+
+void untrack(reg_series *s, void *ptr)
+{
+    for (size_t i = 0; i + 1 < s->allocs.size(); i += 2)
+        if (s->allocs[i] == ptr) {
+            dfree(s, ptr, reinterpret_cast<size_t>(s->allocs[i + 1]));
+            s->allocs.erase(s->allocs.begin() + i, s->allocs.begin() + i + 2);
+            return;
+        }
+}
+
+BatchDev make_batch(reg_series *s)
+{
+    BatchDev b;
+    memset(&b, 0, sizeof(b));
+    b.ops = s->d_ops;
+    b.st = s->d_st;
+    int c = s->cap_ops;
+    b.listP = s->d_lists;
+    b.listG = s->d_lists + c;
+    b.listT = s->d_lists + 2 * c;
+    b.prefP = s->d_lists + 3 * c;
+    b.prefG = s->d_lists + 4 * c + 1;
+    b.prefT = s->d_lists + 5 * c + 2;
+    b.ctr = s->d_ctr;
+    b.partG = s->d_partG;
+    b.partT = s->d_partT;
+    b.work = s->d_work;
+    b.trace = s->d_trace;
+    b.trace_len = s->d_trace_len;
+    b.trace_cap = s->trace_cap;
+    b.lambda = s->p.lambda;
+    b.sigma = s->p.armijo_sigma;
+    b.tau_init = s->p.tau_init;
+    b.tau_max = s->p.tau_max;
+    b.tau_min = s->p.tau_min;
+    b.eps = s->p.epsilon;
+    b.iter_max = s->p.iter_max;
+    b.J = s->p.trials_per_pass;
+    b.bf16 = s->bf16;
+    return b;
+}
+
+int node_tiles(int n) { return cdiv(n, REG_TX) * cdiv(n, REG_TY); }
+
+reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t items_per_op)
+{
+    bool changed = false;
+    if (n_ops > s->cap_ops) {
+        int c = std::max(n_ops, 2 * s->cap_ops);
+        untrack(s, s->d_ops);
+        untrack(s, s->d_st);
+        untrack(s, s->d_lists);
+        if (s->h_ops) cudaFreeHost(s->h_ops);
+        RET(track(s, (void **)&s->d_ops, sizeof(OpDesc) * c));
+        RET(track(s, (void **)&s->d_st, sizeof(OpState) * c));
+        RET(track(s, (void **)&s->d_lists, sizeof(int) * (6 * c + 3)));
+        CK(cudaMallocHost((void **)&s->h_ops, sizeof(OpDesc) * c));
+        s->cap_ops = c;
+        changed = true;
+    }
+    int64_t items = (int64_t)n_ops * items_per_op;
+    if (items > s->cap_items) {
+        int64_t c = std::max(items, (int64_t)(1.25 * s->cap_items));
+        untrack(s, s->d_partG);
+        untrack(s, s->d_partT);
+        RET(track(s, (void **)&s->d_partG, sizeof(double) * c));
+        RET(track(s, (void **)&s->d_partT, sizeof(double) * PT_STRIDE * c));
+        s->cap_items = c;
+        changed = true;
+    }
+    size_t ws = (size_t)n_ops * ws_per_op;
+    if (ws > s->cap_ws) {
+        untrack(s, s->d_ws);
+        RET(track(s, (void **)&s->d_ws, ws));
+        s->cap_ws = ws;
+    }
+    if (changed) s->buf_gen++;
+    return REG_OK;
+}
+
+// Capture GRAPH_STEPS steps [P G T C plan] into one executable graph.
+reg_status build_graph(reg_series *s)
+{
+    if (s->gexec && s->graph_gen == s->buf_gen) return REG_OK;
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    BatchDev b = make_batch(s);
+    cudaGraph_t g;
+    // The caller's stream may be the legacy default stream, which cannot be
+    // captured: capture on a private stream, launch on the caller's stream.
+    if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = s->cap_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < GRAPH_STEPS; k++) {
+        k_prolong<<<s->grid_work, REG_THREADS, 0, cs>>>(b);
+        launch_grad(s->bf16, s->grid_work, cs, b);
+        launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, cs, b);
+        k_control<<<std::min(s->cap_ops, 2048), 256, 0, cs>>>(b);
+        k_plan<<<1, 1024, 0, cs>>>(b);
+    }
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) return fail(REG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(REG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    s->graph_gen = s->buf_gen;
+    return REG_OK;
+}
+
+void collect_profile(reg_series *s)
+{
+    if (!((s->p.flags & REG_FLAG_PROFILE) && s->ev_ok)) return;
+    for (int k = 0; k < GRAPH_STEPS; k++) {
+        cudaEvent_t seq[NFAM] = {s->ev[k][F_P], s->ev[k][F_G], s->ev[k][F_T], s->ev[k][F_C], s->ev[k][F_PLAN], s->ev_end[k]};
+        for (int f = 0; f < 5; f++) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, seq[f], seq[f + 1]);
+            if (e == cudaSuccess) s->fam[f].ms += ms;
+            else {
+                cudaGetLastError();
+                s->ev_ok = false;
+            }
+        }
+    }
+}
+
+// Resolve image pointers of frame f (series si) at level index k.
+const void *img_ptr(reg_series *s, const SeriesInfo &si, int frame, int k)
+{
+    size_t esz = s->bf16 ? 2 : 4;
+    return (const char *)si.pyr + ((size_t)frame * si.frame_block + si.img_off[k]) * esz;
+}
+
+// Run one batch of operator applications.  pre_iter runs on the stream after
+// all operands have been read (composition) and before any result is written.
+template <class F>
+reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, int32_t *status_out,
+                     int32_t *iters_out)
+{
+    int n = (int)ops.size();
+    if (n == 0) return pre_iter();
+    size_t ws = 0;
+    int64_t items = 0;
+    int nl = 0, nLmax = 0;
+    for (auto &o : ops) {
+        const SeriesInfo &si = s->S[o.series];
+        ws = std::max(ws, si.ws_bytes);
+        items = std::max<int64_t>(items, node_tiles(si.n[si.nl - 1]));
+        nl = std::max(nl, si.nl);
+        nLmax = std::max(nLmax, si.n[si.nl - 1]);
+    }
+    RET(ensure_capacity(s, n, ws, items));
+    for (int i = 0; i < n; i++) {
+        const OpReq &o = ops[i];
+        const SeriesInfo &si = s->S[o.series];
+        OpDesc &d = s->h_ops[i];
+        memset(&d, 0, sizeof(d));
+        d.nl = si.nl;
+        d.init = o.init;
+        d.left = o.left >= 0 ? si.slots + (size_t)o.left * si.slot_elems : nullptr;
+        d.right = o.right >= 0 ? si.slots + (size_t)o.right * si.slot_elems : nullptr;
+        d.out = si.slots + (size_t)o.dst * si.slot_elems;
+        d.slot_pitch = si.pitch[si.nl - 1];
+        char *w = s->d_ws + (size_t)i * ws;
+        for (int k = 0; k < si.nl; k++) {
+            LevelDesc &L = d.lv[k];
+            L.n = si.n[k];
+            L.pitch = si.pitch[k];
+            double h = 1.0 / (L.n - 1);
+            L.h2d = h * h;
+            L.h2 = (float)L.h2d;
+            L.R = img_ptr(s, si, o.frame_i, k);
+            L.T = img_ptr(s, si, o.frame_k, k);
+            size_t fb = si.field_bytes(k), ub = si.ufield_bytes(k);
+            char *base = w + si.ws_off[k];
+            L.U[0] = (float4 *)(base);
+            L.U[1] = (float4 *)(base + ub);
+            L.D[0] = (float2 *)(base + 2 * ub);
+            L.D[1] = (float2 *)(base + 2 * ub + fb);
+        }
+    }
+    CK(cudaMemcpyAsync(s->d_ops, s->h_ops, sizeof(OpDesc) * n, cudaMemcpyHostToDevice, s->stream));
+    s->h_ctr[0] = n;
+    for (int k = 1; k < 16; k++) s->h_ctr[k] = 0;
+    CK(cudaMemcpyAsync(s->d_ctr, s->h_ctr, sizeof(int) * 16, cudaMemcpyHostToDevice, s->stream));
+    BatchDev b = make_batch(s);
+    dim3 blk(32, 8);
+    k_compose<<<dim3(cdiv(nLmax, 32), cdiv(nLmax, 8), n), blk, 0, s->stream>>>(b);
+    for (int st = 1; st < nl; st++) {
+        int nc = 0;
+        for (auto &o : ops) {
+            const SeriesInfo &si = s->S[o.series];
+            int k = si.nl - 1 - st;
+            if (k >= 0) nc = std::max(nc, si.n[k]);
+        }
+        k_restrict_u<<<dim3(cdiv(nc, 32), cdiv(nc, 8), n), blk, 0, s->stream>>>(b, st);
+    }
+    int n0 = 0;
+    for (auto &o : ops) n0 = std::max(n0, s->S[o.series].n[0]);
+    k_zero_u<<<dim3(cdiv(n0, 32), cdiv(n0, 8), n), blk, 0, s->stream>>>(b);
+    CK(cudaGetLastError());
+    RET(pre_iter());
+    k_init_state<<<cdiv(n, 256), 256, 0, s->stream>>>(b, n);
+    k_plan<<<1, 1024, 0, s->stream>>>(b);
+    CK(cudaGetLastError());
+    s->fam[F_SETUP].launches += 4 + nl;
+    RET(build_graph(s));
+    int max_steps = s->p.max_steps > 0 ? s->p.max_steps
+                                       : nl * (s->p.iter_max * (2 + 48 / std::max(1, s->p.trials_per_pass)) + 4) + 64;
+    int steps = 0;
+    const bool prof = (s->p.flags & REG_FLAG_PROFILE) && s->ev_ok;
+    for (;;) {
+        if (prof) {
+            // profiling: the same step kernels launched one by one between events
+            for (int k = 0; k < GRAPH_STEPS; k++) {
+                cudaEventRecord(s->ev[k][F_P], s->stream);
+                k_prolong<<<s->grid_work, REG_THREADS, 0, s->stream>>>(b);
+                cudaEventRecord(s->ev[k][F_G], s->stream);
+                launch_grad(s->bf16, s->grid_work, s->stream, b);
+                cudaEventRecord(s->ev[k][F_T], s->stream);
+                launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, s->stream, b);
+                cudaEventRecord(s->ev[k][F_C], s->stream);
+                k_control<<<std::min(s->cap_ops, 2048), 256, 0, s->stream>>>(b);
+                cudaEventRecord(s->ev[k][F_PLAN], s->stream);
+                k_plan<<<1, 1024, 0, s->stream>>>(b);
+                cudaEventRecord(s->ev_end[k], s->stream);
+            }
+            CK(cudaGetLastError());
+        } else {
+            CK(cudaGraphLaunch(s->gexec, s->stream));
+        }
+        CK(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(int) * 16, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        steps += GRAPH_STEPS;
+        collect_profile(s);
+        for (int f = 0; f < 5; f++) s->fam[f].launches += GRAPH_STEPS;
+        if (s->h_ctr[8]) return fail(REG_EKERNEL, "operator state machine reported an internal error");
+        if (s->h_ctr[7] == 0) break;
+        if (steps > max_steps) return fail(REG_ETIMEOUT, "batch did not finish within %d steps", max_steps);
+    }
+    s->tot_steps += steps;
+    s->tot_ops += n;
+    if (n > s->h_st_cap) {
+        if (s->h_st) cudaFreeHost(s->h_st);
+        CK(cudaMallocHost((void **)&s->h_st, sizeof(OpState) * n));
+        s->h_st_cap = n;
+    }
+    CK(cudaMemcpyAsync(s->h_st, s->d_st, sizeof(OpState) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < n; i++) {
+        const OpState &st = s->h_st[i];
+        s->tot_iters += st.iters_total;
+        s->tot_trials += st.trials_seq;
+        s->tot_evals += st.evals;
+        if (status_out) status_out[i] = st.nonfinite_seen ? REG_OP_NONFINITE : st.status;
+        if (iters_out) iters_out[i] = st.iters_total;
+    }
+    return REG_OK;
+}
+
+reg_status validate_params(const reg_params *p)
+{
+    if (p->iter_max < 1 || p->iter_max > 100000) return fail(REG_EINVAL, "iter_max out of range");
+    if (!(p->lambda >= 0.0) || !(p->armijo_sigma > 0.0 && p->armijo_sigma < 1.0))
+        return fail(REG_EINVAL, "lambda must be >= 0 and 0 < sigma < 1");
+    if (!(p->tau_min > 0.0 && p->tau_init >= p->tau_min && p->tau_max >= p->tau_init))
+        return fail(REG_EINVAL, "need 0 < tau_min <= tau_init <= tau_max");
+    if (p->trials_per_pass < 1 || p->trials_per_pass > REG_MAX_TRIALS)
+        return fail(REG_EINVAL, "trials_per_pass must be in [1, %d]", REG_MAX_TRIALS);
+    if (p->storage != REG_STORAGE_F32 && p->storage != REG_STORAGE_BF16) return fail(REG_EINVAL, "bad storage");
+    return REG_OK;
+}
+
+// Copy a slot field (device) to another slot.
+reg_status copy_slot(reg_series *s, const SeriesInfo &si, int dst, int src)
+{
+    CK(cudaMemcpyAsync(si.slots + (size_t)dst * si.slot_elems, si.slots + (size_t)src * si.slot_elems,
+                       si.slot_elems * sizeof(float2), cudaMemcpyDeviceToDevice, s->stream));
+    return REG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void reg_default_params(reg_params *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->n_levels = 3;
+    p->iter_max = 50;
+    p->epsilon = 1e-7;
+    p->lambda = 10.0;
+    p->armijo_sigma = 0.5;
+    p->tau_init = 1.0;
+    p->tau_max = 1e4;
+    p->tau_min = 1e-12;
+    p->storage = REG_STORAGE_F32;
+    p->trials_per_pass = 4;
+    p->max_steps = 0;
+    p->flags = 0;
+}
+
+const char *reg_status_string(reg_status st)
+{
+    switch (st) {
+    case REG_OK: return "ok";
+    case REG_EINVAL: return "invalid argument";
+    case REG_ENOMEM: return "out of memory";
+    case REG_ECUDA: return "CUDA error";
+    case REG_ESTATE: return "invalid state";
+    case REG_ETIMEOUT: return "step budget exhausted";
+    case REG_EKERNEL: return "kernel reported an error";
+    }
+    return "unknown status";
+}
+
+const char *reg_last_error(void) { return g_err.c_str(); }
+
+reg_status reg_create_series(const float *frames, int32_t n_series, const int32_t *frames_per_series,
+                             const int32_t *side_px, int64_t pitch_elems, int32_t frames_on_device,
+                             const reg_params *p, void *cuda_stream, reg_series_t *out)
+{
+    g_err.clear();
+    if (!out || !frames || !frames_per_series || !side_px || !p || n_series < 1)
+        return fail(REG_EINVAL, "null argument or n_series < 1");
+    *out = nullptr;
+    RET(validate_params(p));
+    int64_t total_frames = 0;
+    int maxside = 0;
+    for (int i = 0; i < n_series; i++) {
+        int sd = side_px[i];
+        if (sd < 32 || sd > 4096 || (sd & (sd - 1))) return fail(REG_EINVAL, "side %d is not a power of two in [32, 4096]", sd);
+        if (frames_per_series[i] < 2) return fail(REG_EINVAL, "series %d has fewer than 2 frames", i);
+        int L = 0;
+        while ((1 << L) < sd) L++;
+        if (p->n_levels < 1 || p->n_levels > L - 3 || p->n_levels > REG_MAX_LEVELS)
+            return fail(REG_EINVAL, "n_levels must be in [1, L-3] (L = %d)", L);
+        total_frames += frames_per_series[i];
+        maxside = std::max(maxside, sd);
+    }
+    if (pitch_elems < maxside) return fail(REG_EINVAL, "pitch_elems smaller than the largest side");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    reg_series *s = new reg_series();
+    s->stream = (cudaStream_t)cuda_stream;
+    s->p = *p;
+    s->bf16 = p->storage == REG_STORAGE_BF16;
+    cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
+    int occ = trial_blocks_per_sm(p->trials_per_pass);
+    s->grid_work = s->nsm * std::max(1, std::min(occ, 8));
+    CK(cudaMallocHost((void **)&s->h_ctr, sizeof(int) * 16));
+    s->ev_ok = true;
+    for (int k = 0; k < GRAPH_STEPS && s->ev_ok; k++) {
+        for (int f = 0; f < NFAM; f++)
+            if (cudaEventCreate(&s->ev[k][f]) != cudaSuccess) s->ev_ok = false;
+        if (cudaEventCreate(&s->ev_end[k]) != cudaSuccess) s->ev_ok = false;
+    }
+    auto cleanup = [&](reg_status st) {
+        reg_destroy_series(s);
+        return st;
+    };
+    reg_status st;
+    if ((st = track(s, (void **)&s->d_ctr, sizeof(int) * 16)) != REG_OK) return cleanup(st);
+    if ((st = track(s, (void **)&s->d_work, sizeof(unsigned long long) * 16)) != REG_OK) return cleanup(st);
+    if (cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long) * 16, s->stream) != cudaSuccess)
+        return cleanup(fail(REG_ECUDA, "memset"));
+    // series geometry
+    int fb = 0;
+    int64_t frame_off = 0;
+    for (int i = 0; i < n_series; i++) {
+        SeriesInfo si;
+        si.n_frames = frames_per_series[i];
+        si.side = side_px[i];
+        while ((1 << si.L) < si.side) si.L++;
+        si.nl = p->n_levels;
+        si.m0 = si.L - si.nl + 1;
+        si.frame_base = fb;
+        fb += si.n_frames;
+        si.n_data = si.n_frames - 1;
+        int aux = 0;
+        for (int kind = 0; kind <= regsched::K_BLELLOCH; kind++)
+            aux = std::max(aux, regsched::aux_slots(kind, si.n_data, 0, 0));
+        // chunked strategies: up to 64 chunks with any global algorithm
+        aux = std::max(aux, regsched::aux_slots(regsched::K_CHUNKED, si.n_data, 64, regsched::K_BLELLOCH));
+        si.n_slots = si.n_data + aux;
+        size_t off = 0, woff = 0;
+        for (int k = 0; k < si.nl; k++) {
+            int nn = (1 << (si.m0 + k)) + 1;
+            si.n.push_back(nn);
+            si.pitch.push_back(round_up(nn, 32));
+            si.img_off.push_back(off);
+            off += (size_t)nn * si.pitch.back();
+            si.ws_off.push_back(woff);
+            woff += 2 * si.ufield_bytes(k) + 2 * si.field_bytes(k);
+        }
+        si.frame_block = round_up((int)std::min<size_t>(off, (size_t)1 << 30), 64);
+        si.ws_bytes = woff;
+        si.slot_elems = (size_t)si.n[si.nl - 1] * si.pitch[si.nl - 1];
+        si.meta.assign(si.n_slots, SlotMeta{});
+        size_t esz = s->bf16 ? 2 : 4;
+        if ((st = track(s, &si.pyr, si.frame_block * si.n_frames * esz)) != REG_OK) return cleanup(st);
+        if ((st = track(s, (void **)&si.slots, si.slot_elems * si.n_slots * sizeof(float2))) != REG_OK) return cleanup(st);
+        s->S.push_back(si);
+    }
+    // Pyramid construction in chunks of frames: raw level L, restriction chain,
+    // per-level FE mean/sigma, normalisation into the stored pyramid.
+    for (int i = 0; i < n_series; i++) {
+        SeriesInfo &si = s->S[i];
+        int nL = si.side + 1;
+        int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(si.n_frames, (512ll << 20) / ((int64_t)nL * nL * 4 * 2)));
+        void *raw = nullptr, *stage = nullptr, *stats = nullptr;
+        size_t raw_bytes = (size_t)chunk * si.frame_block * 4;
+        if ((st = dalloc(s, &raw, raw_bytes)) != REG_OK) return cleanup(st);
+        if ((st = dalloc(s, &stats, sizeof(double) * 2 * chunk)) != REG_OK) return cleanup(st);
+        size_t stage_bytes = (size_t)chunk * si.side * si.side * 4;
+        if (!frames_on_device && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
+        for (int f0 = 0; f0 < si.n_frames; f0 += chunk) {
+            int nf = std::min(chunk, si.n_frames - f0);
+            const float *src = frames + (frame_off + f0) * (int64_t)si.side * pitch_elems;
+            int64_t fstride = (int64_t)si.side * pitch_elems, pitch = pitch_elems;
+            if (!frames_on_device) {
+                cudaError_t e = cudaMemcpy2DAsync(stage, si.side * 4, src, pitch_elems * 4, si.side * 4,
+                                                  (size_t)si.side * nf, cudaMemcpyHostToDevice, s->stream);
+                if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "frame upload: %s", cudaGetErrorString(e)));
+                src = (const float *)stage;
+                fstride = (int64_t)si.side * si.side;
+                pitch = si.side;
+            }
+            int kL = si.nl - 1;
+            float *rawf = (float *)raw;
+            dim3 blk(32, 8);
+            k_embed<<<dim3(cdiv(nL, 32), cdiv(nL, 8), nf), blk, 0, s->stream>>>(
+                src, fstride, pitch, si.side, rawf + si.img_off[kL], (int64_t)si.frame_block, si.pitch[kL]);
+            for (int k = kL - 1; k >= 0; k--)
+                k_restrict_img<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+                    rawf + si.img_off[k + 1], (int64_t)si.frame_block, si.pitch[k + 1], si.n[k + 1],
+                    rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k]);
+            for (int k = 0; k < si.nl; k++) {
+                k_image_stats<<<nf, 512, 0, s->stream>>>(rawf + si.img_off[k], (int64_t)si.frame_block,
+                                                         si.pitch[k], si.n[k], (double *)stats);
+                size_t esz = s->bf16 ? 2 : 4;
+                char *dst = (char *)si.pyr + ((size_t)f0 * si.frame_block + si.img_off[k]) * esz;
+                k_normalize<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+                    rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k], si.n[k], (const double *)stats,
+                    dst, (int64_t)si.frame_block, si.pitch[k], s->bf16);
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid kernels: %s", cudaGetErrorString(e)));
+        }
+        dfree(s, raw, raw_bytes);
+        dfree(s, stats, 0);
+        dfree(s, stage, stage_bytes);
+        frame_off += si.n_frames;
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid sync"));
+    *out = s;
+    return REG_OK;
+}
+
+reg_status reg_destroy_series(reg_series_t s)
+{
+    if (!s) return REG_OK;
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (size_t i = 0; i + 1 < s->allocs.size(); i += 2) dfree(s, s->allocs[i], reinterpret_cast<size_t>(s->allocs[i + 1]));
+    cudaStreamSynchronize(s->stream);
+    if (s->h_ops) cudaFreeHost(s->h_ops);
+    if (s->h_ctr) cudaFreeHost(s->h_ctr);
+    if (s->h_st) cudaFreeHost(s->h_st);
+    for (int k = 0; k < GRAPH_STEPS; k++) {
+        for (int f = 0; f < NFAM; f++)
+            if (s->ev[k][f]) cudaEventDestroy(s->ev[k][f]);
+        if (s->ev_end[k]) cudaEventDestroy(s->ev_end[k]);
+    }
+    delete s;
+    return REG_OK;
+}
+
+static reg_status check_op(reg_series *s, const reg_op_desc &o, OpReq &r)
+{
+    if (o.series < 0 || o.series >= (int)s->S.size()) return fail(REG_EINVAL, "series index out of range");
+    const SeriesInfo &si = s->S[o.series];
+    if (o.frame_i < 0 || o.frame_i >= si.n_frames || o.frame_k < 0 || o.frame_k >= si.n_frames)
+        return fail(REG_EINVAL, "frame index out of range");
+    if (o.dst_slot < 0 || o.dst_slot >= si.n_slots) return fail(REG_EINVAL, "dst slot out of range");
+    auto slot_ok = [&](int k) { return k < 0 || k < si.n_slots; };
+    if (!slot_ok(o.left_slot) || !slot_ok(o.right_slot)) return fail(REG_EINVAL, "slot out of range");
+    if (o.right_slot >= 0 && o.left_slot < 0) return fail(REG_EINVAL, "right operand without left operand");
+    r.series = o.series;
+    r.frame_i = si.frame_base + o.frame_i;
+    r.frame_k = si.frame_base + o.frame_k;
+    // frame indices inside the series pyramid are local
+    r.frame_i = o.frame_i;
+    r.frame_k = o.frame_k;
+    r.left = o.left_slot;
+    r.right = o.right_slot;
+    r.dst = o.dst_slot;
+    r.init = o.left_slot < 0 ? 0 : (o.right_slot < 0 ? 1 : 2);
+    if (r.init >= 1) {
+        const SlotMeta &a = si.meta[o.left_slot];
+        if (a.end < 0) return fail(REG_EINVAL, "left slot %d holds no deformation", o.left_slot);
+        if (r.init == 1 && (a.start != o.frame_i || a.end != o.frame_k))
+            return fail(REG_EINVAL, "left slot holds phi_{%d,%d}, op registers (%d,%d)", a.start, a.end, o.frame_i, o.frame_k);
+        if (r.init == 2) {
+            const SlotMeta &b = si.meta[o.right_slot];
+            if (b.end < 0) return fail(REG_EINVAL, "right slot %d holds no deformation", o.right_slot);
+            if (a.end != b.start) return fail(REG_EINVAL, "chain mismatch: phi_{%d,%d} then phi_{%d,%d}", a.start, a.end, b.start, b.end);
+            if (a.start != o.frame_i || b.end != o.frame_k)
+                return fail(REG_EINVAL, "operands span (%d,%d), op registers (%d,%d)", a.start, b.end, o.frame_i, o.frame_k);
+        }
+    }
+    return REG_OK;
+}
+
+reg_status reg_apply_operator_batch(reg_series_t s, int32_t n_ops, const reg_op_desc *ops, int32_t *op_status_out,
+                                    int32_t *iters_out)
+{
+    g_err.clear();
+    if (!s || n_ops < 0 || (n_ops > 0 && !ops)) return fail(REG_EINVAL, "null handle or ops");
+    std::vector<OpReq> req(n_ops);
+    for (int i = 0; i < n_ops; i++) RET(check_op(s, ops[i], req[i]));
+    for (int i = 0; i < n_ops; i++)
+        for (int j = i + 1; j < n_ops; j++)
+            if (ops[i].series == ops[j].series && ops[i].dst_slot == ops[j].dst_slot)
+                return fail(REG_EINVAL, "two ops write slot %d", ops[i].dst_slot);
+    RET(run_batch(s, req, [] { return REG_OK; }, op_status_out, iters_out));
+    for (int i = 0; i < n_ops; i++) {
+        SlotMeta &m = s->S[ops[i].series].meta[ops[i].dst_slot];
+        m.start = ops[i].frame_i;
+        m.end = ops[i].frame_k;
+    }
+    return REG_OK;
+}
+
+reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, reg_scan_kind global_kind,
+                           char *report, size_t buf_len)
+{
+    g_err.clear();
+    if (!s) return fail(REG_EINVAL, "null handle");
+    if (kind < REG_SCAN_SERIAL || kind > REG_SCAN_CHUNKED_ALT) return fail(REG_EINVAL, "unknown scan kind");
+    if ((kind == REG_SCAN_CHUNKED || kind == REG_SCAN_CHUNKED_ALT) &&
+        (chunks < 1 || chunks > 64 || global_kind < REG_SCAN_SERIAL || global_kind > REG_SCAN_BLELLOCH))
+        return fail(REG_EINVAL, "chunked scans need 1 <= chunks <= 64 and a non-chunked global kind");
+    auto t0 = std::chrono::steady_clock::now();
+    int64_t ops0 = s->tot_ops, it0 = s->tot_iters, tr0 = s->tot_trials, st0 = s->tot_steps, ev0 = s->tot_evals;
+    // preprocessing: A(f_e, f_{e+1}, I) -> slot e, all series in one batch
+    std::vector<OpReq> pre;
+    for (int si = 0; si < (int)s->S.size(); si++) {
+        SeriesInfo &S = s->S[si];
+        for (auto &m : S.meta) m = SlotMeta{};
+        for (int e = 0; e < S.n_data; e++) pre.push_back(OpReq{si, e, e + 1, 0, -1, -1, e});
+    }
+    std::vector<int32_t> stat(pre.size());
+    RET(run_batch(s, pre, [] { return REG_OK; }, stat.data(), nullptr));
+    int counts[5] = {0, 0, 0, 0, 0};
+    for (auto v : stat) counts[std::min(std::max(v, 0), 4)]++;
+    for (auto &o : pre) s->S[o.series].meta[o.dst] = SlotMeta{o.frame_i, o.frame_k};
+    std::vector<regsched::Schedule> sch(s->S.size());
+    size_t nlev = 0;
+    for (size_t si = 0; si < s->S.size(); si++) {
+        if (!regsched::make_schedule((int)kind, s->S[si].n_data, chunks, (int)global_kind, sch[si]))
+            return fail(REG_EINVAL, "schedule generation failed");
+        nlev = std::max(nlev, sch[si].levels.size());
+    }
+    int batches = 0, scan_ops = 0;
+    for (size_t t = 0; t < nlev; t++) {
+        std::vector<OpReq> reg;
+        struct Copy { int series, dst, src; };
+        std::vector<Copy> copies;
+        std::vector<std::pair<int, std::pair<int, SlotMeta>>> writes;  // series, (slot, meta)
+        for (size_t si = 0; si < s->S.size(); si++) {
+            if (t >= sch[si].levels.size()) continue;
+            SeriesInfo &S = s->S[si];
+            for (auto &o : sch[si].levels[t]) {
+                if (o.kind == regsched::OP_IDENTITY) {
+                    writes.push_back({(int)si, {o.dst, SlotMeta{}}});
+                } else if (o.kind == regsched::OP_COPY) {
+                    const SlotMeta &m = S.meta[o.a];
+                    if (m.end >= 0) copies.push_back({(int)si, o.dst, o.a});
+                    writes.push_back({(int)si, {o.dst, m}});
+                } else {
+                    const SlotMeta &a = S.meta[o.a], &b = S.meta[o.b];
+                    if (a.end < 0) {
+                        if (b.end >= 0) copies.push_back({(int)si, o.dst, o.b});
+                        writes.push_back({(int)si, {o.dst, b}});
+                    } else if (b.end < 0) {
+                        copies.push_back({(int)si, o.dst, o.a});
+                        writes.push_back({(int)si, {o.dst, a}});
+                    } else {
+                        if (a.end != b.start) return fail(REG_EKERNEL, "schedule chain mismatch");
+                        reg.push_back(OpReq{(int)si, a.start, b.end, 2, o.a, o.b, o.dst});
+                        writes.push_back({(int)si, {o.dst, SlotMeta{a.start, b.end}}});
+                    }
+                }
+            }
+        }
+        // copies whose source is also a destination of this level must read first:
+        // they run after composition and before any result is written.
+        auto do_copies = [&]() -> reg_status {
+            for (auto &c : copies)
+                if (c.dst != c.src) RET(copy_slot(s, s->S[c.series], c.dst, c.src));
+            return REG_OK;
+        };
+        std::vector<int32_t> st2(reg.size());
+        RET(run_batch(s, reg, do_copies, st2.data(), nullptr));
+        for (auto v : st2) counts[std::min(std::max(v, 0), 4)]++;
+        if (!reg.empty()) batches++;
+        scan_ops += (int)reg.size();
+        for (auto &w : writes) s->S[w.first].meta[w.second.first] = w.second.second;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (auto &S : s->S)
+        for (int e = 0; e < S.n_data; e++)
+            if (S.meta[e].start != 0 || S.meta[e].end != e + 1) return fail(REG_EKERNEL, "scan did not produce phi_{0,%d}", e + 1);
+    if (report && buf_len > 0) {
+        snprintf(report, buf_len,
+                 "{\"kind\": %d, \"preprocessing_ops\": %zu, \"scan_ops\": %d, \"scan_batches\": %d, "
+                 "\"ops\": %lld, \"iters\": %lld, \"trials\": %lld, \"evals\": %lld, \"steps\": %lld, \"ms\": %.3f, "
+                 "\"status\": {\"converged\": %d, \"maxiter\": %d, \"stalled\": %d, \"nonfinite\": %d, \"zero_gradient\": %d}}",
+                 (int)kind, pre.size(), scan_ops, batches, (long long)(s->tot_ops - ops0),
+                 (long long)(s->tot_iters - it0), (long long)(s->tot_trials - tr0), (long long)(s->tot_evals - ev0),
+                 (long long)(s->tot_steps - st0), ms, counts[0], counts[1], counts[2], counts[3], counts[4]);
+    }
+    return REG_OK;
+}
+
+reg_status reg_get_slot(reg_series_t s, int32_t series, int32_t slot, float *out, int32_t out_on_device,
+                        int32_t *start_end)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad handle or series");
+    SeriesInfo &si = s->S[series];
+    if (slot < 0 || slot >= si.n_slots) return fail(REG_EINVAL, "slot out of range");
+    if (start_end) {
+        start_end[0] = si.meta[slot].start;
+        start_end[1] = si.meta[slot].end;
+    }
+    if (!out) return REG_OK;
+    int n = si.side + 1;
+    size_t bytes = (size_t)2 * n * n * sizeof(float);
+    float *dst = out;
+    void *tmp = nullptr;
+    if (!out_on_device) {
+        RET(dalloc(s, &tmp, bytes));
+        dst = (float *)tmp;
+    }
+    const float2 *src = si.meta[slot].end >= 0 ? si.slots + (size_t)slot * si.slot_elems : nullptr;
+    k_slot_to_planes<<<dim3(cdiv(n, 32), cdiv(n, 8)), dim3(32, 8), 0, s->stream>>>(src, si.pitch[si.nl - 1], n, dst);
+    CK(cudaGetLastError());
+    if (!out_on_device) {
+        CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s->stream));
+        dfree(s, tmp, bytes);
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+reg_status reg_set_slot(reg_series_t s, int32_t series, int32_t slot, const float *field, int32_t on_device,
+                        int32_t start, int32_t end)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad handle or series");
+    SeriesInfo &si = s->S[series];
+    if (slot < 0 || slot >= si.n_slots) return fail(REG_EINVAL, "slot out of range");
+    if (end < 0) {
+        si.meta[slot] = SlotMeta{};
+        return REG_OK;
+    }
+    if (!field || start < 0 || start >= si.n_frames || end >= si.n_frames) return fail(REG_EINVAL, "bad field or frames");
+    int n = si.side + 1;
+    size_t bytes = (size_t)2 * n * n * sizeof(float);
+    const float *src = field;
+    void *tmp = nullptr;
+    if (!on_device) {
+        RET(dalloc(s, &tmp, bytes));
+        CK(cudaMemcpyAsync(tmp, field, bytes, cudaMemcpyHostToDevice, s->stream));
+        src = (const float *)tmp;
+    }
+    k_planes_to_slot<<<dim3(cdiv(n, 32), cdiv(n, 8)), dim3(32, 8), 0, s->stream>>>(
+        src, n, si.slots + (size_t)slot * si.slot_elems, si.pitch[si.nl - 1]);
+    CK(cudaGetLastError());
+    if (tmp) dfree(s, tmp, bytes);
+    CK(cudaStreamSynchronize(s->stream));
+    si.meta[slot] = SlotMeta{start, end};
+    return REG_OK;
+}
+
+reg_status reg_num_slots(reg_series_t s, int32_t series, int32_t *n_slots)
+{
+    if (!s || !n_slots || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad argument");
+    *n_slots = s->S[series].n_slots;
+    return REG_OK;
+}
+
+reg_status reg_get_deformations(reg_series_t s, int32_t series, int32_t first, int32_t count, float *out,
+                                int32_t out_on_device)
+{
+    g_err.clear();
+    if (!s || !out || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad argument");
+    SeriesInfo &si = s->S[series];
+    if (first < 0 || count < 0 || first + count > si.n_frames) return fail(REG_EINVAL, "frame range out of range");
+    size_t per = (size_t)2 * si.side * si.side;
+    void *tmp = nullptr;
+    float *dst = out;
+    if (!out_on_device && count > 0) {
+        RET(dalloc(s, &tmp, per * count * sizeof(float)));
+        dst = (float *)tmp;
+    }
+    for (int k = first; k < first + count; k++) {
+        const float2 *src = nullptr;
+        if (k > 0) {
+            const SlotMeta &m = si.meta[k - 1];
+            if (m.start != 0 || m.end != k) {
+                if (tmp) dfree(s, tmp, 0);
+                return fail(REG_ESTATE, "phi_{0,%d} not available (run reg_prefix_scan first)", k);
+            }
+            src = si.slots + (size_t)(k - 1) * si.slot_elems;
+        }
+        k_slot_to_planes<<<dim3(cdiv(si.side, 32), cdiv(si.side, 8)), dim3(32, 8), 0, s->stream>>>(
+            src, si.pitch[si.nl - 1], si.side, dst + (size_t)(k - first) * per);
+    }
+    CK(cudaGetLastError());
+    if (tmp) {
+        CK(cudaMemcpyAsync(out, tmp, per * count * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        dfree(s, tmp, 0);
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+// Diagnostics: one START step (energy) and optionally one G pass (direction)
+// of a single op at a single level, through the same kernels as the batches.
+static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int level, const float *u_grid, int &k)
+{
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad handle or series");
+    SeriesInfo &si = s->S[series];
+    if (fi < 0 || fi >= si.n_frames || fk < 0 || fk >= si.n_frames) return fail(REG_EINVAL, "frame out of range");
+    k = level - si.m0;
+    if (k < 0 || k >= si.nl) return fail(REG_EINVAL, "level outside the pyramid");
+    if (!u_grid) return fail(REG_EINVAL, "null displacement");
+    std::vector<OpReq> one{OpReq{series, fi, fk, 0, -1, -1, 0}};
+    RET(ensure_capacity(s, 1, si.ws_bytes, node_tiles(si.n[si.nl - 1])));
+    OpDesc &d = s->h_ops[0];
+    memset(&d, 0, sizeof(d));
+    d.nl = si.nl;
+    d.init = 0;
+    d.out = nullptr;
+    for (int q = 0; q < si.nl; q++) {
+        LevelDesc &L = d.lv[q];
+        L.n = si.n[q];
+        L.pitch = si.pitch[q];
+        double h = 1.0 / (L.n - 1);
+        L.h2d = h * h;
+        L.h2 = (float)L.h2d;
+        L.R = img_ptr(s, si, fi, q);
+        L.T = img_ptr(s, si, fk, q);
+        size_t fb = si.field_bytes(q), ub = si.ufield_bytes(q);
+        char *base = s->d_ws + si.ws_off[q];
+        L.U[0] = (float4 *)base;
+        L.U[1] = (float4 *)(base + ub);
+        L.D[0] = (float2 *)(base + 2 * ub);
+        L.D[1] = (float2 *)(base + 2 * ub + fb);
+    }
+    CK(cudaMemcpyAsync(s->d_ops, s->h_ops, sizeof(OpDesc), cudaMemcpyHostToDevice, s->stream));
+    // u planes (2 x n x n) -> float2 field U0 of level k
+    int n = si.n[k];
+    std::vector<float4> tmp((size_t)n * si.pitch[k], make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++)
+            tmp[(size_t)r * si.pitch[k] + c] =
+                make_float4(u_grid[(size_t)r * n + c], u_grid[(size_t)n * n + (size_t)r * n + c], 0.f, 0.f);
+    CK(cudaMemcpyAsync(d.lv[k].U[0], tmp.data(), tmp.size() * sizeof(float4), cudaMemcpyHostToDevice, s->stream));
+    s->h_ctr[0] = 1;
+    for (int q = 1; q < 16; q++) s->h_ctr[q] = 0;
+    CK(cudaMemcpyAsync(s->d_ctr, s->h_ctr, sizeof(int) * 16, cudaMemcpyHostToDevice, s->stream));
+    BatchDev b = make_batch(s);
+    k_init_state<<<1, 32, 0, s->stream>>>(b, 1);
+    OpState st;
+    memset(&st, 0, sizeof(st));
+    st.phase = PH_START;
+    st.lvl = k;
+    st.tau = s->p.tau_init;
+    CK(cudaMemcpyAsync(s->d_st, &st, sizeof(OpState), cudaMemcpyHostToDevice, s->stream));
+    // START: plan, T, C
+    k_plan<<<1, 1024, 0, s->stream>>>(b);
+    launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, s->stream, b);
+    k_control<<<1, 256, 0, s->stream>>>(b);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+reg_status reg_eval_energy(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                           const float *u_grid, double *parts)
+{
+    g_err.clear();
+    int k;
+    RET(diag_setup(s, series, frame_i, frame_k, level, u_grid, k));
+    OpState st;
+    CK(cudaMemcpy(&st, s->d_st, sizeof(OpState), cudaMemcpyDeviceToHost));
+    if (parts) {
+        parts[0] = st.E;
+        parts[1] = st.ncc;
+        parts[2] = st.E + st.ncc;
+        parts[3] = st.Tbar;
+        parts[4] = st.sigT;
+    }
+    return REG_OK;
+}
+
+__global__ void k_sum_range(const double *v, int b, int e, double *out)
+{
+    double s = 0.0;
+    for (int i = b + threadIdx.x; i < e; i += 32) s += v[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
+}
+
+reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                              const float *u_grid, float *d_out, double *slope)
+{
+    g_err.clear();
+    int k;
+    RET(diag_setup(s, series, frame_i, frame_k, level, u_grid, k));
+    BatchDev b = make_batch(s);
+    // state is now PH_GRAD with src = 0, cur = 1 (no pending step)
+    k_plan<<<1, 1024, 0, s->stream>>>(b);
+    launch_grad(s->bf16, s->grid_work, s->stream, b);
+    CK(cudaGetLastError());
+    OpState st;
+    CK(cudaMemcpyAsync(&st, s->d_st, sizeof(OpState), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (st.phase != PH_GRAD) return fail(REG_ESTATE, "energy at the given displacement is not finite");
+    if (!s->d_scratch) RET(track(s, (void **)&s->d_scratch, sizeof(double) * 16));
+    k_sum_range<<<1, 32, 0, s->stream>>>(s->d_partG, st.g_begin, st.g_end, s->d_scratch);
+    double sl = 0.0;
+    CK(cudaMemcpyAsync(&sl, s->d_scratch, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    const SeriesInfo &si = s->S[series];
+    int n = si.n[k];
+    std::vector<float2> tmp((size_t)n * si.pitch[k]);
+    OpDesc d;
+    CK(cudaMemcpyAsync(&d, s->d_ops, sizeof(OpDesc), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(tmp.data(), d.lv[k].D[st.cur], tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+    if (slope) *slope = sl;
+    if (d_out)
+        for (int r = 0; r < n; r++)
+            for (int c = 0; c < n; c++) {
+                d_out[(size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].x;
+                d_out[(size_t)n * n + (size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].y;
+            }
+    return REG_OK;
+}
+
+reg_status reg_schedule(reg_scan_kind kind, int32_t n, int32_t chunks, reg_scan_kind global_kind,
+                        reg_schedule_op *buf, int64_t buf_len, int64_t *n_out, int32_t *n_aux)
+{
+    g_err.clear();
+    if (n < 0 || !n_out) return fail(REG_EINVAL, "bad argument");
+    regsched::Schedule sch;
+    if (!regsched::make_schedule((int)kind, n, chunks, (int)global_kind, sch)) return fail(REG_EINVAL, "unknown schedule");
+    int64_t cnt = 0;
+    for (size_t l = 0; l < sch.levels.size(); l++)
+        for (auto &o : sch.levels[l]) {
+            if (buf && cnt < buf_len) buf[cnt] = reg_schedule_op{(int32_t)l, o.kind, o.dst, o.a, o.b};
+            cnt++;
+        }
+    *n_out = cnt;
+    if (n_aux) *n_aux = regsched::aux_slots((int)kind, n, chunks, (int)global_kind);
+    return REG_OK;
+}
+
+reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t buf_len, int32_t *n_out)
+{
+    if (!s || !n_out) return fail(REG_EINVAL, "bad argument");
+    unsigned long long w[16];
+    CK(cudaMemcpyAsync(w, s->d_work, sizeof(w), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    *n_out = NFAM;
+    for (int f = 0; f < NFAM && f < buf_len; f++) {
+        reg_kernel_stats &k = buf[f];
+        memset(&k, 0, sizeof(k));
+        snprintf(k.name, sizeof(k.name), "%s", s->fam[f].name);
+        k.launches = s->fam[f].launches;
+        k.ms = s->fam[f].ms;
+        // algorithmic bytes per node (float storage; bf16 images save 2 B per image read)
+        double img = s->bf16 ? 2.0 : 4.0;
+        // per node: u 16 B (float pair per component), d 8 B, R and T one image value each
+        if (f == F_G) {
+            k.items = (int64_t)w[KW_G];
+            k.bytes = w[KW_G] * (16.0 + 8.0 + 2 * img + 16.0 + 8.0);
+        } else if (f == F_T) {
+            k.items = (int64_t)(w[KW_T] + w[KW_TSTART]);
+            k.bytes = w[KW_T] * (16.0 + 8.0 + 2 * img) + w[KW_TSTART] * (16.0 + 2 * img);
+        } else if (f == F_P) {
+            k.items = (int64_t)(w[KW_PPROL] + w[KW_PFIN]);
+            k.bytes = w[KW_PPROL] * (16.0 + 6.0) + w[KW_PFIN] * (16.0 + 8.0 + 8.0);
+        }
+    }
+    return REG_OK;
+}
+
+reg_status reg_set_trace(reg_series_t s, int64_t capacity)
+{
+    g_err.clear();
+    if (!s || capacity < 0) return fail(REG_EINVAL, "bad argument");
+    if (s->d_trace) {
+        untrack(s, s->d_trace);
+        untrack(s, s->d_trace_len);
+        s->d_trace = nullptr;
+        s->d_trace_len = nullptr;
+    }
+    s->trace_cap = capacity;
+    if (capacity > 0) {
+        RET(track(s, (void **)&s->d_trace, sizeof(double) * 7 * capacity));
+        RET(track(s, (void **)&s->d_trace_len, sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(s->d_trace_len, 0, sizeof(unsigned long long), s->stream));
+    }
+    s->buf_gen++;  // the captured step graph holds the old pointers
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+reg_status reg_get_trace(reg_series_t s, double *out, int64_t cap, int64_t *n_out)
+{
+    g_err.clear();
+    if (!s || !n_out) return fail(REG_EINVAL, "bad argument");
+    *n_out = 0;
+    if (!s->d_trace) return REG_OK;
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, s->d_trace_len, sizeof(n), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    long long m = std::min<long long>((long long)n, s->trace_cap);
+    *n_out = m;
+    if (out && cap > 0) {
+        CK(cudaMemcpyAsync(out, s->d_trace, sizeof(double) * 7 * std::min<long long>(m, cap), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return REG_OK;
+}
+
+reg_status reg_reset_kernel_stats(reg_series_t s)
+{
+    if (!s) return fail(REG_EINVAL, "null handle");
+    for (auto &f : s->fam) {
+        f.launches = 0;
+        f.ms = 0.0;
+    }
+    CK(cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long) * 16, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+}  // extern "C"

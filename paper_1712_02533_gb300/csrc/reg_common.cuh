@@ -1,0 +1,140 @@
+// Internal device data structures of libreg (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define REG_MAX_LEVELS 8
+#define REG_MAX_TRIALS 8
+#define REG_TX 32        // work tile width (nodes or cells along x_0)
+#define REG_TY 32        // work tile height
+#define REG_THREADS 256  // threads per step-kernel block (8 warps)
+#define REG_ROWSTEP (REG_THREADS / REG_TX)  // thread (lx, ly) handles rows ly + k REG_ROWSTEP
+#define REG_RPT (REG_TY / REG_ROWSTEP)      // rows per thread
+
+// Phases of the per-operator state machine.
+enum {
+    PH_START = 0,    // evaluate the energy at the level's initial u (tau = 0)
+    PH_GRAD = 1,     // apply the pending step, then gradient + first trial pass
+    PH_TRIAL = 2,    // more step sizes of the same Armijo search
+    PH_PROLONG = 3,  // apply pending step, prolongate to the next level, then START there
+    PH_FINAL = 4,    // apply pending step on the finest level into the output slot
+    PH_DONE = 5
+};
+enum { SEARCH_INIT = 0, SEARCH_WIDEN = 1, SEARCH_SHRINK = 2 };
+enum { OPST_CONVERGED = 0, OPST_MAXITER = 1, OPST_STALLED = 2, OPST_NONFINITE = 3, OPST_ZERO_GRAD = 4 };
+
+// Device work counters (nodes swept per kernel family, summed over steps).
+enum { KW_G = 0,         // gradient pass nodes
+       KW_T = 1,         // trial pass nodes (u, d, R, T read)
+       KW_TSTART = 2,    // level-start energy nodes (u, R, T read)
+       KW_TSAMPLES = 3,  // trial samples (nodes x step sizes)
+       KW_PPROL = 4,     // prolongation: fine nodes written
+       KW_PFIN = 5,      // final write: nodes
+       KW_COUNT = 6 };
+
+struct LevelDesc {
+    int n;            // nodes per side (2^l + 1)
+    int pitch;        // row pitch in elements (float2 for U/D, scalar for images)
+    float h2;         // h^2 = 4^-l (as float for scaling, exact)
+    double h2d;       // h^2 in double
+    const void *R;    // normalised reference frame (mean 0, FE sigma 1) at this level
+    const void *T;    // normalised template frame
+    float4 *U[2];     // displacement (grid units of this level) as a float pair per
+                      // component, value = (x, y) + (z, w) ("double-float"), double-buffered
+    float2 *D[2];     // descent direction d = -g / w (grid units)
+};
+
+struct OpDesc {
+    int nl;                 // number of levels
+    int init;               // 0 identity, 1 copy left, 2 compose(left, right)
+    const float2 *left;     // finest-level slot fields (px == grid units of level L)
+    const float2 *right;
+    float2 *out;            // destination slot (finest level)
+    int slot_pitch;
+    int pad;
+    LevelDesc lv[REG_MAX_LEVELS];  // index 0 = coarsest level m0
+};
+
+struct OpState {
+    int phase, lvl, cur, src;
+    int iter, iters_total, trials_seq, evals;
+    int status, nonfinite_seen, search, ntr;
+    int t_begin, t_end, g_begin, g_end;
+    double tau;       // base step of the current search
+    double tau_acc;   // step to apply at the start of the next G/P pass
+    double sh_tau;    // shrinking: last rejected step
+    double E, Tbar, sigT, ncc;      // at the current u
+    double S1, S2, S3;              // FE sums int That, int That^2, int That R~ at the current u
+    double bS1, bS2, bS3, bncc, bdE;  // last accepted trial of the search
+    double btau;
+    double slope;
+    double trial_tau[REG_MAX_TRIALS];
+};
+
+// Device-side batch: everything the step kernels need, passed by value.
+// Sizes that change per batch live in device memory (ctr) so that a captured
+// graph stays valid across batches.
+struct BatchDev {
+    OpDesc *ops;
+    OpState *st;
+    int *listP, *listG, *listT;  // compacted op indices per family
+    int *prefP, *prefG, *prefT;  // exclusive prefix of tile counts (n+1 entries)
+    int *ctr;                    // [0] n_ops [1] nP [2] nG [3] nT [4] itemsP [5] itemsG [6] itemsT
+                                 // [7] n_active [8] error flag
+    double *partG;               // per G item: slope partial
+    double *partT;               // per T item: REG_MAX_TRIALS x 4 partial sums
+    unsigned long long *work;    // per kernel family: nodes processed
+    double *trace;               // optional Armijo trial records (7 doubles each)
+    unsigned long long *trace_len;
+    long long trace_cap;
+    double lambda, sigma, tau_init, tau_max, tau_min, eps;
+    int iter_max, J, bf16, pad;
+};
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Compensated ("double-float") displacement arithmetic.  The accepted steps of
+// a level shrink to ~1e-6 grid units while |u| is several units: one float
+// cannot take such a step without rounding it by percents, so u is kept as an
+// unevaluated sum hi + lo of two floats and updated with an exact two-sum.
+// (explicitly rounded adds: the compiler must not contract them into FMAs)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi + lo) + v, renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void df_add(float &hi, float &lo, float v)
+{
+    float s, e;
+    two_sum(hi, v, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ float4 df_add2(float4 u, float vx, float vy)
+{
+    df_add(u.x, u.z, vx);
+    df_add(u.y, u.w, vy);
+    return u;
+}
+
+// Integer part and fraction of hi + lo.  The fraction is rounded to float, the
+// integer part is exact: hi - floor(hi) is exact and is either 0 or at least
+// ulp(hi) > |lo|, so hi + lo lies below floor(hi) only when that fraction is 0
+// and lo < 0.
+__device__ __forceinline__ void df_split(float hi, float lo, int &ip, float &fr)
+{
+    float f = floorf(hi);
+    float a = (hi - f) + lo;
+    if (a < 0.f) {
+        f -= 1.f;
+        a += 1.f;
+    }
+    ip = (int)f;
+    fr = a;
+}

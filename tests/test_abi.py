@@ -1,0 +1,77 @@
+"""Host-side checks of the C-ABI library (no GPU compute): it loads, exports
+every function include/reg.h declares, and its scan schedules are the
+oracle's, op for op."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from oracle import schedules as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as reg
+    return reg
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(reg_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert {"reg_create_series", "reg_apply_operator_batch", "reg_prefix_scan", "reg_get_deformations"} <= declared
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared if not hasattr(so, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (reg_\w+)", out))
+    assert declared <= exported
+
+
+def test_status_strings_and_defaults(lib):
+    so = lib._load()
+    assert so.reg_status_string(0) == b"ok"
+    assert b"invalid" in so.reg_status_string(1)
+    p = lib.default_params()
+    assert p.n_levels == 3 and p.iter_max == 50 and p.armijo_sigma == 0.5 and p.trials_per_pass == 4
+
+
+def _norm(levels):
+    return [sorted(lv) for lv in levels if lv]
+
+
+@pytest.mark.parametrize("kind", [S.SERIAL, S.SKLANSKY, S.KOGGE_STONE, S.BRENT_KUNG, S.BLELLOCH])
+def test_schedules_match_oracle(lib, kind):
+    for n in list(range(1, 70)) + [127, 399]:
+        got, aux = lib.schedule(kind, n)
+        assert _norm(got) == _norm(S.schedule(kind, n)), (kind, n)
+        assert aux == S.aux_slots(kind, n)
+
+
+@pytest.mark.parametrize("kind", [S.CHUNKED, S.CHUNKED_ALT])
+@pytest.mark.parametrize("gkind", [S.SERIAL, S.SKLANSKY, S.KOGGE_STONE, S.BRENT_KUNG, S.BLELLOCH])
+def test_chunked_schedules_match_oracle(lib, kind, gkind):
+    for n in [1, 2, 5, 16, 33, 100, 399]:
+        for p in [1, 2, 3, 8, 16, 64]:
+            got, aux = lib.schedule(kind, n, p, gkind)
+            assert _norm(got) == _norm(S.schedule(kind, n, p, gkind)), (kind, gkind, n, p)
+            assert aux == S.aux_slots(kind, n, p, gkind)
+
+
+def test_invalid_schedule_kind_is_rejected(lib):
+    with pytest.raises(lib.RegError):
+        lib.schedule(42, 8)

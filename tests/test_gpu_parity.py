@@ -1,0 +1,146 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances (FP32 kernels against the FP64 oracle): single energy evaluations
+to 1e-5 relative, gradient-flow directions to 1e-4 of their maximum, and
+registered displacements to 1e-3 px with final energies to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_PX = 1e-3
+TOL_E = 1e-5
+
+
+@pytest.fixture(scope="module")
+def reg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as r
+    return r
+
+
+def _pyramid(orc, frame, nl):
+    g = [orc.embed(frame)]
+    for _ in range(nl - 1):
+        g.append(orc.restrict(g[-1]))
+    return g[::-1]  # coarsest first
+
+
+def _rand_u(n, seed, amp):
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0, 1, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u = np.stack([amp * np.sin(2 * np.pi * (X + 0.3 * Y) + 0.4), amp * np.cos(2 * np.pi * (0.7 * X - Y))])
+    return u + rng.uniform(-0.2, 0.2, size=u.shape)
+
+
+@pytest.mark.parametrize("side,nl", [(64, 3), (128, 3), (256, 2)])
+def test_energy_matches_oracle(reg, orc, syn, side, nl):
+    fr = syn.series(3, 2, side, peak=10.0, spacing=10.0, sigma=2.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, lam=lam)
+    Rp, Tp = _pyramid(orc, fr[0], nl), _pyramid(orc, fr[1], nl)
+    L = int(np.log2(side))
+    with reg.Series(fr, p) as s:
+        for k in range(nl):
+            n = Rp[k].shape[0]
+            level = L - nl + 1 + k
+            for seed, amp in [(0, 0.0), (1, 1.3), (2, 4.0)]:
+                ug = _rand_u(n, seed, amp).astype(np.float32)
+                got = s.eval_energy(0, 1, level, ug)
+                E, parts = orc.energy(Rp[k], Tp[k], ug.astype(np.float64) / (n - 1), lam)
+                # relative to the size of the two terms: E itself can cancel to ~0
+                scale = abs(parts["ncc"]) + abs(parts["reg"])
+                assert abs(got["E"] - E) <= TOL_E * scale, (level, seed, got, E)
+                assert abs(got["ncc"] - parts["ncc"]) <= TOL_E * abs(parts["ncc"])
+                assert abs(got["reg"] - parts["reg"]) <= 1e-5 * max(abs(parts["reg"]), 1e-6)
+
+
+@pytest.mark.parametrize("side,nl", [(64, 3), (128, 2)])
+def test_direction_matches_oracle(reg, orc, syn, side, nl):
+    fr = syn.series(4, 2, side, peak=10.0, spacing=10.0, sigma=2.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, lam=lam)
+    Rp, Tp = _pyramid(orc, fr[0], nl), _pyramid(orc, fr[1], nl)
+    L = int(np.log2(side))
+    with reg.Series(fr, p) as s:
+        for k in range(nl):
+            n = Rp[k].shape[0]
+            h = 1.0 / (n - 1)
+            level = L - nl + 1 + k
+            for seed, amp in [(0, 0.5), (3, 2.5)]:
+                ug = _rand_u(n, seed, amp).astype(np.float32)
+                d, slope = s.eval_direction(0, 1, level, ug)
+                uo = ug.astype(np.float64) * h
+                g = orc.gradient(Rp[k], Tp[k], uo, lam)
+                w = orc.lumped(n)
+                dd = -g / w
+                want = dd / h
+                assert np.max(np.abs(d - want)) <= 1e-4 * np.max(np.abs(want)), (level, seed)
+                want_slope = float(np.sum(g * dd))
+                assert abs(slope - want_slope) <= 1e-5 * abs(want_slope), (slope, want_slope)
+
+
+def test_function_a_matches_oracle(reg, orc, syn):
+    side, nl = 64, 3
+    fr = syn.series(5, 2, side, peak=20.0, spacing=8.0, sigma=1.5, drift_sd=0.7)
+    p = reg.default_params(n_levels=nl, iter_max=30, lam=10.0)
+    with reg.Series(fr, p) as s:
+        st, it = s.apply_operator_batch([(0, -1, -1, 0, 0, 1)])
+        got, se = s.get_slot(0)
+        assert se == (0, 1)
+        eg = s.eval_energy(0, 1, int(np.log2(side)), got)
+    op = orc.params(n_levels=nl, iter_max=30, lam=10.0)
+    u, status, stl = orc.register(orc.embed(fr[0]), orc.embed(fr[1]), op)
+    want = u * side
+    assert int(st[0]) == status
+    assert int(it[0]) == sum(x.iters for x in stl)
+    assert np.max(np.abs(got - want)) <= TOL_PX
+    assert abs(eg["E"] - stl[-1].E) <= TOL_E * abs(stl[-1].E)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+def test_series_config1_matches_oracle(reg, orc, syn, kind):
+    cfg = dict(syn.CONFIGS["c1_8x64"])
+    nl = cfg.pop("n_levels")
+    fr = syn.series(**cfg)
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
+    with reg.Series(fr, p) as s:
+        rep = s.prefix_scan(kind)
+        got = s.get_deformations()
+    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    want, info = orc.register_series([fr], op, kind=kind, return_info=True)
+    want = want[0][:, :, :64, :64]
+    assert rep["ops"] == info["ops"]
+    err = np.abs(got - want)
+    worst = np.unravel_index(np.argmax(err), err.shape)
+    assert err.max() <= TOL_PX, (err.max(), worst, [float(err[k].max()) for k in range(len(err))])
+
+
+def test_identical_frames_give_zero_displacement(reg, syn):
+    f = syn.series(9, 1, 64)
+    fr = np.concatenate([f, f, f])
+    with reg.Series(fr, reg.default_params(n_levels=3, lam=10.0)) as s:
+        s.prefix_scan(reg.SERIAL)
+        d = s.get_deformations()
+    assert np.abs(d).max() < 1e-6
+
+
+def test_invalid_arguments_are_rejected(reg, syn):
+    fr = syn.series(9, 3, 64)
+    with reg.Series(fr, reg.default_params(n_levels=3)) as s:
+        with pytest.raises(reg.RegError) as e:
+            s.apply_operator_batch([(0, 0, -1, 1, 0, 1)])  # slot 0 holds nothing yet
+        assert e.value.code == reg.EINVAL
+        s.apply_operator_batch([(0, -1, -1, 0, 0, 1), (0, -1, -1, 1, 1, 2)])
+        with pytest.raises(reg.RegError):
+            s.apply_operator_batch([(0, 1, 0, 2, 0, 2)])  # chain mismatch: phi_12 then phi_01
+        with pytest.raises(reg.RegError):
+            s.apply_operator_batch([(0, -1, -1, 99, 0, 1)])
+    with pytest.raises(reg.RegError):
+        reg.Series(syn.series(9, 3, 48), reg.default_params(n_levels=2))  # not a power of two
