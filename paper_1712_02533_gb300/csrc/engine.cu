@@ -30,6 +30,7 @@ __global__ void k_prolong(BatchDev);
 void launch_grad(int bf16, int grid, cudaStream_t st, const BatchDev &b);
 void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b);
 int trial_blocks_per_sm(int J);
+int step_blocks_per_sm(int which, int J);
 __global__ void k_control(BatchDev);
 __global__ void k_slot_to_planes(const float2 *, int, int, float *);
 __global__ void k_planes_to_slot(const float *, int, float2 *, int);
@@ -109,7 +110,7 @@ struct reg_series {
     reg_params p{};
     int bf16 = 0;
     int nsm = 0;
-    int grid_work = 0;
+    int grid_P = 0, grid_G = 0, grid_T = 0;  // resident-block grids of the step kernels
     std::vector<SeriesInfo> S;
     std::vector<void *> allocs;
     // batch buffers
@@ -281,9 +282,9 @@ reg_status build_graph(reg_series *s)
     cudaStream_t cs = s->cap_stream;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < GRAPH_STEPS; k++) {
-        k_prolong<<<s->grid_work, REG_THREADS, 0, cs>>>(b);
-        launch_grad(s->bf16, s->grid_work, cs, b);
-        launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, cs, b);
+        k_prolong<<<s->grid_P, REG_THREADS, 0, cs>>>(b);
+        launch_grad(s->bf16, s->grid_G, cs, b);
+        launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, cs, b);
         k_control<<<std::min(s->cap_ops, 2048), 256, 0, cs>>>(b);
         k_plan<<<1, 1024, 0, cs>>>(b);
     }
@@ -403,11 +404,11 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
             // profiling: the same step kernels launched one by one between events
             for (int k = 0; k < GRAPH_STEPS; k++) {
                 cudaEventRecord(s->ev[k][F_P], s->stream);
-                k_prolong<<<s->grid_work, REG_THREADS, 0, s->stream>>>(b);
+                k_prolong<<<s->grid_P, REG_THREADS, 0, s->stream>>>(b);
                 cudaEventRecord(s->ev[k][F_G], s->stream);
-                launch_grad(s->bf16, s->grid_work, s->stream, b);
+                launch_grad(s->bf16, s->grid_G, s->stream, b);
                 cudaEventRecord(s->ev[k][F_T], s->stream);
-                launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, s->stream, b);
+                launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, s->stream, b);
                 cudaEventRecord(s->ev[k][F_C], s->stream);
                 k_control<<<std::min(s->cap_ops, 2048), 256, 0, s->stream>>>(b);
                 cudaEventRecord(s->ev[k][F_PLAN], s->stream);
@@ -538,8 +539,13 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
     s->p = *p;
     s->bf16 = p->storage == REG_STORAGE_BF16;
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
-    int occ = trial_blocks_per_sm(p->trials_per_pass);
-    s->grid_work = s->nsm * std::max(1, std::min(occ, 8));
+    auto grid_of = [&](int which) {
+        int occ = step_blocks_per_sm(which, p->trials_per_pass);
+        return s->nsm * std::max(1, std::min(occ, 8));
+    };
+    s->grid_P = grid_of(0);
+    s->grid_G = grid_of(1);
+    s->grid_T = grid_of(2);
     CK(cudaMallocHost((void **)&s->h_ctr, sizeof(int) * 16));
     s->ev_ok = true;
     for (int k = 0; k < GRAPH_STEPS && s->ev_ok; k++) {
@@ -809,10 +815,12 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
         snprintf(report, buf_len,
                  "{\"kind\": %d, \"preprocessing_ops\": %zu, \"scan_ops\": %d, \"scan_batches\": %d, "
                  "\"ops\": %lld, \"iters\": %lld, \"trials\": %lld, \"evals\": %lld, \"steps\": %lld, \"ms\": %.3f, "
+                 "\"grids\": [%d, %d, %d], "
                  "\"status\": {\"converged\": %d, \"maxiter\": %d, \"stalled\": %d, \"nonfinite\": %d, \"zero_gradient\": %d}}",
                  (int)kind, pre.size(), scan_ops, batches, (long long)(s->tot_ops - ops0),
                  (long long)(s->tot_iters - it0), (long long)(s->tot_trials - tr0), (long long)(s->tot_evals - ev0),
-                 (long long)(s->tot_steps - st0), ms, counts[0], counts[1], counts[2], counts[3], counts[4]);
+                 (long long)(s->tot_steps - st0), ms, s->grid_P, s->grid_G, s->grid_T, counts[0], counts[1], counts[2],
+                 counts[3], counts[4]);
     }
     return REG_OK;
 }
@@ -976,7 +984,7 @@ static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int leve
     CK(cudaMemcpyAsync(s->d_st, &st, sizeof(OpState), cudaMemcpyHostToDevice, s->stream));
     // START: plan, T, C
     k_plan<<<1, 1024, 0, s->stream>>>(b);
-    launch_trial(s->bf16, s->p.trials_per_pass, s->grid_work, s->stream, b);
+    launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, s->stream, b);
     k_control<<<1, 256, 0, s->stream>>>(b);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
@@ -1018,7 +1026,7 @@ reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, i
     BatchDev b = make_batch(s);
     // state is now PH_GRAD with src = 0, cur = 1 (no pending step)
     k_plan<<<1, 1024, 0, s->stream>>>(b);
-    launch_grad(s->bf16, s->grid_work, s->stream, b);
+    launch_grad(s->bf16, s->grid_G, s->stream, b);
     CK(cudaGetLastError());
     OpState st;
     CK(cudaMemcpyAsync(&st, s->d_st, sizeof(OpState), cudaMemcpyDeviceToHost, s->stream));

@@ -464,7 +464,7 @@ __device__ __forceinline__ void block_range(int items, int &b0, int &b1)
 // P: apply the pending step and prolongate to the next level (or write the
 // finest-level result into the destination slot).  Tile: 32 x 32 fine nodes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(REG_THREADS) k_prolong(BatchDev b)
+__global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
 {
     int nent = b.ctr[1], items = b.ctr[4];
     int b0, b1;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(REG_THREADS) k_prolong(BatchDev b)
 // Tile: 32 x 32 nodes plus a one-node halo staged in shared memory.
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(REG_THREADS) k_grad(BatchDev b)
+__global__ void __launch_bounds__(REG_THREADS, 4) k_grad(BatchDev b)
 {
     constexpr int HX = REG_TX + 2, HY = REG_TY + 2, HN = HX * HY;
     __shared__ float4 su[HN];
@@ -561,10 +561,11 @@ __global__ void __launch_bounds__(REG_THREADS) k_grad(BatchDev b)
         const float Tbar = (float)s.Tbar;
         const float isig = (float)(1.0 / s.sigT), ncc = (float)s.ncc, lam = (float)b.lambda;
         __syncthreads();
+        // staging pass 1: the tile's own data (independent loads)
         for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
             int r = r0 - 1 + p / HX, c = c0 - 1 + p % HX;
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            float tv = 0.f, rv = 0.f, gx = 0.f, gy = 0.f;
+            float rv = 0.f;
             if (r >= 0 && r < n && c >= 0 && c < n) {
                 int64_t idx = (int64_t)r * pitch + c;
                 u = Us[idx];
@@ -572,10 +573,18 @@ __global__ void __launch_bounds__(REG_THREADS) k_grad(BatchDev b)
                     float2 d = Ds[idx];
                     u = df_add2(u, tau * d.x, tau * d.y);
                 }
-                tv = sample_df<BF16, true>(Lv.T, n, pitch, c, r, u, &gx, &gy) - Tbar;
                 rv = ldimg<BF16>(Lv.R, (int)idx);
             }
-            su[p] = u; sT[p] = tv; sR[p] = rv; sgx[p] = gx; sgy[p] = gy;
+            su[p] = u; sR[p] = rv;
+        }
+        __syncthreads();
+        // staging pass 2: the warped template and its derivative (gathers)
+        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
+            int r = r0 - 1 + p / HX, c = c0 - 1 + p % HX;
+            float tv = 0.f, gx = 0.f, gy = 0.f;
+            if (r >= 0 && r < n && c >= 0 && c < n)
+                tv = sample_df<BF16, true>(Lv.T, n, pitch, c, r, su[p], &gx, &gy) - Tbar;
+            sT[p] = tv; sgx[p] = gx; sgy[p] = gy;
         }
         __syncthreads();
         float contrib = 0.f;
@@ -738,7 +747,7 @@ constexpr int trial_smem_bytes()
 }
 
 template <bool BF16, int JM>
-__global__ void __launch_bounds__(REG_THREADS) k_trial(BatchDev b)
+__global__ void __launch_bounds__(REG_THREADS, 4) k_trial(BatchDev b)
 {
     constexpr int HX = REG_TX + 1, HY = REG_TY + 1, HN = HX * HY;
     constexpr int NACC = 3 * JM + 3;
@@ -771,16 +780,28 @@ __global__ void __launch_bounds__(REG_THREADS) k_trial(BatchDev b)
         const float4 *U = Lv.U[s.cur];
         const float2 *D = Lv.D[s.cur];
         __syncthreads();
+        // staging pass 1: the tile's own data (independent loads)
         for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
             int r = r0 + p / HX, c = c0 + p % HX;
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 d = make_float2(0.f, 0.f);
-            float rv = 0.f, t0 = 0.f;
+            float rv = 0.f;
             if (r < n && c < n) {
                 int64_t idx = (int64_t)r * pitch + c;
                 u = U[idx];
                 if (!start) d = D[idx];
                 rv = ldimg<BF16>(Lv.R, (int)idx);
+            }
+            su[p] = u; sd[p] = d; sR[p] = rv;
+        }
+        __syncthreads();
+        // staging pass 2: warped template at u and its changes for every step
+        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
+            int r = r0 + p / HX, c = c0 + p % HX;
+            float t0 = 0.f;
+            if (r < n && c < n) {
+                const float4 u = su[p];
+                const float2 d = sd[p];
                 Texel4 q;
                 locate_df(n, c, r, u, q.jx, q.jy, q.ax, q.ay, q.clx, q.cly);
                 fetch<BF16>(q, Lv.T, pitch);
@@ -794,14 +815,22 @@ __global__ void __launch_bounds__(REG_THREADS) k_trial(BatchDev b)
                         if (!(q.clx | q.cly) && ax1 >= 0.f && ax1 < 1.f && ay1 >= 0.f && ay1 < 1.f) {
                             del = ex * ((1.f - ay1) * (q.t01 - q.t00) + ay1 * (q.t11 - q.t10)) +
                                   ey * ((1.f - q.ax) * (q.t10 - q.t00) + q.ax * (q.t11 - q.t01));
-                        } else {
+                        } else if (fabsf(ex) < 0x1p-10f && fabsf(ey) < 0x1p-10f) {
+                            // a tiny move across a cell line or at a clamp: double precision
                             del = cross_delta<BF16>(Lv.T, n, pitch, c, r, u, tau[j], d.x, d.y);
+                        } else {
+                            // a move of at least 2^-10 grid units: a fresh float sample;
+                            // its rounding (~1e-7 of That) is small against delta
+                            Texel4 w;
+                            locate(n, c, r, (u.x + u.z) + ex, (u.y + u.w) + ey, w.jx, w.jy, w.ax, w.ay, w.clx, w.cly);
+                            fetch<BF16>(w, Lv.T, pitch);
+                            del = bil(w) - t0;
                         }
                         sDel[j * HN + p] = del;
                     }
                 }
             }
-            su[p] = u; sd[p] = d; sR[p] = rv; sT0[p] = t0;
+            sT0[p] = t0;
         }
         __syncthreads();
         float acc[NACC];
@@ -1179,12 +1208,53 @@ void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b)
     else launch_trial_j<8>(bf16, grid, st, b);
 }
 
+int trial_blocks_per_sm(int J);
+
+// Resident blocks per SM of the step kernels (shared-memory carveout set to
+// the maximum first, so that the occupancy reflects what a launch gets).
+int step_blocks_per_sm(int which, int J)
+{
+    int occ = 0;
+    if (which == 0) {
+        cudaFuncSetAttribute(k_prolong, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prolong, REG_THREADS, 0);
+    } else if (which == 1) {
+        cudaFuncSetAttribute(k_grad<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_grad<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_grad<false>, REG_THREADS, 0);
+    } else {
+        cudaFuncSetAttribute(k_trial<false, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<false, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<true, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<true, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<true, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_trial<true, 8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        // the dynamic shared memory exceeds the 48 KB default: opt in before sizing
+        cudaFuncSetAttribute(k_trial<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<1>());
+        cudaFuncSetAttribute(k_trial<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<2>());
+        cudaFuncSetAttribute(k_trial<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<4>());
+        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
+        cudaFuncSetAttribute(k_trial<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<1>());
+        cudaFuncSetAttribute(k_trial<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<2>());
+        cudaFuncSetAttribute(k_trial<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<4>());
+        cudaFuncSetAttribute(k_trial<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
+        occ = trial_blocks_per_sm(J);
+    }
+    cudaGetLastError();
+    return occ;
+}
+
 int trial_blocks_per_sm(int J)
 {
     int occ = 0;
     if (J <= 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 1>, REG_THREADS, trial_smem_bytes<1>());
     else if (J <= 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 2>, REG_THREADS, trial_smem_bytes<2>());
     else if (J <= 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 4>, REG_THREADS, trial_smem_bytes<4>());
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 8>, REG_THREADS, trial_smem_bytes<8>());
+    else {
+        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 8>, REG_THREADS, trial_smem_bytes<8>());
+    }
     return occ;
 }
