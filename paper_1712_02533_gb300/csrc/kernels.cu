@@ -664,9 +664,9 @@ struct Texel4 {
 __device__ __forceinline__ void locate(int n, int c, int r, float vx, float vy, int &jx, int &jy, float &ax,
                                        float &ay, bool &clx, bool &cly)
 {
-    float fx = floorf(vx), fy = floorf(vy);
-    jx = c + (int)fx;
-    jy = r + (int)fy;
+    float fx, fy;
+    jx = c + floor_i(vx, fx);
+    jy = r + floor_i(vy, fy);
     ax = vx - fx;
     ay = vy - fy;
     clx = cly = false;
@@ -735,6 +735,54 @@ __device__ __noinline__ float cross_delta(const void *img, int n, int pitch, int
     double X0 = c + ((double)u.x + (double)u.z), Y0 = r + ((double)u.y + (double)u.w);
     double X1 = X0 + (double)tau * dx, Y1 = Y0 + (double)tau * dy;
     return (float)(sample_d<BF16>(img, n, pitch, X1, Y1) - sample_d<BF16>(img, n, pitch, X0, Y0));
+}
+
+// Change of the interpolant for a move (ex, ey) of less than one cell from an
+// unclamped base point in cell (jx, jy) at fractions (ax, ay), when the move
+// leaves the cell.  The move is split into its x part (along the row band of
+// the base point) and its y part (at the new column); each part is a sum of
+// segment lengths times the slope of the cell the segment lies in, so float
+// rounding stays relative to the change itself even for moves far below one
+// ulp of the fraction.  Past the grid border the interpolant is constant.
+template <bool BF16>
+__device__ __noinline__ float cross_delta_f32(const void *img, int n, int pitch, int jx, int jy, float ax, float ay,
+                                              float ex, float ey)
+{
+    auto T = [&](int r, int c) { return ldimg<BF16>(img, r * pitch + c); };
+    // slope along x of cell column i in row band jy at fraction ay (grid units)
+    auto sx = [&](int i) {
+        return (1.f - ay) * (T(jy, i + 1) - T(jy, i)) + ay * (T(jy + 1, i + 1) - T(jy + 1, i));
+    };
+    float dx = 0.f, ax1 = ax + ex;
+    int cx = jx;  // cell column of the new x position
+    if (ax1 >= 1.f) {
+        dx = (1.f - ax) * sx(jx);
+        if (jx + 1 <= n - 2) dx += (ex - (1.f - ax)) * sx(jx + 1);  // beyond the border: flat
+        cx = jx + 1 <= n - 2 ? jx + 1 : jx;
+        ax1 = jx + 1 <= n - 2 ? ex - (1.f - ax) : 1.f;
+    } else if (ax1 < 0.f) {
+        dx = -ax * sx(jx);
+        if (jx - 1 >= 0) dx += (ex + ax) * sx(jx - 1);
+        cx = jx - 1 >= 0 ? jx - 1 : jx;
+        ax1 = jx - 1 >= 0 ? 1.f + (ex + ax) : 0.f;
+    } else {
+        dx = ex * sx(jx);
+    }
+    // slope along y of cell row j at column cell cx and fraction ax1
+    auto sy = [&](int j) {
+        return (1.f - ax1) * (T(j + 1, cx) - T(j, cx)) + ax1 * (T(j + 1, cx + 1) - T(j, cx + 1));
+    };
+    float dy = 0.f, ay1 = ay + ey;
+    if (ay1 >= 1.f) {
+        dy = (1.f - ay) * sy(jy);
+        if (jy + 1 <= n - 2) dy += (ey - (1.f - ay)) * sy(jy + 1);
+    } else if (ay1 < 0.f) {
+        dy = -ay * sy(jy);
+        if (jy - 1 >= 0) dy += (ey + ay) * sy(jy - 1);
+    } else {
+        dy = ey * sy(jy);
+    }
+    return dx + dy;
 }
 
 }  // namespace
@@ -816,8 +864,12 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_trial(BatchDev b)
                             del = ex * ((1.f - ay1) * (q.t01 - q.t00) + ay1 * (q.t11 - q.t10)) +
                                   ey * ((1.f - q.ax) * (q.t10 - q.t00) + q.ax * (q.t11 - q.t01));
                         } else if (fabsf(ex) < 0x1p-10f && fabsf(ey) < 0x1p-10f) {
-                            // a tiny move across a cell line or at a clamp: double precision
-                            del = cross_delta<BF16>(Lv.T, n, pitch, c, r, u, tau[j], d.x, d.y);
+                            // a tiny move across a cell line: exact segment split; from a
+                            // clamped base point (outside the grid): double precision
+                            if (!(q.clx | q.cly))
+                                del = cross_delta_f32<BF16>(Lv.T, n, pitch, q.jx, q.jy, q.ax, q.ay, ex, ey);
+                            else
+                                del = cross_delta<BF16>(Lv.T, n, pitch, c, r, u, tau[j], d.x, d.y);
                         } else {
                             // a move of at least 2^-10 grid units: a fresh float sample;
                             // its rounding (~1e-7 of That) is small against delta

@@ -123,18 +123,37 @@ __device__ __forceinline__ float4 df_add2(float4 u, float vx, float vy)
     return u;
 }
 
+// floor(x) as an int and as a float without a float-to-int conversion
+// instruction (conversions run on the narrow double-precision pipe of this
+// GPU): adding 1.5 * 2^23 rounds x to an integer held in the low mantissa
+// bits, one correction step turns round-to-nearest into floor.  |x| < 2^22.
+__device__ __forceinline__ int floor_i(float x, float &fl)
+{
+    const float magic = 12582912.0f;  // 1.5 * 2^23
+    float t = __fadd_rn(x, magic);
+    int i = __float_as_int(t) - 0x4B400000;
+    float r = __fsub_rn(t, magic);
+    if (r > x) {
+        i -= 1;
+        r -= 1.f;
+    }
+    fl = r;
+    return i;
+}
+
 // Integer part and fraction of hi + lo.  The fraction is rounded to float, the
 // integer part is exact: hi - floor(hi) is exact and is either 0 or at least
 // ulp(hi) > |lo|, so hi + lo lies below floor(hi) only when that fraction is 0
 // and lo < 0.
 __device__ __forceinline__ void df_split(float hi, float lo, int &ip, float &fr)
 {
-    float f = floorf(hi);
+    float f;
+    int i = floor_i(hi, f);
     float a = (hi - f) + lo;
     if (a < 0.f) {
-        f -= 1.f;
+        i -= 1;
         a += 1.f;
     }
-    ip = (int)f;
+    ip = i;
     fr = a;
 }
