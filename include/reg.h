@@ -233,6 +233,35 @@ reg_status reg_reset_kernel_stats(reg_series_t s);
 reg_status reg_set_trace(reg_series_t s, int64_t capacity);
 reg_status reg_get_trace(reg_series_t s, double *out, int64_t cap, int64_t *n_out);
 
+/* Energy of one frame pair at one grid level, allocating no memory at all.
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory (for instance a plug-in inside an acquisition
+ * pipeline whose host application reserved the device memory up front, or a
+ * per-frame loop that cannot afford the synchronisation cudaMalloc implies).
+ * It needs no handle.
+ *   R, T      device pointers to the raw reference and template images of the
+ *             level, n x n nodes (the vertex grid), row pitch `pitch` floats;
+ *   u_grid    device pointer, displacement of the level in grid units, two
+ *             planes of n x n floats (columns, then rows), dense;
+ *   lambda    regulariser weight;
+ *   parts_out {E, NCC, regulariser, T_bar, sigma_T} (5 doubles), host memory
+ *             unless out_on_device;
+ *   cuda_stream the stream to run on (NULL: legacy default stream); the call
+ *             returns when the result is in parts_out.
+ * Scratch: a file-scope device array sized for n <= REG_NOALLOC_MAX_NODES
+ * (frames of 2048^2; about 192 KiB), held by every GPU that loads the library
+ * until the process exits.  Its device address is looked up on the first
+ * call on each device, so that first call should come before any stream
+ * capture.  Every call shares the array and leaves its partial sums in it
+ * (each call overwrites all it reads, so no clearing is needed); calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors: REG_EINVAL for a null pointer, n < 3, n > REG_NOALLOC_MAX_NODES or
+ * pitch < n; REG_ECUDA if a CUDA call fails.  Allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine. */
+#define REG_NOALLOC_MAX_NODES 2049
+reg_status reg_eval_energy_noalloc(const float *R, const float *T, int32_t n, int32_t pitch, const float *u_grid,
+                                   double lambda, double *parts_out, int32_t out_on_device, void *cuda_stream);
+
 reg_status reg_destroy_series(reg_series_t s);
 const char *reg_status_string(reg_status st);
 /* Message of the last error on this thread (empty if none). */

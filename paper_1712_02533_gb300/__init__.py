@@ -93,6 +93,7 @@ def _load():
         "reg_reset_kernel_stats": ([vp], ctypes.c_int),
         "reg_set_trace": ([vp, i64], ctypes.c_int),
         "reg_get_trace": ([vp, vp, i64, P(i64)], ctypes.c_int),
+        "reg_eval_energy_noalloc": ([vp, vp, i32, i32, vp, d, vp, i32, vp], ctypes.c_int),
         "reg_destroy_series": ([vp], ctypes.c_int),
         "reg_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "reg_last_error": ([], ctypes.c_char_p),
@@ -293,6 +294,22 @@ def get_trace(h):
     out = np.empty((max(1, n.value), 7))
     _check(_load().reg_get_trace(h, out.ctypes.data, n.value, ctypes.byref(n)))
     return out[:n.value]
+
+
+def eval_energy_noalloc(R, T, u_grid, lam, stream=None):
+    """Energy of one pair at one level through the allocation-free entry point.
+    R, T: CUDA float32 tensors (n, n) of the level's raw images; u_grid: CUDA
+    float32 tensor (2, n, n) in grid units.  Returns the same dict as
+    eval_energy.  The caller owns every buffer; the library allocates none."""
+    torch = _torch()
+    n = int(R.shape[-1])
+    assert R.is_cuda and T.is_cuda and u_grid.is_cuda
+    R, T, u = R.contiguous(), T.contiguous(), u_grid.contiguous()
+    parts = np.empty(5)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_load().reg_eval_energy_noalloc(R.data_ptr(), T.data_ptr(), n, n, u.data_ptr(), lam,
+                                           parts.ctypes.data, 0, ctypes.c_void_p(st.cuda_stream)))
+    return dict(E=parts[0], ncc=parts[1], reg=parts[2], Tbar=parts[3], sigT=parts[4])
 
 
 def destroy_series(h):
