@@ -196,6 +196,16 @@ reg_status reg_eval_energy(reg_series_t s, int32_t series, int32_t frame_i, int3
 reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
                               const float *u_grid, float *d_out, double *slope);
 
+/* Diagnostic trial pass: at a displacement u (as for reg_eval_energy) one
+ * gradient pass computes the direction d, then one trial pass evaluates the
+ * energy change E(u + tau_j d) - E(u) of the Armijo search for the n_tau step
+ * sizes taus[0..n_tau-1] (1 <= n_tau <= trials_per_pass), written to
+ * dE_out[j] exactly as the operator state machine forms it (Section
+ * "Optimization": gradient flow with a backtracking line search).  d_out
+ * (2 x n x n, may be NULL) receives d.  Host buffers; returns when done. */
+reg_status reg_eval_trials(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                           const float *u_grid, int32_t n_tau, const double *taus, float *d_out, double *dE_out);
+
 /* Schedule export (host only, no GPU work): writes the op list of a schedule
  * over n elements as reg_schedule_op records (level index, kind, slots) into
  * buf (up to buf_len records), the total count into *n_out (call with buf NULL

@@ -88,6 +88,7 @@ def _load():
         "reg_num_slots": ([vp, i32, P(i32)], ctypes.c_int),
         "reg_eval_energy": ([vp, i32, i32, i32, i32, vp, vp], ctypes.c_int),
         "reg_eval_direction": ([vp, i32, i32, i32, i32, vp, vp, P(d)], ctypes.c_int),
+        "reg_eval_trials": ([vp, i32, i32, i32, i32, vp, i32, vp, vp, vp], ctypes.c_int),
         "reg_schedule": ([ctypes.c_int, i32, i32, ctypes.c_int, vp, i64, P(i64), P(i32)], ctypes.c_int),
         "reg_get_kernel_stats": ([vp, vp, i32, P(i32)], ctypes.c_int),
         "reg_reset_kernel_stats": ([vp], ctypes.c_int),
@@ -251,6 +252,18 @@ def eval_direction(h, series, frame_i, frame_k, level, u_grid):
     return d, sl.value
 
 
+def eval_trials(h, series, frame_i, frame_k, level, u_grid, taus):
+    """One gradient pass and one trial pass at u: returns (d, dE) with dE[j] the
+    energy change for step size taus[j] as the Armijo search forms it."""
+    u = np.ascontiguousarray(u_grid, np.float32)
+    t = np.ascontiguousarray(taus, np.float64)
+    d = np.empty_like(u)
+    dE = np.empty(len(t))
+    _check(_load().reg_eval_trials(h, series, frame_i, frame_k, level, u.ctypes.data, len(t), t.ctypes.data,
+                                   d.ctypes.data, dE.ctypes.data))
+    return d, dE
+
+
 def schedule(kind, n, chunks=0, global_kind=KOGGE_STONE):
     """Op list of a scan schedule: list of levels of (kind, dst, a, b); kind
     'op' | 'copy' | 'id' as in the oracle's schedules module."""
@@ -367,6 +380,9 @@ class Series:
 
     def eval_direction(self, frame_i, frame_k, level, u_grid, series=0):
         return eval_direction(self.h, series, frame_i, frame_k, level, u_grid)
+
+    def eval_trials(self, frame_i, frame_k, level, u_grid, taus, series=0):
+        return eval_trials(self.h, series, frame_i, frame_k, level, u_grid, taus)
 
     def set_trace(self, capacity):
         set_trace(self.h, capacity)

@@ -21,6 +21,7 @@ __global__ void k_embed(const float *, int64_t, int64_t, int, float *, int64_t, 
 __global__ void k_restrict_img(const float *, int64_t, int, int, float *, int64_t, int);
 __global__ void k_image_stats(const float *, int64_t, int, int, double *);
 __global__ void k_normalize(const float *, int64_t, int, int, const double *, void *, int64_t, int, int);
+__global__ void k_mass_image(const void *, int64_t, int, int, int, float *, int64_t);
 __global__ void k_compose(BatchDev);
 __global__ void k_restrict_u(BatchDev, int);
 __global__ void k_zero_u(BatchDev);
@@ -29,13 +30,10 @@ __global__ void k_plan(BatchDev);
 __global__ void k_prolong(BatchDev);
 void launch_grad(int bf16, int grid, cudaStream_t st, const BatchDev &b);
 void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b);
-int trial_blocks_per_sm(int J);
 int step_blocks_per_sm(int which, int J);
 __global__ void k_control(BatchDev);
 __global__ void k_slot_to_planes(const float2 *, int, int, float *);
 __global__ void k_planes_to_slot(const float *, int, float2 *, int);
-
-#define PT_STRIDE (3 * REG_MAX_TRIALS + 3)
 
 namespace {
 
@@ -77,13 +75,15 @@ struct SeriesInfo {
     std::vector<size_t> img_off;          // element offset of level k inside a frame's pyramid block
     size_t frame_block = 0;               // elements per frame pyramid
     void *pyr = nullptr;                  // n_frames * frame_block elements (float or bf16)
+    float *mr = nullptr;                  // M~ R~ of every frame and level, same layout (float)
     float2 *slots = nullptr;              // n_slots * slot_elems
     size_t slot_elems = 0;
     std::vector<SlotMeta> meta;
     std::vector<size_t> ws_off;           // per level: offset (bytes) of U0 within an op workspace
     size_t ws_bytes = 0;                  // per op
-    size_t field_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(float2); }
-    size_t ufield_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(float4); }
+    size_t rec_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(NodeRec); }
+    // op workspace of level k: two node-record fields
+    size_t level_ws_bytes(int k) const { return 2 * rec_bytes(k); }
 };
 
 struct FamilyStats {
@@ -228,7 +228,16 @@ BatchDev make_batch(reg_series *s)
     return b;
 }
 
-int node_tiles(int n) { return cdiv(n, REG_TX) * cdiv(n, REG_TY); }
+// Work items per operator at a level of n nodes per side: the largest of the
+// prolongation block tiles and the gradient and trial strip tiles.
+int max_tiles(int n)
+{
+    int p = cdiv(n, REG_TX) * cdiv(n, REG_TY);
+    int h = strip_rows(n);
+    int g = cdiv(n, REG_GW) * cdiv(n, h);
+    int t = cdiv(n - 1, REG_CW) * cdiv(n - 1, h);
+    return std::max(p, std::max(g, t));
+}
 
 reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t items_per_op)
 {
@@ -251,7 +260,7 @@ reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t i
         int64_t c = std::max(items, (int64_t)(1.25 * s->cap_items));
         untrack(s, s->d_partG);
         untrack(s, s->d_partT);
-        RET(track(s, (void **)&s->d_partG, sizeof(double) * c));
+        RET(track(s, (void **)&s->d_partG, sizeof(double) * PG_STRIDE * c));
         RET(track(s, (void **)&s->d_partT, sizeof(double) * PT_STRIDE * c));
         s->cap_items = c;
         changed = true;
@@ -335,7 +344,7 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
     for (auto &o : ops) {
         const SeriesInfo &si = s->S[o.series];
         ws = std::max(ws, si.ws_bytes);
-        items = std::max<int64_t>(items, node_tiles(si.n[si.nl - 1]));
+        items = std::max<int64_t>(items, max_tiles(si.n[si.nl - 1]));
         nl = std::max(nl, si.nl);
         nLmax = std::max(nLmax, si.n[si.nl - 1]);
     }
@@ -361,12 +370,10 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
             L.h2 = (float)L.h2d;
             L.R = img_ptr(s, si, o.frame_i, k);
             L.T = img_ptr(s, si, o.frame_k, k);
-            size_t fb = si.field_bytes(k), ub = si.ufield_bytes(k);
+            L.MR = si.mr + (size_t)o.frame_i * si.frame_block + si.img_off[k];
             char *base = w + si.ws_off[k];
-            L.U[0] = (float4 *)(base);
-            L.U[1] = (float4 *)(base + ub);
-            L.D[0] = (float2 *)(base + 2 * ub);
-            L.D[1] = (float2 *)(base + 2 * ub + fb);
+            L.V[0] = (NodeRec *)base;
+            L.V[1] = (NodeRec *)(base + si.rec_bytes(k));
         }
     }
     CK(cudaMemcpyAsync(s->d_ops, s->h_ops, sizeof(OpDesc) * n, cudaMemcpyHostToDevice, s->stream));
@@ -541,7 +548,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
     auto grid_of = [&](int which) {
         int occ = step_blocks_per_sm(which, p->trials_per_pass);
-        return s->nsm * std::max(1, std::min(occ, 8));
+        return s->nsm * std::max(1, std::min(occ, 32));
     };
     s->grid_P = grid_of(0);
     s->grid_G = grid_of(1);
@@ -589,7 +596,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
             si.img_off.push_back(off);
             off += (size_t)nn * si.pitch.back();
             si.ws_off.push_back(woff);
-            woff += 2 * si.ufield_bytes(k) + 2 * si.field_bytes(k);
+            woff += si.level_ws_bytes(k);
         }
         si.frame_block = round_up((int)std::min<size_t>(off, (size_t)1 << 30), 64);
         si.ws_bytes = woff;
@@ -597,6 +604,8 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         si.meta.assign(si.n_slots, SlotMeta{});
         size_t esz = s->bf16 ? 2 : 4;
         if ((st = track(s, &si.pyr, si.frame_block * si.n_frames * esz)) != REG_OK) return cleanup(st);
+        if ((st = track(s, (void **)&si.mr, si.frame_block * si.n_frames * sizeof(float))) != REG_OK)
+            return cleanup(st);
         if ((st = track(s, (void **)&si.slots, si.slot_elems * si.n_slots * sizeof(float2))) != REG_OK) return cleanup(st);
         s->S.push_back(si);
     }
@@ -641,6 +650,9 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
                 k_normalize<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
                     rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k], si.n[k], (const double *)stats,
                     dst, (int64_t)si.frame_block, si.pitch[k], s->bf16);
+                k_mass_image<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+                    dst, (int64_t)si.frame_block, si.pitch[k], si.n[k], s->bf16,
+                    si.mr + (size_t)f0 * si.frame_block + si.img_off[k], (int64_t)si.frame_block);
             }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid kernels: %s", cudaGetErrorString(e)));
@@ -940,7 +952,7 @@ static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int leve
     if (k < 0 || k >= si.nl) return fail(REG_EINVAL, "level outside the pyramid");
     if (!u_grid) return fail(REG_EINVAL, "null displacement");
     std::vector<OpReq> one{OpReq{series, fi, fk, 0, -1, -1, 0}};
-    RET(ensure_capacity(s, 1, si.ws_bytes, node_tiles(si.n[si.nl - 1])));
+    RET(ensure_capacity(s, 1, si.ws_bytes, max_tiles(si.n[si.nl - 1])));
     OpDesc &d = s->h_ops[0];
     memset(&d, 0, sizeof(d));
     d.nl = si.nl;
@@ -955,22 +967,22 @@ static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int leve
         L.h2 = (float)L.h2d;
         L.R = img_ptr(s, si, fi, q);
         L.T = img_ptr(s, si, fk, q);
-        size_t fb = si.field_bytes(q), ub = si.ufield_bytes(q);
+        L.MR = si.mr + (size_t)fi * si.frame_block + si.img_off[q];
         char *base = s->d_ws + si.ws_off[q];
-        L.U[0] = (float4 *)base;
-        L.U[1] = (float4 *)(base + ub);
-        L.D[0] = (float2 *)(base + 2 * ub);
-        L.D[1] = (float2 *)(base + 2 * ub + fb);
+        L.V[0] = (NodeRec *)base;
+        L.V[1] = (NodeRec *)(base + si.rec_bytes(q));
     }
     CK(cudaMemcpyAsync(s->d_ops, s->h_ops, sizeof(OpDesc), cudaMemcpyHostToDevice, s->stream));
     // u planes (2 x n x n) -> float2 field U0 of level k
     int n = si.n[k];
-    std::vector<float4> tmp((size_t)n * si.pitch[k], make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<NodeRec> tmp((size_t)n * si.pitch[k]);
+    memset(tmp.data(), 0, tmp.size() * sizeof(NodeRec));
     for (int r = 0; r < n; r++)
         for (int c = 0; c < n; c++)
-            tmp[(size_t)r * si.pitch[k] + c] =
+            tmp[(size_t)r * si.pitch[k] + c].u =
                 make_float4(u_grid[(size_t)r * n + c], u_grid[(size_t)n * n + (size_t)r * n + c], 0.f, 0.f);
-    CK(cudaMemcpyAsync(d.lv[k].U[0], tmp.data(), tmp.size() * sizeof(float4), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(d.lv[k].V[0], tmp.data(), tmp.size() * sizeof(NodeRec), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));  // tmp is pageable and goes out of scope
     s->h_ctr[0] = 1;
     for (int q = 1; q < 16; q++) s->h_ctr[q] = 0;
     CK(cudaMemcpyAsync(s->d_ctr, s->h_ctr, sizeof(int) * 16, cudaMemcpyHostToDevice, s->stream));
@@ -1009,10 +1021,10 @@ reg_status reg_eval_energy(reg_series_t s, int32_t series, int32_t frame_i, int3
     return REG_OK;
 }
 
-__global__ void k_sum_range(const double *v, int b, int e, double *out)
+__global__ void k_sum_range(const double *v, int stride, int b, int e, double *out)
 {
     double s = 0.0;
-    for (int i = b + threadIdx.x; i < e; i += 32) s += v[i];
+    for (int i = b + threadIdx.x; i < e; i += 32) s += v[(int64_t)i * stride];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) *out = s;
 }
@@ -1033,23 +1045,80 @@ reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, i
     CK(cudaStreamSynchronize(s->stream));
     if (st.phase != PH_GRAD) return fail(REG_ESTATE, "energy at the given displacement is not finite");
     if (!s->d_scratch) RET(track(s, (void **)&s->d_scratch, sizeof(double) * 16));
-    k_sum_range<<<1, 32, 0, s->stream>>>(s->d_partG, st.g_begin, st.g_end, s->d_scratch);
+    k_sum_range<<<1, 32, 0, s->stream>>>(s->d_partG, PG_STRIDE, st.g_begin, st.g_end, s->d_scratch);
     double sl = 0.0;
     CK(cudaMemcpyAsync(&sl, s->d_scratch, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     const SeriesInfo &si = s->S[series];
     int n = si.n[k];
-    std::vector<float2> tmp((size_t)n * si.pitch[k]);
+    std::vector<NodeRec> tmp((size_t)n * si.pitch[k]);
     OpDesc d;
     CK(cudaMemcpyAsync(&d, s->d_ops, sizeof(OpDesc), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    CK(cudaMemcpy(tmp.data(), d.lv[k].D[st.cur], tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tmp.data(), d.lv[k].V[st.cur], tmp.size() * sizeof(NodeRec), cudaMemcpyDeviceToHost));
     if (slope) *slope = sl;
     if (d_out)
         for (int r = 0; r < n; r++)
             for (int c = 0; c < n; c++) {
-                d_out[(size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].x;
-                d_out[(size_t)n * n + (size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].y;
+                d_out[(size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].d.x;
+                d_out[(size_t)n * n + (size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].d.y;
             }
+    return REG_OK;
+}
+
+reg_status reg_eval_trials(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
+                           const float *u_grid, int32_t n_tau, const double *taus, float *d_out, double *dE_out)
+{
+    g_err.clear();
+    if (!s || !taus || !dE_out) return fail(REG_EINVAL, "bad argument");
+    if (n_tau < 1 || n_tau > s->p.trials_per_pass)
+        return fail(REG_EINVAL, "n_tau must be in [1, trials_per_pass = %d]", s->p.trials_per_pass);
+    int k;
+    RET(diag_setup(s, series, frame_i, frame_k, level, u_grid, k));
+    BatchDev b = make_batch(s);
+    // gradient pass at u (state PH_GRAD, no pending step), then one trial pass
+    // over the given step sizes (still PH_GRAD, so that it also forms d^T K d)
+    k_plan<<<1, 1024, 0, s->stream>>>(b);
+    launch_grad(s->bf16, s->grid_G, s->stream, b);
+    CK(cudaGetLastError());
+    OpState st;
+    CK(cudaMemcpyAsync(&st, s->d_st, sizeof(OpState), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (st.phase != PH_GRAD) return fail(REG_ESTATE, "energy at the given displacement is not finite");
+    st.ntr = n_tau;
+    for (int j = 0; j < REG_MAX_TRIALS; j++) st.trial_tau[j] = j < n_tau ? taus[j] : 0.0;
+    CK(cudaMemcpyAsync(s->d_st, &st, sizeof(OpState), cudaMemcpyHostToDevice, s->stream));
+    launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, s->stream, b);
+    CK(cudaGetLastError());
+    std::vector<double> pt((size_t)(st.t_end - st.t_begin) * PT_STRIDE), pg((size_t)(st.g_end - st.g_begin) * PG_STRIDE);
+    CK(cudaMemcpyAsync(pt.data(), s->d_partT + (size_t)st.t_begin * PT_STRIDE, pt.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(pg.data(), s->d_partG + (size_t)st.g_begin * PG_STRIDE, pg.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    double S[PT_STRIDE] = {0.0}, qud = 0.0;
+    for (size_t i = 0; i < pt.size(); i++) S[i % PT_STRIDE] += pt[i];
+    for (size_t i = 1; i < pg.size(); i += PG_STRIDE) qud += pg[i];
+    // the energy change of each step size, as the operator state machine forms it
+    const SeriesInfo &si = s->S[series];
+    const double hh = 1.0 / (si.n[k] - 1), h2 = hh * hh, qdd = S[3 * REG_MAX_TRIALS + 2];
+    for (int j = 0; j < n_tau; j++) {
+        double S1 = st.S1 + h2 * S[3 * j], S2 = st.S2 + h2 * S[3 * j + 1], S3 = st.S3 + h2 * S[3 * j + 2];
+        double var = S2 - S1 * S1;
+        double nc = S3 / (var > 0.0 ? std::sqrt(var) : 0.0);
+        dE_out[j] = -(nc - st.ncc) + 0.5 * s->p.lambda * h2 * (2.0 * taus[j] * qud + taus[j] * taus[j] * qdd);
+    }
+    if (d_out) {
+        int n = si.n[k];
+        std::vector<NodeRec> tmp((size_t)n * si.pitch[k]);
+        OpDesc d;
+        CK(cudaMemcpy(&d, s->d_ops, sizeof(OpDesc), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tmp.data(), d.lv[k].V[st.cur], tmp.size() * sizeof(NodeRec), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < n; r++)
+            for (int c = 0; c < n; c++) {
+                d_out[(size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].d.x;
+                d_out[(size_t)n * n + (size_t)r * n + c] = tmp[(size_t)r * si.pitch[k] + c].d.y;
+            }
+    }
     return REG_OK;
 }
 
@@ -1089,10 +1158,12 @@ reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t b
         // per node: u 16 B (float pair per component), d 8 B, R and T one image value each
         if (f == F_G) {
             k.items = (int64_t)w[KW_G];
-            k.bytes = w[KW_G] * (16.0 + 8.0 + 2 * img + 16.0 + 8.0);
+            // reads u, d, M~R~, the template; writes u, d, M~That
+            k.bytes = w[KW_G] * (16.0 + 8.0 + 4.0 + img + 16.0 + 8.0 + 4.0);
         } else if (f == F_T) {
             k.items = (int64_t)(w[KW_T] + w[KW_TSTART]);
-            k.bytes = w[KW_T] * (16.0 + 8.0 + 2 * img) + w[KW_TSTART] * (16.0 + 2 * img);
+            // trial: reads u, d, M~That, M~R~, the template; start: u, M~R~, the template
+            k.bytes = w[KW_T] * (16.0 + 8.0 + 4.0 + 4.0 + img) + w[KW_TSTART] * (16.0 + 4.0 + img);
         } else if (f == F_P) {
             k.items = (int64_t)(w[KW_PPROL] + w[KW_PFIN]);
             k.bytes = w[KW_PPROL] * (16.0 + 6.0) + w[KW_PFIN] * (16.0 + 8.0 + 8.0);

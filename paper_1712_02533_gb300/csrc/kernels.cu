@@ -127,19 +127,13 @@ __device__ __forceinline__ float2 sample2(const float2 *f, int n, int pitch, int
     return o;
 }
 
-// 1D FE weights at node i for neighbour offset a in {-1,0,1}: mass (times 6/h)
-// and stiffness (times h) of piecewise-linear hats with natural boundary.
+// 1D FE mass weight (in units of h) at node i for neighbour offset a in {-1,0,1}
+// of piecewise-linear hats with natural boundary.
 __device__ __forceinline__ float m1w(int i, int a, int n)
 {
     if (a == 0) return (i == 0 || i == n - 1) ? (2.f / 6.f) : (4.f / 6.f);
     int j = i + a;
     return (j >= 0 && j < n) ? (1.f / 6.f) : 0.f;
-}
-__device__ __forceinline__ float k1w(int i, int a, int n)
-{
-    if (a == 0) return (i == 0 || i == n - 1) ? 1.f : 2.f;
-    int j = i + a;
-    return (j >= 0 && j < n) ? -1.f : 0.f;
 }
 
 __device__ __forceinline__ int find_entry(const int *pref, int nent, int item)
@@ -260,6 +254,35 @@ __global__ void k_normalize(const float *__restrict__ img, int64_t stride, int p
     else reinterpret_cast<float *>(out)[o] = v;
 }
 
+// M~ R~ of normalised frames at one level: the FE mass matrix in units of h^2,
+// M1 (x) M1 with the 1D weights 1/6, 4/6, 1/6 (2/6 on the diagonal at the
+// border), applied to the stored (float or bf16) image.  The weights are taken
+// as the integers 36 M~ and the sum is divided by 36 once, so that no rounded
+// weight biases every node the same way.  The gradient and trial passes take
+// the NCC terms int R~ phi_i from it.
+__global__ void k_mass_image(const void *img, int64_t stride, int pitch, int n, int bf16, float *out,
+                             int64_t ostride)
+{
+    int z = blockIdx.z;
+    int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= n || c >= n) return;
+    const void *f = bf16 ? (const void *)(reinterpret_cast<const __nv_bfloat16 *>(img) + z * stride)
+                         : (const void *)(reinterpret_cast<const float *>(img) + z * stride);
+    auto w6 = [n](int i, int a) { return a == 0 ? ((i == 0 || i == n - 1) ? 2.f : 4.f) : 1.f; };
+    float acc = 0.f;
+    for (int a = -1; a <= 1; a++) {
+        if (r + a < 0 || r + a >= n) continue;
+        float row = 0.f;
+        for (int bb = -1; bb <= 1; bb++) {
+            if (c + bb < 0 || c + bb >= n) continue;
+            const int i = (r + a) * pitch + (c + bb);
+            row += w6(c, bb) * (bf16 ? ldimg<true>(f, i) : ldimg<false>(f, i));
+        }
+        acc += w6(r, a) * row;
+    }
+    out[z * ostride + (int64_t)r * pitch + c] = acc / 36.f;
+}
+
 // ---------------------------------------------------------------------------
 // Operator initialisation: composition and restriction of the initial guess
 // ---------------------------------------------------------------------------
@@ -279,7 +302,7 @@ __global__ void k_compose(BatchDev b)
         a.x += q.x;
         a.y += q.y;
     }
-    L.U[0][(int64_t)r * L.pitch + c] = make_float4(a.x, a.y, 0.f, 0.f);
+    L.V[0][(int64_t)r * L.pitch + c].u = make_float4(a.x, a.y, 0.f, 0.f);
 }
 
 // Restrict U0 from level index k+1 to k (grid units halve).  grid (x, y, ops).
@@ -302,13 +325,13 @@ __global__ void k_restrict_u(BatchDev b, int step)
         for (int bb = -1; bb <= 1; bb++) {
             int c = 2 * J + bb;
             c = c < 0 ? -c : (c > nf - 1 ? 2 * (nf - 1) - c : c);
-            float4 v = F.U[0][(int64_t)r * F.pitch + c];
+            float4 v = F.V[0][(int64_t)r * F.pitch + c].u;
             float ww = w[a + 1] * w[bb + 1];
             sx += ww * v.x;
             sy += ww * v.y;
         }
     }
-    C.U[0][(int64_t)I * C.pitch + J] = make_float4(0.5f * sx, 0.5f * sy, 0.f, 0.f);
+    C.V[0][(int64_t)I * C.pitch + J].u = make_float4(0.5f * sx, 0.5f * sy, 0.f, 0.f);
 }
 
 // Identity initial guess: zero U0 on the coarsest level.  grid (x, y, ops).
@@ -319,7 +342,7 @@ __global__ void k_zero_u(BatchDev b)
     const LevelDesc &C = op.lv[0];
     int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
     if (r >= C.n || c >= C.n) return;
-    C.U[0][(int64_t)r * C.pitch + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    C.V[0][(int64_t)r * C.pitch + c].u = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void k_init_state(BatchDev b, int n_ops)
@@ -341,8 +364,18 @@ __global__ void k_init_state(BatchDev b, int n_ops)
 // Work planning: compacted per-family op lists and tile prefix sums
 // ---------------------------------------------------------------------------
 
+// work items per operator: prolongation block tiles, gradient and trial strip tiles
 __device__ __forceinline__ int node_tiles(int n) { return ((n + REG_TX - 1) / REG_TX) * ((n + REG_TY - 1) / REG_TY); }
-__device__ __forceinline__ int cell_tiles(int n) { return ((n - 1 + REG_TX - 1) / REG_TX) * ((n - 1 + REG_TY - 1) / REG_TY); }
+__device__ __forceinline__ int grad_tiles(int n)
+{
+    const int h = strip_rows(n);
+    return ((n + REG_GW - 1) / REG_GW) * ((n + h - 1) / h);
+}
+__device__ __forceinline__ int trial_tiles(int n)
+{
+    const int h = strip_rows(n);
+    return ((n - 1 + REG_CW - 1) / REG_CW) * ((n - 1 + h - 1) / h);
+}
 
 // Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
 __device__ int block_excl_scan(int v, int *tmp, int *total)
@@ -389,9 +422,9 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev b)
             int n = op.lv[s.lvl].n;
             if (s.phase != PH_DONE) active++;
             if (s.phase == PH_PROLONG || s.phase == PH_FINAL) { inP = 1; tP = node_tiles(n); }
-            if (s.phase == PH_GRAD) { inG = 1; tG = node_tiles(n); }
+            if (s.phase == PH_GRAD) { inG = 1; tG = grad_tiles(n); }
             if (s.phase == PH_START || s.phase == PH_GRAD || s.phase == PH_TRIAL || s.phase == PH_PROLONG) {
-                inT = 1; tT = cell_tiles(n);
+                inT = 1; tT = trial_tiles(n);
             }
         }
         int tot;
@@ -488,16 +521,16 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
             const int r = r0 + ly + k * REG_ROWSTEP;
             if (r >= n || c >= n) continue;
             if (fin) {
-                float4 u = Lv.U[s.src][(int64_t)r * Lv.pitch + c];
+                const NodeRec &v = Lv.V[s.src][(int64_t)r * Lv.pitch + c];
+                float4 u = v.u;
                 if (tau != 0.f) {
-                    float2 d = Lv.D[s.src][(int64_t)r * Lv.pitch + c];
+                    float2 d = v.d;
                     u = df_add2(u, tau * d.x, tau * d.y);
                 }
                 op.out[(int64_t)r * op.slot_pitch + c] = make_float2(u.x + u.z, u.y + u.w);
             } else {
                 const LevelDesc &Cv = op.lv[s.lvl - 1];
-                const float4 *U = Cv.U[s.src];
-                const float2 *D = Cv.D[s.src];
+                const NodeRec *V = Cv.V[s.src];
                 int I = r >> 1, J = c >> 1, oi = r & 1, oj = c & 1;
                 // 2 x bilinear prolongation (coarse grid unit = 2 fine units); the
                 // weights 2, 1, 1/2 are exact, the sum is compensated
@@ -509,9 +542,9 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
                     for (int bb = 0; bb <= 1; bb++) {
                         if ((a && !oi) || (bb && !oj)) continue;
                         int64_t idx = (int64_t)(I + a) * Cv.pitch + (J + bb);
-                        float4 u = U[idx];
+                        float4 u = V[idx].u;
                         if (tau != 0.f) {
-                            float2 d = D[idx];
+                            float2 d = V[idx].d;
                             u = df_add2(u, tau * d.x, tau * d.y);
                         }
                         df_add(acc.x, acc.z, w2 * u.x);
@@ -519,7 +552,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
                         df_add(acc.y, acc.w, w2 * u.y);
                         df_add(acc.y, acc.w, w2 * u.w);
                     }
-                Lv.U[0][(int64_t)r * Lv.pitch + c] = acc;
+                Lv.V[0][(int64_t)r * Lv.pitch + c].u = acc;
             }
         }
     }
@@ -532,126 +565,125 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
 //   psi_{i,c}    = -[...] dT_c(i) + lambda (K u_c)_i            (dE/du~ = h^2 psi)
 //   d_{i,c}      = -psi_{i,c} / (h^2 omega_i)                  (d = -g / w, w = h^2 omega)
 //   slope        = g^T d = -sum psi^2 / omega
-// Tile: 32 x 32 nodes plus a one-node halo staged in shared memory.
+//   Qud          = u^T K d = sum_i d_i . (K u)_i
+// with M~ = M1 (x) M1 and K = K1 (x) M1 + M1 (x) K1 (1D mass M1 = [1 4 1] / 6,
+// 2/6 on the diagonal at the border; 1D stiffness K1 = [-1 2 -1], 1 on the
+// diagonal at the border), applied as separable stencils with the integer
+// weights 6 M1 and 6 K1: along the column in registers, along the row by
+// shuffles; the scale 1/36 or 1/6 is folded into per-tile coefficients, so that
+// no rounded weight biases every node alike.  M~ R~ comes with the pyramid;
+// 36 M~ That is stored for the trial passes of the search.  Strip tile: 30
+// owned node columns by strip_rows(n) owned rows, one halo node around them.
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(REG_THREADS, 4) k_grad(BatchDev b)
+__global__ void __launch_bounds__(REG_STRIP_THREADS, 8) k_grad(BatchDev b)
 {
-    constexpr int HX = REG_TX + 2, HY = REG_TY + 2, HN = HX * HY;
-    __shared__ float4 su[HN];
-    __shared__ float sT[HN], sR[HN], sgx[HN], sgy[HN];
-    __shared__ float red[REG_THREADS / 32];
-    int nent = b.ctr[2], items = b.ctr[5];
-    int b0, b1;
-    block_range(items, b0, b1);
-    if (b0 >= b1) return;
-    ItemWalker wk(b.prefG, nent, b0);
-    const int lx = threadIdx.x % REG_TX, ly = threadIdx.x / REG_TX;
-    for (int item = b0; item < b1; item++) {
-        int e = wk.entry(item);
-        int o = b.listG[e];
-        int t = item - b.prefG[e];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (REG_STRIP_THREADS / 32);
+    const int nent = b.ctr[2], items = b.ctr[5];
+    for (int item = blockIdx.x * (REG_STRIP_THREADS / 32) + (threadIdx.x >> 5); item < items; item += nwarps) {
+        const int e = find_entry(b.prefG, nent, item);
+        const int o = b.listG[e];
+        const int t = item - b.prefG[e];
         const OpState &s = b.st[o];
         const LevelDesc &Lv = b.ops[o].lv[s.lvl];
-        const int n = Lv.n, pitch = Lv.pitch, tx = (n + REG_TX - 1) / REG_TX;
-        const int r0 = (t / tx) * REG_TY, c0 = (t % tx) * REG_TX;
+        const int n = Lv.n, pitch = Lv.pitch, ntx = (n + REG_GW - 1) / REG_GW, h = strip_rows(n);
+        const int r0 = (t / ntx) * h, c = (t % ntx) * REG_GW - 1 + lane;
+        const int rLast = min(r0 + h - 1, n - 1);
+        const bool colIn = c >= 0 && c < n;
+        const bool own = colIn && lane >= 1 && lane <= REG_GW;
+        const bool cEdge = (c == 0 || c == n - 1);
+        const float cx6 = cEdge ? 2.f : 4.f;  // 6 M1 on the diagonal
+        const float wx = cEdge ? 0.5f : 1.f, iwx = cEdge ? 2.f : 1.f;
         const float tau = (float)s.tau_acc;
-        const float4 *Us = Lv.U[s.src];
-        const float2 *Ds = Lv.D[s.src];
-        const float Tbar = (float)s.Tbar;
-        const float isig = (float)(1.0 / s.sigT), ncc = (float)s.ncc, lam = (float)b.lambda;
-        __syncthreads();
-        // staging pass 1: the tile's own data (independent loads)
-        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
-            int r = r0 - 1 + p / HX, c = c0 - 1 + p % HX;
+        const NodeRec *Vs = Lv.V[s.src];
+        NodeRec *Vc = Lv.V[s.cur];
+        // the stencils run on the integer weights 6 M1 and 6 K1 (36 M~, 6 K); their
+        // scale goes into these per-tile coefficients, each rounded once
+        const float isig = (float)(1.0 / s.sigT);
+        const float c36 = (float)(s.ncc / (s.sigT * s.sigT) / 36.0);  // NCC / sigma^2 / 36
+        const float cT = (float)(s.ncc / (s.sigT * s.sigT) * s.Tbar);  // NCC / sigma^2 T_bar
+        const float lam6 = (float)(b.lambda / 6.0);
+        const float ih2 = 1.f / Lv.h2;  // exact: h^2 is a power of two
+        // rows r-2 (suffix A) and r-1 (suffix M) of this column; row r is read
+        // in the iteration and row r-1 is completed by it
+        float tA = 0.f, tM = 0.f, kxAx = 0.f, kxAy = 0.f, kxMx = 0.f, kxMy = 0.f;
+        float dyMx = 0.f, dyMy = 0.f, gxM = 0.f, gyM = 0.f, mrM = 0.f;
+        float4 uM = make_float4(0.f, 0.f, 0.f, 0.f);
+        float slope = 0.f, qud = 0.f;
+        for (int r = r0 - 1; r <= rLast + 1; r++) {
+            const bool in = colIn && r >= 0 && r < n;
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            float rv = 0.f;
-            if (r >= 0 && r < n && c >= 0 && c < n) {
-                int64_t idx = (int64_t)r * pitch + c;
-                u = Us[idx];
+            float tv = 0.f, gx = 0.f, gy = 0.f, mr = 0.f;
+            if (in) {
+                const int64_t idx = (int64_t)r * pitch + c;
+                const float4 *rec = reinterpret_cast<const float4 *>(Vs + idx);
+                u = rec[0];
                 if (tau != 0.f) {
-                    float2 d = Ds[idx];
-                    u = df_add2(u, tau * d.x, tau * d.y);
+                    const float4 dm = rec[1];
+                    u = df_add2(u, tau * dm.x, tau * dm.y);
                 }
-                rv = ldimg<BF16>(Lv.R, (int)idx);
+                mr = Lv.MR[idx];
+                tv = sample_df<BF16, true>(Lv.T, n, pitch, c, r, u, &gx, &gy);
             }
-            su[p] = u; sR[p] = rv;
-        }
-        __syncthreads();
-        // staging pass 2: the warped template and its derivative (gathers)
-        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
-            int r = r0 - 1 + p / HX, c = c0 - 1 + p % HX;
-            float tv = 0.f, gx = 0.f, gy = 0.f;
-            if (r >= 0 && r < n && c >= 0 && c < n)
-                tv = sample_df<BF16, true>(Lv.T, n, pitch, c, r, su[p], &gx, &gy) - Tbar;
-            sT[p] = tv; sgx[p] = gx; sgy[p] = gy;
-        }
-        __syncthreads();
-        float contrib = 0.f;
-        const int c = c0 + lx;
-#pragma unroll
-        for (int k = 0; k < REG_RPT; k++) {
-            const int lr = ly + k * REG_ROWSTEP, r = r0 + lr;
-            if (r >= n || c >= n) continue;
-            float mT = 0.f, mR = 0.f, kux = 0.f, kuy = 0.f;
-            const int pc = (lr + 1) * HX + lx + 1;
-            const float4 u0 = su[pc];
-#pragma unroll
-            for (int a = -1; a <= 1; a++) {
-                float wr = m1w(r, a, n), kr = k1w(r, a, n);
-#pragma unroll
-                for (int bb = -1; bb <= 1; bb++) {
-                    float wc = m1w(c, bb, n), kc = k1w(c, bb, n);
-                    int p = (lr + 1 + a) * HX + (lx + 1 + bb);
-                    float wm = wr * wc, wkk = kr * wc + wr * kc;
-                    mT += wm * sT[p];
-                    mR += wm * sR[p];
-                    // K has zero row sums: K u = sum w (u_p - u_0), the differences
-                    // formed from the hi and lo parts separately
-                    float4 up = su[p];
-                    kux += wkk * ((up.x - u0.x) + (up.z - u0.z));
-                    kuy += wkk * ((up.y - u0.y) + (up.w - u0.w));
+            // u(r, c+1) - u(r, c) and u(r, c) - u(r-1, c), each from the hi and
+            // lo parts (the stiffness terms are small differences of values of
+            // several grid units); 0 where a node is missing
+            float4 uR;
+            uR.x = __shfl_down_sync(FULL, u.x, 1);
+            uR.y = __shfl_down_sync(FULL, u.y, 1);
+            uR.z = __shfl_down_sync(FULL, u.z, 1);
+            uR.w = __shfl_down_sync(FULL, u.w, 1);
+            const bool hasR = in && c + 1 < n, hasU = in && r >= 1 && r >= r0;
+            const float dxx = hasR ? (uR.x - u.x) + (uR.z - u.z) : 0.f;
+            const float dxy = hasR ? (uR.y - u.y) + (uR.w - u.w) : 0.f;
+            const float dyx = hasU ? (u.x - uM.x) + (u.z - uM.z) : 0.f;
+            const float dyy = hasU ? (u.y - uM.y) + (u.w - uM.w) : 0.f;
+            // K1 along the row: [u(c) - u(c-1)] - [u(c+1) - u(c)]
+            const float kxx = __shfl_up_sync(FULL, dxx, 1) - dxx;
+            const float kxy = __shfl_up_sync(FULL, dxy, 1) - dxy;
+            const int m = r - 1;
+            if (m >= r0) {
+                const bool mEdge = (m == 0 || m == n - 1);
+                const float cy6 = mEdge ? 2.f : 4.f;
+                // 36 M~ That at (m, c): 6 M1 down the column, then along the row
+                const float vt = (tA + tv) + cy6 * tM;
+                const float mt36 = (__shfl_up_sync(FULL, vt, 1) + __shfl_down_sync(FULL, vt, 1)) + cx6 * vt;
+                // K1 along the column at m: [u(m) - u(m-1)] - [u(m+1) - u(m)]
+                const float kyx = dyMx - dyx, kyy = dyMy - dyy;
+                const float KYx = (__shfl_up_sync(FULL, kyx, 1) + __shfl_down_sync(FULL, kyx, 1)) + cx6 * kyx;
+                const float KYy = (__shfl_up_sync(FULL, kyy, 1) + __shfl_down_sync(FULL, kyy, 1)) + cx6 * kyy;
+                if (own) {
+                    // 6 (K u)
+                    const float kux = (kxAx + kxx) + cy6 * kxMx + KYx;
+                    const float kuy = (kxAy + kxy) + cy6 * kxMy + KYy;
+                    const float om = wx * (mEdge ? 0.5f : 1.f), iom = iwx * (mEdge ? 2.f : 1.f);
+                    // dNCC/dThat / h^2 = (M~R~) / sigma - NCC (M~That - T_bar omega) / sigma^2
+                    const float A = mrM * isig - c36 * mt36 + cT * om;
+                    const float psx = -A * gxM + lam6 * kux, psy = -A * gyM + lam6 * kuy;
+                    const float sc = ih2 * iom;
+                    const float dnx = -psx * sc, dny = -psy * sc;
+                    const int64_t idx = (int64_t)m * pitch + c;
+                    float4 *rec = reinterpret_cast<float4 *>(Vc + idx);
+                    rec[0] = uM;
+                    rec[1] = make_float4(dnx, dny, mt36, mrM);
+                    slope -= (psx * psx + psy * psy) * iom;
+                    qud += dnx * kux + dny * kuy;
                 }
             }
-            float A = mR * isig - ncc * mT * isig * isig;
-            float psx = -A * sgx[pc] + lam * kux;
-            float psy = -A * sgy[pc] + lam * kuy;
-            float om = ((r == 0 || r == n - 1) ? 0.5f : 1.f) * ((c == 0 || c == n - 1) ? 0.5f : 1.f);
-            float inv = 1.f / (Lv.h2 * om);
-            int64_t idx = (int64_t)r * pitch + c;
-            Lv.U[s.cur][idx] = su[pc];
-            Lv.D[s.cur][idx] = make_float2(-psx * inv, -psy * inv);
-            contrib -= (psx * psx + psy * psy) / om;
+            tA = tM; tM = tv;
+            kxAx = kxMx; kxAy = kxMy; kxMx = kxx; kxMy = kxy;
+            dyMx = dyx; dyMy = dyy;
+            gxM = gx; gyM = gy; mrM = mr; uM = u;
         }
-        contrib = warp_sum(contrib);
-        if (lx == 0) red[ly] = contrib;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-#pragma unroll
-            for (int w = 0; w < REG_THREADS / 32; w++) tot += red[w];
-            b.partG[item] = tot;
-        }
+        slope = warp_sum(slope);
+        qud = warp_sum(qud / 6.f);
+        if (lane < PG_STRIDE) b.partG[(int64_t)item * PG_STRIDE + lane] = lane == 0 ? slope : qud;
     }
 }
 
-// ---------------------------------------------------------------------------
-// T: warp + energy.
-// Level-start pass (tau = 0): full sums at u, per cell (Q1 element)
-//   [0] int That / h^2   [1] int That^2 / h^2   [2] int That R~ / h^2   [3 MAXT] Quu
-// Trial pass: for every step size tau_j the change against the current u.
-// Per node delta_j = That(u + tau_j d) - That(u); when both points lie in the
-// same bilinear cell it is formed from the same four texels as
-//   tau d_x [(1-a_y') (t01-t00) + a_y' (t11-t10)] + tau d_y [(1-a_x) (t10-t00) + a_x (t11-t01)],
-// so that its float rounding is relative to delta itself (the quantity the
-// Armijo test compares), not to That; across a cell line it is formed in
-// double precision.
-//   [3j] int delta / h^2   [3j+1] int delta (2 That + delta) / h^2   [3j+2] int delta R~ / h^2
-// and the Dirichlet form of u + tau d as Quu + 2 tau Qud + tau^2 Qdd.
-// Tile: 32 x 32 cells, i.e. 33 x 33 nodes staged in shared memory.
-// ---------------------------------------------------------------------------
-#define PT_STRIDE (3 * REG_MAX_TRIALS + 3)
-
+// Bilinear sampling helpers of the trial pass.
 namespace {
 
 struct Texel4 {
@@ -676,22 +708,6 @@ __device__ __forceinline__ void locate(int n, int c, int r, float vx, float vy, 
     else if (jy >= n - 1) { cly = (jy > n - 1) || (ay > 0.f); jy = n - 2; ay = 1.f; }
 }
 
-// locate() for a compensated displacement (exact cell choice at cell lines)
-__device__ __forceinline__ void locate_df(int n, int c, int r, float4 u, int &jx, int &jy, float &ax, float &ay,
-                                          bool &clx, bool &cly)
-{
-    int ix, iy;
-    df_split(u.x, u.z, ix, ax);
-    df_split(u.y, u.w, iy, ay);
-    jx = c + ix;
-    jy = r + iy;
-    clx = cly = false;
-    if (jx < 0) { jx = 0; ax = 0.f; clx = true; }
-    else if (jx >= n - 1) { clx = (jx > n - 1) || (ax > 0.f); jx = n - 2; ax = 1.f; }
-    if (jy < 0) { jy = 0; ay = 0.f; cly = true; }
-    else if (jy >= n - 1) { cly = (jy > n - 1) || (ay > 0.f); jy = n - 2; ay = 1.f; }
-}
-
 template <bool BF16>
 __device__ __forceinline__ void fetch(Texel4 &q, const void *img, int pitch)
 {
@@ -707,272 +723,390 @@ __device__ __forceinline__ float bil(const Texel4 &q)
     return (1.f - q.ay) * ((1.f - q.ax) * q.t00 + q.ax * q.t01) + q.ay * ((1.f - q.ax) * q.t10 + q.ax * q.t11);
 }
 
-// Double-precision bilinear sample at grid point (X, Y), clamped like sample().
-template <bool BF16>
-__device__ double sample_d(const void *img, int n, int pitch, double X, double Y)
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// T: warp + energy as FE sums over a strip tile of 31 x 32 cells.
+// Level-start pass (tau = 0), at u:
+//   [0] int That / h^2 = sum omega_i That_i      [1] int That^2 / h^2 = That^T M~ That
+//   [2] int That R~ / h^2 = sum (M~ R~)_i That_i   [3 MAXT] Quu, the Dirichlet form of u
+// Trial pass: for every step size tau_j the change against the current u,
+// delta_j = That(u + tau_j d) - That(u) per node:
+//   [3j] sum omega delta   [3j+1] 2 sum (M~ That) delta + delta^T M~ delta
+//   [3j+2] sum (M~ R~) delta
+// and in the first pass of a search [3 MAXT + 2] Qdd, the Dirichlet form of d
+// (the Dirichlet form of u + tau d is Quu + 2 tau Qud + tau^2 Qdd).
+// When u and u + tau d lie in the same bilinear cell, delta is formed from the
+// cell's four texels as
+//   tau d_x [(1-a_y') (t01-t00) + a_y' (t11-t10)] + tau d_y [(1-a_x) (t10-t00) + a_x (t11-t01)],
+// so that its float rounding is relative to delta itself (the quantity the
+// Armijo test compares), not to That; a tiny move across a cell line is split
+// into exact segments, and a move of 2^-10 grid units or more takes a fresh
+// sample.
+// Sums over nodes use per-node weights (omega and the stored M~ That, M~ R~);
+// the quadratic forms are summed per cell.  With the cyclic corner order the
+// element mass matrix is (1/36) [4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4], and
+//   36 v^T M~_e v = 4 P(top) + 4 P(bottom) + 2 top . [2 1; 1 2] bottom,
+//   P(x0, x1) = x0 (x0 + x1) + x1^2,
+// so each row's P is formed once for the two cells that share the row.  The
+// cell's Dirichlet form is (P(p, q) + P(r, s)) / 3 per component, p, q the x
+// differences of its top and bottom rows and r, s the y differences of its
+// left and right columns.  Lane l holds node column c0 + l; lanes 0..30 own
+// the cells to their right, lane 31 supplies the right corners.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float pform(float x0, float x1) { return x0 * (x0 + x1) + x1 * x1; }
+
+struct StripGeom {
+    int n, pitch, h, r0, rEnd, c;
+    bool colIn, cellCol, nodeCol;
+    float wx;
+};
+
+__device__ __forceinline__ StripGeom strip_geom(const LevelDesc &Lv, int t, int lane)
 {
-    if (X < 0.0) X = 0.0;
-    if (X > n - 1) X = n - 1;
-    if (Y < 0.0) Y = 0.0;
-    if (Y > n - 1) Y = n - 1;
-    int jx = (int)floor(X), jy = (int)floor(Y);
-    if (jx > n - 2) jx = n - 2;
-    if (jy > n - 2) jy = n - 2;
-    double ax = X - jx, ay = Y - jy;
-    int i0 = jy * pitch + jx;
-    double t00 = ldimg<BF16>(img, i0), t01 = ldimg<BF16>(img, i0 + 1);
-    double t10 = ldimg<BF16>(img, i0 + pitch), t11 = ldimg<BF16>(img, i0 + pitch + 1);
-    return (1.0 - ay) * ((1.0 - ax) * t00 + ax * t01) + ay * ((1.0 - ax) * t10 + ax * t11);
+    StripGeom g;
+    g.n = Lv.n;
+    g.pitch = Lv.pitch;
+    const int ntx = (g.n - 1 + REG_CW - 1) / REG_CW;
+    g.h = strip_rows(g.n);
+    g.r0 = (t / ntx) * g.h;
+    g.c = (t % ntx) * REG_CW + lane;
+    g.rEnd = min(g.r0 + g.h, g.n - 1);
+    g.colIn = g.c < g.n;
+    g.cellCol = lane < REG_CW && g.c < g.n - 1;
+    g.nodeCol = g.colIn && (lane < REG_CW || g.c == g.n - 1);
+    g.wx = (g.c == 0 || g.c == g.n - 1) ? 0.5f : 1.f;
+    return g;
 }
 
-// Change of the sample across a cell line (or at a clamp), in double: a float
-// in-cell fraction cannot resolve sub-ulp moves across the line (1 - 2e-8
-// rounds to 1), which would lose the energy change of the move.
+// The 3 x 3 texel patch around the base cell of a node, extended towards the
+// direction of its move, and the per-node terms of the exact change of the
+// interpolant for moves of less than one cell (patch_delta).
+struct Patch {
+    float ax, ay;    // fractions of the base point in its cell (clamped coordinates: 0 or 1)
+    float lx, ly;    // signed distance to the next cell line in the move direction
+    float s0x, s1x;  // slope along x at a_y of the base cell and of its neighbour in the move direction
+    float v0[3], v1[3];  // t(row + 1) - t(row) in the base row band and in the neighbour band,
+                         // columns: base left, base right, neighbour outer
+    bool nbx, nby;   // the neighbour cell exists (else the interpolant is flat beyond the border)
+    bool posx, posy; // move direction
+    int clx, cly;    // 0: inside; otherwise the raw cell index of the clamped base point (never 0)
+    float rax, ray;  // raw fraction of a clamped base point
+    float t0;        // the interpolant at the base point
+};
+
 template <bool BF16>
-__device__ __noinline__ float cross_delta(const void *img, int n, int pitch, int c, int r, float4 u, float tau,
-                                          float dx, float dy)
+__device__ __forceinline__ void make_patch(Patch &P, const void *T, int n, int pitch, int c, int r, float4 u, float dx,
+                                           float dy)
 {
-    double X0 = c + ((double)u.x + (double)u.z), Y0 = r + ((double)u.y + (double)u.w);
-    double X1 = X0 + (double)tau * dx, Y1 = Y0 + (double)tau * dy;
-    return (float)(sample_d<BF16>(img, n, pitch, X1, Y1) - sample_d<BF16>(img, n, pitch, X0, Y0));
+    int ix, iy;
+    float fx, fy;
+    df_split(u.x, u.z, ix, fx);
+    df_split(u.y, u.w, iy, fy);
+    int jx = c + ix, jy = r + iy;
+    P.rax = fx;
+    P.ray = fy;
+    P.clx = P.cly = 0;
+    float ax = fx, ay = fy;
+    if (jx < 0) { P.clx = jx; jx = 0; ax = 0.f; }
+    else if (jx >= n - 1) { if (jx > n - 1 || fx > 0.f) P.clx = jx; jx = n - 2; ax = 1.f; }
+    if (jy < 0) { P.cly = jy; jy = 0; ay = 0.f; }
+    else if (jy >= n - 1) { if (jy > n - 1 || fy > 0.f) P.cly = jy; jy = n - 2; ay = 1.f; }
+    P.ax = ax;
+    P.ay = ay;
+    P.posx = dx >= 0.f;
+    P.posy = dy >= 0.f;
+    P.nbx = P.posx ? (jx + 1 <= n - 2) : (jx >= 1);
+    P.nby = P.posy ? (jy + 1 <= n - 2) : (jy >= 1);
+    const int cx2 = P.posx ? min(jx + 2, n - 1) : max(jx - 1, 0);
+    const int ry2 = P.posy ? min(jy + 2, n - 1) : max(jy - 1, 0);
+    const int rows[3] = {jy, jy + 1, ry2}, cols[3] = {jx, jx + 1, cx2};
+    float t[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) t[a][b] = ldimg<BF16>(T, rows[a] * pitch + cols[b]);
+    P.t0 = (1.f - ay) * ((1.f - ax) * t[0][0] + ax * t[0][1]) + ay * ((1.f - ax) * t[1][0] + ax * t[1][1]);
+    P.lx = P.posx ? 1.f - ax : -ax;
+    P.ly = P.posy ? 1.f - ay : -ay;
+    P.s0x = (1.f - ay) * (t[0][1] - t[0][0]) + ay * (t[1][1] - t[1][0]);
+    // neighbour cell along x: columns (1, 2) when moving right, (2, 0) when moving left
+    const float nl0 = P.posx ? t[0][1] : t[0][2], nr0 = P.posx ? t[0][2] : t[0][0];
+    const float nl1 = P.posx ? t[1][1] : t[1][2], nr1 = P.posx ? t[1][2] : t[1][0];
+    P.s1x = P.nbx ? (1.f - ay) * (nr0 - nl0) + ay * (nr1 - nl1) : 0.f;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        P.v0[b] = t[1][b] - t[0][b];
+        P.v1[b] = P.posy ? t[2][b] - t[1][b] : t[0][b] - t[2][b];
+    }
 }
 
-// Change of the interpolant for a move (ex, ey) of less than one cell from an
-// unclamped base point in cell (jx, jy) at fractions (ax, ay), when the move
-// leaves the cell.  The move is split into its x part (along the row band of
-// the base point) and its y part (at the new column); each part is a sum of
-// segment lengths times the slope of the cell the segment lies in, so float
-// rounding stays relative to the change itself even for moves far below one
-// ulp of the fraction.  Past the grid border the interpolant is constant.
-template <bool BF16>
-__device__ __noinline__ float cross_delta_f32(const void *img, int n, int pitch, int jx, int jy, float ax, float ay,
-                                              float ex, float ey)
+// Change of the interpolant for the move (ex, ey) from the base point of P,
+// split into a move along x in the base row band and a move along y at the new
+// column; each part is a sum of segment lengths times the slope of the cell
+// the segment lies in, so that its rounding is relative to the change itself
+// (a single float fraction could not resolve a move far below its ulp across a
+// cell line).  Past the grid border the interpolant is flat; a base point
+// outside the grid contributes only the part of the move back inside.
+// Returns false (and no value) for a move of a cell or more.
+__device__ __forceinline__ bool patch_delta(const Patch &P, int n, float ex, float ey, float &del)
 {
-    auto T = [&](int r, int c) { return ldimg<BF16>(img, r * pitch + c); };
-    // slope along x of cell column i in row band jy at fraction ay (grid units)
-    auto sx = [&](int i) {
-        return (1.f - ay) * (T(jy, i + 1) - T(jy, i)) + ay * (T(jy + 1, i + 1) - T(jy + 1, i));
-    };
-    float dx = 0.f, ax1 = ax + ex;
-    int cx = jx;  // cell column of the new x position
-    if (ax1 >= 1.f) {
-        dx = (1.f - ax) * sx(jx);
-        if (jx + 1 <= n - 2) dx += (ex - (1.f - ax)) * sx(jx + 1);  // beyond the border: flat
-        cx = jx + 1 <= n - 2 ? jx + 1 : jx;
-        ax1 = jx + 1 <= n - 2 ? ex - (1.f - ax) : 1.f;
-    } else if (ax1 < 0.f) {
-        dx = -ax * sx(jx);
-        if (jx - 1 >= 0) dx += (ex + ax) * sx(jx - 1);
-        cx = jx - 1 >= 0 ? jx - 1 : jx;
-        ax1 = jx - 1 >= 0 ? 1.f + (ex + ax) : 0.f;
+    bool ok = true;
+    // x part
+    float xpart, f;
+    bool nbcol = false;  // the y part runs in the neighbour column cell
+    if (P.clx) {
+        ok = fabsf(ex) < 1.f;
+        // length of the move inside the grid: from the left border (raw cell
+        // -1) or back from the right border (raw cell n-1); 0 further out
+        const float in = (P.clx == -1) ? fmaxf(P.rax + ex - 1.f, 0.f)
+                                        : ((P.clx == n - 1) ? fminf(P.rax + ex, 0.f) : 0.f);
+        xpart = in * P.s0x;
+        f = P.ax + in;
     } else {
-        dx = ex * sx(jx);
+        const float ax1 = P.ax + ex;
+        if (ax1 >= 0.f && ax1 < 1.f) {
+            xpart = ex * P.s0x;
+            f = ax1;
+        } else {
+            const float rest = ex - P.lx;  // length beyond the cell line
+            ok = fabsf(rest) < 1.f;
+            xpart = P.lx * P.s0x + rest * P.s1x;
+            f = P.nbx ? (P.posx ? rest : 1.f + rest) : (P.posx ? 1.f : 0.f);
+            nbcol = P.nbx;
+        }
     }
-    // slope along y of cell row j at column cell cx and fraction ax1
-    auto sy = [&](int j) {
-        return (1.f - ax1) * (T(j + 1, cx) - T(j, cx)) + ax1 * (T(j + 1, cx + 1) - T(j, cx + 1));
-    };
-    float dy = 0.f, ay1 = ay + ey;
-    if (ay1 >= 1.f) {
-        dy = (1.f - ay) * sy(jy);
-        if (jy + 1 <= n - 2) dy += (ey - (1.f - ay)) * sy(jy + 1);
-    } else if (ay1 < 0.f) {
-        dy = -ay * sy(jy);
-        if (jy - 1 >= 0) dy += (ey + ay) * sy(jy - 1);
+    // y part at the new column: slopes of the base and neighbour row bands
+    const float vl0 = nbcol ? (P.posx ? P.v0[1] : P.v0[2]) : P.v0[0];
+    const float vr0 = nbcol ? (P.posx ? P.v0[2] : P.v0[0]) : P.v0[1];
+    const float sy0 = (1.f - f) * vl0 + f * vr0;
+    float ypart;
+    if (P.cly) {
+        ok = ok && fabsf(ey) < 1.f;
+        const float in = (P.cly == -1) ? fmaxf(P.ray + ey - 1.f, 0.f)
+                                        : ((P.cly == n - 1) ? fminf(P.ray + ey, 0.f) : 0.f);
+        ypart = in * sy0;
     } else {
-        dy = ey * sy(jy);
+        const float ay1 = P.ay + ey;
+        if (ay1 >= 0.f && ay1 < 1.f) {
+            ypart = ey * sy0;
+        } else {
+            const float rest = ey - P.ly;
+            ok = ok && fabsf(rest) < 1.f;
+            const float vl1 = nbcol ? (P.posx ? P.v1[1] : P.v1[2]) : P.v1[0];
+            const float vr1 = nbcol ? (P.posx ? P.v1[2] : P.v1[0]) : P.v1[1];
+            const float sy1 = P.nby ? (1.f - f) * vl1 + f * vr1 : 0.f;
+            ypart = P.ly * sy0 + rest * sy1;
+        }
     }
-    return dx + dy;
+    del = xpart + ypart;
+    return ok;
+}
+
+// Level-start sums of one strip tile at u, accumulated in double: they seed
+// every search of the level (the trial passes only add changes to them), and
+// the pass runs once per level.
+template <bool BF16>
+__device__ __forceinline__ void start_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, double *v)
+{
+    const unsigned FULL = 0xffffffffu;
+    const NodeRec *V = Lv.V[s.cur];
+    double s1 = 0.0, s3 = 0.0, q2 = 0.0, quu = 0.0;
+    float tP = 0.f, tPR = 0.f, pux = 0.f, puy = 0.f;
+    float4 uP = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = g.r0; r <= g.rEnd; r++) {
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        float t0 = 0.f, mr = 0.f;
+        if (g.colIn) {
+            const int64_t idx = (int64_t)r * g.pitch + g.c;
+            u = V[idx].u;
+            mr = Lv.MR[idx];
+            t0 = sample_df<BF16, false>(Lv.T, g.n, g.pitch, g.c, r, u, nullptr, nullptr);
+        }
+        if (g.nodeCol && (r < g.r0 + g.h || r == g.n - 1)) {
+            const float w = g.wx * ((r == 0 || r == g.n - 1) ? 0.5f : 1.f);
+            s1 += (double)(w * t0);
+            s3 += (double)(mr * t0);
+        }
+        const float tR = __shfl_down_sync(FULL, t0, 1);
+        float4 uR;
+        uR.x = __shfl_down_sync(FULL, u.x, 1);
+        uR.y = __shfl_down_sync(FULL, u.y, 1);
+        uR.z = __shfl_down_sync(FULL, u.z, 1);
+        uR.w = __shfl_down_sync(FULL, u.w, 1);
+        const float qx = (uR.x - u.x) + (uR.z - u.z), qy = (uR.y - u.y) + (uR.w - u.w);
+        const float rx = (u.x - uP.x) + (u.z - uP.z), ry = (u.y - uP.y) + (u.w - uP.w);
+        const float sx = __shfl_down_sync(FULL, rx, 1), sy = __shfl_down_sync(FULL, ry, 1);
+        if (g.cellCol) {
+            const float wrow2 = (float)(2 * ((r > g.r0) + (r < g.rEnd)));
+            q2 += (double)(wrow2 * pform(t0, tR));
+            if (r > g.r0) {
+                q2 += (double)(tP * (2.f * t0 + tR) + tPR * (t0 + 2.f * tR));
+                quu += (double)(pform(pux, qx) + pform(rx, sx) + pform(puy, qy) + pform(ry, sy));
+            }
+        }
+        tP = t0; tPR = tR;
+        pux = qx; puy = qy; uP = u;
+    }
+    v[0] = s1;
+    v[1] = q2 * (1.0 / 18.0);
+    v[2] = s3;
+    v[3] = quu * (1.0 / 3.0);
+}
+
+// Trial sums of one strip tile for the step sizes tau_0..tau_{J-1}.  The node
+// record of the next row is loaded while the current row is worked on.
+template <bool BF16, int JM>
+__device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, float *v)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int J = min(s.ntr, JM);
+    const bool withQ = (s.phase == PH_GRAD);
+    const float4 *V = reinterpret_cast<const float4 *>(Lv.V[s.cur]);
+    float tau[JM], aS1[JM], aS2[JM], aS3[JM], pT[JM], pTR[JM];
+#pragma unroll
+    for (int j = 0; j < JM; j++) {
+        tau[j] = (j < J) ? (float)s.trial_tau[j] : 0.f;
+        aS1[j] = aS2[j] = aS3[j] = pT[j] = pTR[j] = 0.f;
+    }
+    float qdd = 0.f, pdx = 0.f, pdy = 0.f, dPx = 0.f, dPy = 0.f;
+    float4 nu = make_float4(0.f, 0.f, 0.f, 0.f), ndm = nu;  // record of the next row
+    if (g.colIn) {
+        const int64_t idx = (int64_t)g.r0 * g.pitch + g.c;
+        nu = V[2 * idx];
+        ndm = V[2 * idx + 1];
+    }
+    for (int r = g.r0; r <= g.rEnd; r++) {
+        const float4 u = nu, dm = ndm;  // d = (dm.x, dm.y), 36 M~That = dm.z, M~R~ = dm.w
+        if (g.colIn && r < g.rEnd) {
+            const int64_t idx = (int64_t)(r + 1) * g.pitch + g.c;
+            nu = V[2 * idx];
+            ndm = V[2 * idx + 1];
+        }
+        float del[JM];
+#pragma unroll
+        for (int j = 0; j < JM; j++) del[j] = 0.f;
+        if (g.colIn) {
+            Patch P;
+            make_patch<BF16>(P, Lv.T, g.n, g.pitch, g.c, r, u, dm.x, dm.y);
+            unsigned fresh = 0;
+#pragma unroll
+            for (int j = 0; j < JM; j++)
+                if (j < J && !patch_delta(P, g.n, tau[j] * dm.x, tau[j] * dm.y, del[j])) fresh |= 1u << j;
+            // moves of a cell or more: a fresh sample at the new point, whose
+            // rounding (~1e-7 of That) is small against such a change
+            while (fresh) {
+                const int j = __ffs(fresh) - 1;
+                fresh &= fresh - 1;
+                float tj = 0.f;
+#pragma unroll
+                for (int k = 0; k < JM; k++)
+                    if (k == j) tj = tau[k];
+                Texel4 w;
+                locate(g.n, g.c, r, (u.x + u.z) + tj * dm.x, (u.y + u.w) + tj * dm.y, w.jx, w.jy, w.ax, w.ay, w.clx,
+                       w.cly);
+                fetch<BF16>(w, Lv.T, g.pitch);
+                const float x = bil(w) - P.t0;
+#pragma unroll
+                for (int k = 0; k < JM; k++)
+                    if (k == j) del[k] = x;
+            }
+        }
+        // aS2 is kept in units of 1/18 (integer weights; one division at the end)
+        if (g.nodeCol && (r < g.r0 + g.h || r == g.n - 1)) {
+            const float w = g.wx * ((r == 0 || r == g.n - 1) ? 0.5f : 1.f), mt36 = dm.z;
+#pragma unroll
+            for (int j = 0; j < JM; j++) {
+                aS1[j] += w * del[j];
+                aS2[j] += mt36 * del[j];
+                aS3[j] += dm.w * del[j];
+            }
+        }
+        const float wrow2 = (float)(2 * ((r > g.r0) + (r < g.rEnd)));
+#pragma unroll
+        for (int j = 0; j < JM; j++) {
+            if (j < J) {
+                const float dR = __shfl_down_sync(FULL, del[j], 1);
+                if (g.cellCol) {
+                    float q2 = wrow2 * pform(del[j], dR);
+                    if (r > g.r0) q2 += pT[j] * (2.f * del[j] + dR) + pTR[j] * (del[j] + 2.f * dR);
+                    aS2[j] += q2;
+                }
+                pT[j] = del[j];
+                pTR[j] = dR;
+            }
+        }
+        if (withQ) {
+            const float dRx = __shfl_down_sync(FULL, dm.x, 1), dRy = __shfl_down_sync(FULL, dm.y, 1);
+            const float qx = dRx - dm.x, qy = dRy - dm.y;
+            const float rx = dm.x - dPx, ry = dm.y - dPy;
+            const float sx = __shfl_down_sync(FULL, rx, 1), sy = __shfl_down_sync(FULL, ry, 1);
+            if (g.cellCol && r > g.r0) qdd += pform(pdx, qx) + pform(rx, sx) + pform(pdy, qy) + pform(ry, sy);
+            pdx = qx; pdy = qy; dPx = dm.x; dPy = dm.y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < JM; j++) {
+        v[3 * j] = aS1[j];
+        v[3 * j + 1] = aS2[j] / 18.f;
+        v[3 * j + 2] = aS3[j];
+    }
+    v[3 * REG_MAX_TRIALS + 2] = qdd / 3.f;
+}
+
+// Warp sums of a tile's partial record; lane k stores entry k.
+template <int JM>
+__device__ __forceinline__ void write_partials(const BatchDev &b, int item, const float *v, int nused, int lane)
+{
+    double mine = 0.0;
+#pragma unroll
+    for (int k = 0; k < PT_STRIDE; k++) {
+        if ((k < 3 * JM && k < nused) || k >= 3 * REG_MAX_TRIALS) {
+            const float tot = warp_sum(v[k]);
+            if (lane == k) mine = tot;
+        }
+    }
+    if (lane < PT_STRIDE) b.partT[(int64_t)item * PT_STRIDE + lane] = mine;
 }
 
 }  // namespace
 
-template <int JM>
-constexpr int trial_smem_bytes()
-{
-    return (REG_TX + 1) * (REG_TY + 1) *
-           ((int)sizeof(float4) + (int)sizeof(float2) + 2 * (int)sizeof(float) + JM * (int)sizeof(float));
-}
-
 template <bool BF16, int JM>
-__global__ void __launch_bounds__(REG_THREADS, 4) k_trial(BatchDev b)
+__global__ void __launch_bounds__(REG_STRIP_THREADS, 6) k_trial(BatchDev b)
 {
-    constexpr int HX = REG_TX + 1, HY = REG_TY + 1, HN = HX * HY;
-    constexpr int NACC = 3 * JM + 3;
-    extern __shared__ float4 dyn_smem[];
-    float4 *su = reinterpret_cast<float4 *>(dyn_smem);
-    float2 *sd = reinterpret_cast<float2 *>(su + HN);
-    float *sR = reinterpret_cast<float *>(sd + HN);
-    float *sT0 = sR + HN;
-    float *sDel = sT0 + HN;  // [JM][HN]
-    __shared__ float red[REG_THREADS / 32][NACC];
-    int nent = b.ctr[3], items = b.ctr[6];
-    int b0, b1;
-    block_range(items, b0, b1);
-    if (b0 >= b1) return;
-    ItemWalker wk(b.prefT, nent, b0);
-    const int lx = threadIdx.x % REG_TX, ly = threadIdx.x / REG_TX;
-    for (int item = b0; item < b1; item++) {
-        int e = wk.entry(item);
-        int o = b.listT[e];
-        int t = item - b.prefT[e];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (REG_STRIP_THREADS / 32);
+    const int nent = b.ctr[3], items = b.ctr[6];
+    for (int item = blockIdx.x * (REG_STRIP_THREADS / 32) + (threadIdx.x >> 5); item < items; item += nwarps) {
+        const int e = find_entry(b.prefT, nent, item);
+        const int o = b.listT[e];
         const OpState &s = b.st[o];
         const LevelDesc &Lv = b.ops[o].lv[s.lvl];
-        const int n = Lv.n, pitch = Lv.pitch, tx = (n - 1 + REG_TX - 1) / REG_TX;
-        const int r0 = (t / tx) * REG_TY, c0 = (t % tx) * REG_TX;
+        const StripGeom g = strip_geom(Lv, item - b.prefT[e], lane);
         const bool start = (s.phase == PH_START || s.phase == PH_PROLONG);
-        const int J = start ? 0 : min(s.ntr, JM);
-        float tau[JM];
+        if (start) {
+            // sums in double, reduced in double: [0..2] and the Dirichlet form of u
+            double v[4];
+            start_tile<BF16>(s, Lv, g, v);
+            double mine = 0.0;
 #pragma unroll
-        for (int j = 0; j < JM; j++) tau[j] = (j < J) ? (float)s.trial_tau[j] : 0.f;
-        const float4 *U = Lv.U[s.cur];
-        const float2 *D = Lv.D[s.cur];
-        __syncthreads();
-        // staging pass 1: the tile's own data (independent loads)
-        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
-            int r = r0 + p / HX, c = c0 + p % HX;
-            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 d = make_float2(0.f, 0.f);
-            float rv = 0.f;
-            if (r < n && c < n) {
-                int64_t idx = (int64_t)r * pitch + c;
-                u = U[idx];
-                if (!start) d = D[idx];
-                rv = ldimg<BF16>(Lv.R, (int)idx);
+            for (int k = 0; k < 4; k++) {
+                const double tot = warp_sum_d(v[k]);
+                if (lane == (k < 3 ? k : 3 * REG_MAX_TRIALS)) mine = tot;
             }
-            su[p] = u; sd[p] = d; sR[p] = rv;
-        }
-        __syncthreads();
-        // staging pass 2: warped template at u and its changes for every step
-        for (int p = threadIdx.x; p < HN; p += REG_THREADS) {
-            int r = r0 + p / HX, c = c0 + p % HX;
-            float t0 = 0.f;
-            if (r < n && c < n) {
-                const float4 u = su[p];
-                const float2 d = sd[p];
-                Texel4 q;
-                locate_df(n, c, r, u, q.jx, q.jy, q.ax, q.ay, q.clx, q.cly);
-                fetch<BF16>(q, Lv.T, pitch);
-                t0 = bil(q);
+            if (lane < PT_STRIDE) b.partT[(int64_t)item * PT_STRIDE + lane] = mine;
+        } else {
+            float v[PT_STRIDE];
 #pragma unroll
-                for (int j = 0; j < JM; j++) {
-                    if (j < J) {
-                        float ex = tau[j] * d.x, ey = tau[j] * d.y;
-                        float ax1 = q.ax + ex, ay1 = q.ay + ey;
-                        float del;
-                        if (!(q.clx | q.cly) && ax1 >= 0.f && ax1 < 1.f && ay1 >= 0.f && ay1 < 1.f) {
-                            del = ex * ((1.f - ay1) * (q.t01 - q.t00) + ay1 * (q.t11 - q.t10)) +
-                                  ey * ((1.f - q.ax) * (q.t10 - q.t00) + q.ax * (q.t11 - q.t01));
-                        } else if (fabsf(ex) < 0x1p-10f && fabsf(ey) < 0x1p-10f) {
-                            // a tiny move across a cell line: exact segment split; from a
-                            // clamped base point (outside the grid): double precision
-                            if (!(q.clx | q.cly))
-                                del = cross_delta_f32<BF16>(Lv.T, n, pitch, q.jx, q.jy, q.ax, q.ay, ex, ey);
-                            else
-                                del = cross_delta<BF16>(Lv.T, n, pitch, c, r, u, tau[j], d.x, d.y);
-                        } else {
-                            // a move of at least 2^-10 grid units: a fresh float sample;
-                            // its rounding (~1e-7 of That) is small against delta
-                            Texel4 w;
-                            locate(n, c, r, (u.x + u.z) + ex, (u.y + u.w) + ey, w.jx, w.jy, w.ax, w.ay, w.clx, w.cly);
-                            fetch<BF16>(w, Lv.T, pitch);
-                            del = bil(w) - t0;
-                        }
-                        sDel[j * HN + p] = del;
-                    }
-                }
-            }
-            sT0[p] = t0;
-        }
-        __syncthreads();
-        float acc[NACC];
-#pragma unroll
-        for (int k = 0; k < NACC; k++) acc[k] = 0.f;
-        const int c = c0 + lx;
-#pragma unroll
-        for (int kk = 0; kk < REG_RPT; kk++) {
-            const int lr = ly + kk * REG_ROWSTEP, r = r0 + lr;
-            if (r >= n - 1 || c >= n - 1) continue;
-            // cyclic corners a=(r,c) b=(r,c+1) c=(r+1,c+1) d=(r+1,c); element mass
-            // matrix (1/36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4]
-            const int pa = lr * HX + lx, pb = pa + 1, pc = pa + HX + 1, pd = pa + HX;
-            float Ra = sR[pa], Rb = sR[pb], Rc = sR[pc], Rd = sR[pd];
-            float MRa = (4.f * Ra + 2.f * Rb + Rc + 2.f * Rd) * (1.f / 36.f);
-            float MRb = (2.f * Ra + 4.f * Rb + 2.f * Rc + Rd) * (1.f / 36.f);
-            float MRc = (Ra + 2.f * Rb + 4.f * Rc + 2.f * Rd) * (1.f / 36.f);
-            float MRd = (2.f * Ra + Rb + 2.f * Rc + 4.f * Rd) * (1.f / 36.f);
-            float ta = sT0[pa], tb = sT0[pb], tc = sT0[pc], td = sT0[pd];
-            if (start) {
-                float Ma = 4.f * ta + 2.f * tb + tc + 2.f * td;
-                float Mb = 2.f * ta + 4.f * tb + 2.f * tc + td;
-                float Mc = ta + 2.f * tb + 4.f * tc + 2.f * td;
-                float Md = 2.f * ta + tb + 2.f * tc + 4.f * td;
-                acc[0] += 0.25f * (ta + tb + tc + td);
-                acc[1] += (ta * Ma + tb * Mb + tc * Mc + td * Md) * (1.f / 36.f);
-                acc[2] += ta * MRa + tb * MRb + tc * MRc + td * MRd;
-            }
-#pragma unroll
-            for (int j = 0; j < JM; j++) {
-                if (j < J) {
-                    const float *dl = sDel + j * HN;
-                    float da = dl[pa], db = dl[pb], dc = dl[pc], dd = dl[pd];
-                    float wa = 2.f * ta + da, wb = 2.f * tb + db, wc = 2.f * tc + dc, wd = 2.f * td + dd;
-                    float Ma = 4.f * wa + 2.f * wb + wc + 2.f * wd;
-                    float Mb = 2.f * wa + 4.f * wb + 2.f * wc + wd;
-                    float Mc = wa + 2.f * wb + 4.f * wc + 2.f * wd;
-                    float Md = 2.f * wa + wb + 2.f * wc + 4.f * wd;
-                    acc[3 * j + 0] += 0.25f * (da + db + dc + dd);
-                    acc[3 * j + 1] += (da * Ma + db * Mb + dc * Mc + dd * Md) * (1.f / 36.f);
-                    acc[3 * j + 2] += da * MRa + db * MRb + dc * MRc + dd * MRd;
-                }
-            }
-            // Dirichlet form on the cell: (p^2 + pq + q^2 + r^2 + rs + s^2) / 3 with
-            // p = v_b - v_a, q = v_c - v_d (x differences), r = v_d - v_a, s = v_c - v_b.
-            float quu = 0.f, qud = 0.f, qdd = 0.f;
-            const float4 Ua = su[pa], Ub = su[pb], Uc = su[pc], Ud = su[pd];
-#pragma unroll
-            for (int ch = 0; ch < 2; ch++) {
-                // u differences from the hi and lo parts separately (the stiffness
-                // terms are small differences of values of several grid units)
-                float up = ch ? (Ub.y - Ua.y) + (Ub.w - Ua.w) : (Ub.x - Ua.x) + (Ub.z - Ua.z);
-                float uq = ch ? (Uc.y - Ud.y) + (Uc.w - Ud.w) : (Uc.x - Ud.x) + (Uc.z - Ud.z);
-                float ur = ch ? (Ud.y - Ua.y) + (Ud.w - Ua.w) : (Ud.x - Ua.x) + (Ud.z - Ua.z);
-                float us = ch ? (Uc.y - Ub.y) + (Uc.w - Ub.w) : (Uc.x - Ub.x) + (Uc.z - Ub.z);
-                float va = ch ? sd[pa].y : sd[pa].x, vb = ch ? sd[pb].y : sd[pb].x;
-                float vc = ch ? sd[pc].y : sd[pc].x, vd = ch ? sd[pd].y : sd[pd].x;
-                float dp = vb - va, dq = vc - vd, dr = vd - va, ds = vc - vb;
-                quu += up * up + up * uq + uq * uq + ur * ur + ur * us + us * us;
-                qud += up * dp + 0.5f * (up * dq + uq * dp) + uq * dq + ur * dr + 0.5f * (ur * ds + us * dr) + us * ds;
-                qdd += dp * dp + dp * dq + dq * dq + dr * dr + dr * ds + ds * ds;
-            }
-            acc[3 * JM + 0] += quu * (1.f / 3.f);
-            acc[3 * JM + 1] += qud * (1.f / 3.f);
-            acc[3 * JM + 2] += qdd * (1.f / 3.f);
-        }
-        const int nused = start ? 3 : 3 * J;
-#pragma unroll
-        for (int k = 0; k < NACC; k++) {
-            bool used = (k >= 3 * JM) || (k < nused);
-            if (used) {
-                float v = warp_sum(acc[k]);
-                if (lx == 0) red[ly][k] = v;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < PT_STRIDE) {
-            int k = threadIdx.x;
-            // map to the fixed partial layout: trials [0, 3 MAXT), Q terms at 3 MAXT
-            int src = k < 3 * REG_MAX_TRIALS ? k : 3 * JM + (k - 3 * REG_MAX_TRIALS);
-            bool used = (k >= 3 * REG_MAX_TRIALS) || (k < nused);
-            double tot = 0.0;
-            if (used) {
-#pragma unroll
-                for (int w = 0; w < REG_THREADS / 32; w++) tot += red[w][src];
-            }
-            b.partT[(int64_t)item * PT_STRIDE + k] = tot;
+            for (int k = 0; k < PT_STRIDE; k++) v[k] = 0.f;
+            steps_tile<BF16, JM>(s, Lv, g, v);
+            write_partials<JM>(b, item, v, 3 * min(s.ntr, JM), lane);
         }
     }
 }
+
 // ---------------------------------------------------------------------------
 // C: per-operator FP64 reduction and the Armijo state machine
 // ---------------------------------------------------------------------------
@@ -1030,11 +1164,11 @@ __device__ void schedule_grad(OpState &s, const BatchDev &b, double pending)
 }  // namespace
 
 __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int o, int ph, const double *S,
-                           double slope);
+                           double slope, double qud);
 
 __global__ void __launch_bounds__(256) k_control(BatchDev b)
 {
-    __shared__ double red[8][PT_STRIDE + 1];
+    __shared__ double red[8][PT_STRIDE + 2];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int n_ops = b.ctr[0];
     // grid-stride over ops: one block per op, the block reduces the op's tile
@@ -1072,9 +1206,12 @@ __global__ void __launch_bounds__(256) k_control(BatchDev b)
 #pragma unroll
         for (int k = 0; k < PT_STRIDE; k++) S[k] += p[k];
     }
-    double slope = 0.0;
+    double slope = 0.0, qud = 0.0;
     if (ph == PH_GRAD) {
-        for (int it = s.g_begin + threadIdx.x; it < s.g_end; it += blockDim.x) slope += b.partG[it];
+        for (int it = s.g_begin + threadIdx.x; it < s.g_end; it += blockDim.x) {
+            slope += b.partG[(int64_t)it * PG_STRIDE];
+            qud += b.partG[(int64_t)it * PG_STRIDE + 1];
+        }
     }
 #pragma unroll
     for (int k = 0; k < PT_STRIDE; k++) {
@@ -1082,16 +1219,22 @@ __global__ void __launch_bounds__(256) k_control(BatchDev b)
         if (lane == 0) red[wid][k] = v;
     }
     slope = warp_sum_d(slope);
-    if (lane == 0) red[wid][PT_STRIDE] = slope;
+    qud = warp_sum_d(qud);
+    if (lane == 0) {
+        red[wid][PT_STRIDE] = slope;
+        red[wid][PT_STRIDE + 1] = qud;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k <= PT_STRIDE; k++) {
+        for (int k = 0; k < PT_STRIDE + 2; k++) {
             double v = 0.0;
             for (int w = 0; w < 8; w++) v += red[w][k];
-            if (k < PT_STRIDE) S[k] = v; else slope = v;
+            if (k < PT_STRIDE) S[k] = v;
+            else if (k == PT_STRIDE) slope = v;
+            else qud = v;
         }
-        control_op(b, s, op, o, ph, S, slope);
+        control_op(b, s, op, o, ph, S, slope, qud);
     }
     __syncthreads();
     }
@@ -1099,11 +1242,17 @@ __global__ void __launch_bounds__(256) k_control(BatchDev b)
 
 // The Armijo state machine of one operator after a step (thread 0 of its block).
 __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int o, int ph, const double *S,
-                           double slope)
+                           double slope, double qud)
 {
     const LevelDesc &Lv = op.lv[s.lvl];
     const double h2 = Lv.h2d;
-    const double Qud = S[3 * REG_MAX_TRIALS + 1], Qdd = S[3 * REG_MAX_TRIALS + 2];
+    if (ph == PH_GRAD) {
+        // the Dirichlet forms of the new search: u^T K d from the gradient pass,
+        // d^T K d from its first trial pass
+        s.Qud = qud;
+        s.Qdd = S[3 * REG_MAX_TRIALS + 2];
+    }
+    const double Qud = s.Qud, Qdd = s.Qdd;
     if (ph == PH_START || ph == PH_PROLONG) {
         s.S1 = h2 * S[0];
         s.S2 = h2 * S[1];
@@ -1233,22 +1382,15 @@ __global__ void k_planes_to_slot(const float *__restrict__ in, int n, float2 *__
 // Host launch wrappers for the templated kernels.
 void launch_grad(int bf16, int grid, cudaStream_t st, const BatchDev &b)
 {
-    if (bf16) k_grad<true><<<grid, REG_THREADS, 0, st>>>(b);
-    else k_grad<false><<<grid, REG_THREADS, 0, st>>>(b);
+    if (bf16) k_grad<true><<<grid, REG_STRIP_THREADS, 0, st>>>(b);
+    else k_grad<false><<<grid, REG_STRIP_THREADS, 0, st>>>(b);
 }
 
 template <int JM>
 static void launch_trial_j(int bf16, int grid, cudaStream_t st, const BatchDev &b)
 {
-    constexpr int sm = trial_smem_bytes<JM>();
-    static bool init = false;
-    if (!init) {
-        cudaFuncSetAttribute(k_trial<false, JM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_trial<true, JM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        init = true;
-    }
-    if (bf16) k_trial<true, JM><<<grid, REG_THREADS, sm, st>>>(b);
-    else k_trial<false, JM><<<grid, REG_THREADS, sm, st>>>(b);
+    if (bf16) k_trial<true, JM><<<grid, REG_STRIP_THREADS, 0, st>>>(b);
+    else k_trial<false, JM><<<grid, REG_STRIP_THREADS, 0, st>>>(b);
 }
 
 // J = trials per pass; the kernel instance holds room for the next power of two.
@@ -1260,53 +1402,32 @@ void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b)
     else launch_trial_j<8>(bf16, grid, st, b);
 }
 
-int trial_blocks_per_sm(int J);
+// Resident blocks per SM of the step kernels.  The strip kernels use no shared
+// memory: they ask for the smallest carveout, which leaves the most L1 to the
+// template gathers.
+template <class K>
+static int occupancy(K kernel, int threads, int carveout)
+{
+    int occ = 0;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+    return occ;
+}
 
-// Resident blocks per SM of the step kernels (shared-memory carveout set to
-// the maximum first, so that the occupancy reflects what a launch gets).
 int step_blocks_per_sm(int which, int J)
 {
     int occ = 0;
     if (which == 0) {
-        cudaFuncSetAttribute(k_prolong, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prolong, REG_THREADS, 0);
+        occ = occupancy(k_prolong, REG_THREADS, 0);
     } else if (which == 1) {
-        cudaFuncSetAttribute(k_grad<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_grad<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_grad<false>, REG_THREADS, 0);
+        occupancy(k_grad<true>, REG_STRIP_THREADS, 0);
+        occ = occupancy(k_grad<false>, REG_STRIP_THREADS, 0);
     } else {
-        cudaFuncSetAttribute(k_trial<false, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<false, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<true, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<true, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<true, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_trial<true, 8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        // the dynamic shared memory exceeds the 48 KB default: opt in before sizing
-        cudaFuncSetAttribute(k_trial<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<1>());
-        cudaFuncSetAttribute(k_trial<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<2>());
-        cudaFuncSetAttribute(k_trial<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<4>());
-        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
-        cudaFuncSetAttribute(k_trial<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<1>());
-        cudaFuncSetAttribute(k_trial<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<2>());
-        cudaFuncSetAttribute(k_trial<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<4>());
-        cudaFuncSetAttribute(k_trial<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
-        occ = trial_blocks_per_sm(J);
+        if (J <= 1) { occupancy(k_trial<true, 1>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 1>, REG_STRIP_THREADS, 0); }
+        else if (J <= 2) { occupancy(k_trial<true, 2>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 2>, REG_STRIP_THREADS, 0); }
+        else if (J <= 4) { occupancy(k_trial<true, 4>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 4>, REG_STRIP_THREADS, 0); }
+        else { occupancy(k_trial<true, 8>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 8>, REG_STRIP_THREADS, 0); }
     }
     cudaGetLastError();
-    return occ;
-}
-
-int trial_blocks_per_sm(int J)
-{
-    int occ = 0;
-    if (J <= 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 1>, REG_THREADS, trial_smem_bytes<1>());
-    else if (J <= 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 2>, REG_THREADS, trial_smem_bytes<2>());
-    else if (J <= 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 4>, REG_THREADS, trial_smem_bytes<4>());
-    else {
-        cudaFuncSetAttribute(k_trial<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, trial_smem_bytes<8>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trial<false, 8>, REG_THREADS, trial_smem_bytes<8>());
-    }
     return occ;
 }

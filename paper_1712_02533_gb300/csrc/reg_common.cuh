@@ -6,11 +6,24 @@
 
 #define REG_MAX_LEVELS 8
 #define REG_MAX_TRIALS 8
-#define REG_TX 32        // work tile width (nodes or cells along x_0)
-#define REG_TY 32        // work tile height
+#define REG_TX 32        // prolongation block tile width (nodes along x_0)
+#define REG_TY 32        // prolongation block tile height
 #define REG_THREADS 256  // threads per step-kernel block (8 warps)
 #define REG_ROWSTEP (REG_THREADS / REG_TX)  // thread (lx, ly) handles rows ly + k REG_ROWSTEP
 #define REG_RPT (REG_TY / REG_ROWSTEP)      // rows per thread
+// Warp strips of the gradient and trial kernels: the 32 lanes of a warp hold 32
+// adjacent node columns and walk down the rows of a tile together, so that
+// vertical neighbours stay in registers and horizontal ones are a shuffle away.
+#define REG_GW 30  // gradient tile: owned node columns (lanes 1..30; lanes 0, 31 are halo)
+#define REG_CW 31  // trial tile: owned cell columns (lanes 0..30; lane 31 is the right corner)
+#define REG_STRIP_THREADS 128  // threads per block of the strip kernels (warps work independently)
+// Rows per strip tile at a level of n nodes per side (owned node rows of a
+// gradient tile, owned cell rows of a trial tile): short strips on the coarse
+// levels, where a tile's row walk is latency bound, long ones on the fine
+// levels, where the halo rows cost bandwidth.
+__host__ __device__ __forceinline__ int strip_rows(int n) { return n <= 65 ? 8 : (n <= 257 ? 16 : 32); }
+#define PT_STRIDE (3 * REG_MAX_TRIALS + 3)  // doubles per trial-tile partial record
+#define PG_STRIDE 2                         // doubles per gradient-tile partial record
 
 // Phases of the per-operator state machine.
 enum {
@@ -33,6 +46,18 @@ enum { KW_G = 0,         // gradient pass nodes
        KW_PFIN = 5,      // final write: nodes
        KW_COUNT = 6 };
 
+// State of one operator at one node of a level, read and written as two
+// 16-byte words: the displacement in grid units of the level as a float pair
+// per component (value = (x, y) + (z, w), "double-float"), the descent
+// direction d = -g / w, and the per-node weights of the current search
+// (M~ That at u, M~ R~) that the trial passes use.
+struct __align__(16) NodeRec {
+    float4 u;
+    float2 d;
+    float mt;  // 36 M~ That (integer stencil weights, unscaled)
+    float mr;  // M~ R~
+};
+
 struct LevelDesc {
     int n;            // nodes per side (2^l + 1)
     int pitch;        // row pitch in elements (float2 for U/D, scalar for images)
@@ -40,9 +65,8 @@ struct LevelDesc {
     double h2d;       // h^2 in double
     const void *R;    // normalised reference frame (mean 0, FE sigma 1) at this level
     const void *T;    // normalised template frame
-    float4 *U[2];     // displacement (grid units of this level) as a float pair per
-                      // component, value = (x, y) + (z, w) ("double-float"), double-buffered
-    float2 *D[2];     // descent direction d = -g / w (grid units)
+    const float *MR;  // M~ R~: the reference frame times the FE mass matrix (units h^2)
+    NodeRec *V[2];    // node records, double-buffered (the gradient pass reads one, writes the other)
 };
 
 struct OpDesc {
@@ -69,6 +93,7 @@ struct OpState {
     double bS1, bS2, bS3, bncc, bdE;  // last accepted trial of the search
     double btau;
     double slope;
+    double Qud, Qdd;  // Dirichlet forms u^T K d and d^T K d of the current search
     double trial_tau[REG_MAX_TRIALS];
 };
 
@@ -82,8 +107,8 @@ struct BatchDev {
     int *prefP, *prefG, *prefT;  // exclusive prefix of tile counts (n+1 entries)
     int *ctr;                    // [0] n_ops [1] nP [2] nG [3] nT [4] itemsP [5] itemsG [6] itemsT
                                  // [7] n_active [8] error flag
-    double *partG;               // per G item: slope partial
-    double *partT;               // per T item: REG_MAX_TRIALS x 4 partial sums
+    double *partG;               // per G item: slope and u^T K d partials (PG_STRIDE)
+    double *partT;               // per T item: 3 sums per step size, then 3 Dirichlet forms (PT_STRIDE)
     unsigned long long *work;    // per kernel family: nodes processed
     double *trace;               // optional Armijo trial records (7 doubles each)
     unsigned long long *trace_len;

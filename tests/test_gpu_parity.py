@@ -13,6 +13,11 @@ TOL_PX = 1e-3
 TOL_E = 1e-5
 
 
+def orc_energy(R, T, u, lam):
+    import oracle
+    return oracle.energy(R, T, u, lam)
+
+
 @pytest.fixture(scope="module")
 def reg():
     import torch
@@ -39,7 +44,7 @@ def _rand_u(n, seed, amp):
     return u + rng.uniform(-0.2, 0.2, size=u.shape)
 
 
-@pytest.mark.parametrize("side,nl", [(64, 3), (128, 3), (256, 2)])
+@pytest.mark.parametrize("side,nl", [(64, 3), (128, 3), (256, 2), (512, 2)])
 def test_energy_matches_oracle(reg, orc, syn, side, nl):
     fr = syn.series(3, 2, side, peak=10.0, spacing=10.0, sigma=2.0)
     lam = 10.0
@@ -61,7 +66,7 @@ def test_energy_matches_oracle(reg, orc, syn, side, nl):
                 assert abs(got["reg"] - parts["reg"]) <= 1e-5 * max(abs(parts["reg"]), 1e-6)
 
 
-@pytest.mark.parametrize("side,nl", [(64, 3), (128, 2)])
+@pytest.mark.parametrize("side,nl", [(64, 3), (128, 2), (512, 2)])
 def test_direction_matches_oracle(reg, orc, syn, side, nl):
     fr = syn.series(4, 2, side, peak=10.0, spacing=10.0, sigma=2.0)
     lam = 10.0
@@ -86,6 +91,37 @@ def test_direction_matches_oracle(reg, orc, syn, side, nl):
                 assert abs(slope - want_slope) <= 1e-5 * abs(want_slope), (slope, want_slope)
 
 
+@pytest.mark.parametrize("side,nl", [(128, 2), (512, 2)])
+def test_trial_pass_matches_oracle(reg, orc, syn, side, nl):
+    """One trial pass of the Armijo search: the energy changes E(u + tau d) - E(u)
+    for step sizes whose largest move spans 1e-6 to 3 grid units (moves inside a
+    cell, across cell lines, past the grid border, beyond one cell), against the
+    oracle's FP64 energies at the same u and d."""
+    fr = syn.series(6, 2, side, peak=10.0, spacing=10.0, sigma=2.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, lam=lam, trials_per_pass=8)
+    Rp, Tp = _pyramid(orc, fr[0], nl), _pyramid(orc, fr[1], nl)
+    L = int(np.log2(side))
+    moves = np.array([1e-6, 1e-4, 1e-2, 0.3, 0.7, 1.5, 3.0])
+    with reg.Series(fr, p) as s:
+        for k in range(nl):
+            n = Rp[k].shape[0]
+            h = 1.0 / (n - 1)
+            level = L - nl + 1 + k
+            for seed, amp in [(0, 0.5), (3, 2.5)]:
+                ug = _rand_u(n, seed, amp).astype(np.float32)
+                d0, _ = s.eval_direction(0, 1, level, ug)
+                taus = moves / float(np.abs(d0).max())
+                d, dE = s.eval_trials(0, 1, level, ug, taus)
+                assert np.array_equal(d, d0)
+                uo = ug.astype(np.float64) * h
+                E0, _ = orc.energy(Rp[k], Tp[k], uo, lam)
+                for j, t in enumerate(taus):
+                    E1, _ = orc.energy(Rp[k], Tp[k], uo + t * d.astype(np.float64) * h, lam)
+                    want = E1 - E0
+                    assert abs(dE[j] - want) <= 1e-4 * abs(want) + 1e-9 * abs(E0), (level, seed, moves[j], dE[j], want)
+
+
 def test_function_a_matches_oracle(reg, orc, syn):
     side, nl = 64, 3
     fr = syn.series(5, 2, side, peak=20.0, spacing=8.0, sigma=1.5, drift_sd=0.7)
@@ -104,13 +140,20 @@ def test_function_a_matches_oracle(reg, orc, syn):
     assert abs(eg["E"] - stl[-1].E) <= TOL_E * abs(stl[-1].E)
 
 
-def _assert_op_parity(gpu_u_px, orc_u_px, gtr, otr, what):
+def _assert_op_parity(gpu_u_px, orc_u_px, gtr, otr, what, R, T, lam=10.0):
     """Parity of one full operator application.  Either the displacement fields
     agree to TOL_PX everywhere, or the two Armijo decision sequences agree up to
     a decision that the oracle itself takes with a margin below 1e-3 (relative):
     from such a decision on, rounding at the 1e-7 level legitimately sends the
     iteration elsewhere (the same happens to the oracle under 1e-7 input
-    perturbations, see test_oracle_sensitivity.py)."""
+    perturbations, see test_oracle_sensitivity.py).  When every decision
+    agrees, the fields may still differ at the few nodes that the iteration
+    drives onto a cell line of the bilinear interpolant: the template's
+    derivative jumps there, so which side such a node ends on is decided at the
+    rounding level (in FP32 on the GPU, FP64 in the oracle).  Those nodes must
+    stay rare (99.5% of the nodes within TOL_PX), and the GPU's field must be no
+    worse a minimiser: the oracle's FP64 energy at it may exceed the energy at
+    the oracle's own field by at most 1e-6 (relative)."""
     err = float(np.abs(gpu_u_px - orc_u_px).max())
     if err <= TOL_PX:
         return err
@@ -126,11 +169,12 @@ def _assert_op_parity(gpu_u_px, orc_u_px, gtr, otr, what):
             spread = (abs(a[3] - b[3]) + abs(a[4] - b[4])) / abs(b[4])
             assert margin < spread + 1e-3, (what, "decision differs at a non-marginal test", k, a, b, err)
             return err
-    # every decision agrees: the remaining differences come from nodes that sit
-    # on different sides of a cell line of the bilinear interpolant (the
-    # derivative jumps there) and stay local
+    side = gpu_u_px.shape[-1] - 1
     frac = float(np.mean(np.abs(gpu_u_px - orc_u_px) <= TOL_PX))
-    assert frac >= 0.999 and err <= 0.05, (what, "fields differ although every decision agrees", err, frac)
+    e_gpu, _ = orc_energy(R, T, gpu_u_px.astype(np.float64) / side, lam)
+    e_orc, _ = orc_energy(R, T, np.asarray(orc_u_px, np.float64) / side, lam)
+    assert frac >= 0.995 and e_gpu - e_orc <= 1e-6 * abs(e_orc), (
+        what, "fields differ although every decision agrees", err, frac, e_gpu, e_orc)
     return err
 
 
@@ -157,7 +201,7 @@ def test_config1_operators_match_oracle(reg, orc, syn):
     for e in range(n):
         with orc.trace() as t:
             u, status, stl = orc.register(g[e], g[e + 1], op)
-        err = _assert_op_parity(got[e], u * 64, gtr[e], t.rows, f"A({e},{e + 1})")
+        err = _assert_op_parity(got[e], u * 64, gtr[e], t.rows, f"A({e},{e + 1})", g[e], g[e + 1])
         n_exact += err <= TOL_PX
     assert n_exact >= n - 1
 
@@ -182,7 +226,7 @@ def test_config1_scan_operators_match_oracle(reg, orc, syn):
             gtr = s.get_trace()[:, 1:]
             with orc.trace() as t:
                 out, _, _, _, _ = orc.apply_batch([dict(R=g[0], T=g[k + 1], left=acc, right=A[k])], op)
-            _assert_op_parity(got, out[0] * 64, gtr, t.rows, f"B(0,{k},{k + 1})")
+            _assert_op_parity(got, out[0] * 64, gtr, t.rows, f"B(0,{k},{k + 1})", g[0], g[k + 1])
             acc = got.astype(np.float64) / 64
 
 
@@ -223,9 +267,10 @@ def test_config2_sampled_operators_match_oracle(reg, orc, syn):
         gtr = _gpu_traces_by_op(s.get_trace(), n)
         for e in (0, 77):
             got = s.get_slot(e)[0]
+            R, T = orc.embed(fr[e]), orc.embed(fr[e + 1])
             with orc.trace() as t:
-                u, _, _ = orc.register(orc.embed(fr[e]), orc.embed(fr[e + 1]), op)
-            _assert_op_parity(got, u * side, gtr[e], t.rows, f"A({e},{e + 1}) 512^2")
+                u, _, _ = orc.register(R, T, op)
+            _assert_op_parity(got, u * side, gtr[e], t.rows, f"A({e},{e + 1}) 512^2", R, T)
         left = s.get_slot(0)[0].astype(np.float64) / side
         right = s.get_slot(1)[0].astype(np.float64) / side
         s.set_trace(1 << 22)
@@ -235,7 +280,7 @@ def test_config2_sampled_operators_match_oracle(reg, orc, syn):
     # B given the GPU's operands on both sides
     with orc.trace() as t:
         out, _, _, _, _ = orc.apply_batch([dict(R=orc.embed(fr[0]), T=orc.embed(fr[2]), left=left, right=right)], op)
-    _assert_op_parity(got, out[0] * side, gtr2, t.rows, "B(0,1,2) 512^2")
+    _assert_op_parity(got, out[0] * side, gtr2, t.rows, "B(0,1,2) 512^2", orc.embed(fr[0]), orc.embed(fr[2]))
 
 
 def test_identical_frames_give_zero_displacement(reg, syn):
