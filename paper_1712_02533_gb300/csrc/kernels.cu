@@ -13,6 +13,8 @@
 // stiffness forms); per-cell values are float, per-warp and per-tile sums
 // float, and the per-operator sum over tiles is double (the global energy and
 // normalisation reductions that the Armijo test compares).
+#include <algorithm>
+
 #include "reg_common.cuh"
 
 namespace {
@@ -956,22 +958,97 @@ __device__ __forceinline__ void start_tile(const OpState &s, const LevelDesc &Lv
     v[3] = quu * (1.0 / 3.0);
 }
 
-// Trial sums of one strip tile for the step sizes tau_0..tau_{J-1}.  The node
-// record of the next row is loaded while the current row is worked on.
+// Shared memory of one warp in the trial pass: the exact changes of the
+// nodes of the previous and the current row that left their cell, and the
+// per-lane sums over those nodes and their cells, for every step size.
+template <int JM>
+struct TrialScratch {
+    float dl[2][JM][32];  // delta_j of such nodes, rows alternating
+    float sn[3][JM][32];  // node sums: omega delta, 36 M~That delta, M~R~ delta
+    float sq[JM][32];     // cell sums of 18 delta^T M~_e delta
+};
+
+// Exact change of the interpolant at one node for every step size, for a
+// node whose largest move leaves its cell (or whose base point lies outside
+// the grid): the moves that stay in the cell take the polynomial of the base
+// cell, the others the texel patch, or a fresh sample for moves of a cell or
+// more (whose rounding, ~1e-7 of That, is small against such a change).  The
+// changes go to the warp's scratch row and, for an owned node, into its node
+// sums.
 template <bool BF16, int JM>
-__device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, float *v)
+__device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const float *tau, int J, int c, int r,
+                                                  float4 u, float4 dm, float w, bool own, TrialScratch<JM> &sh,
+                                                  int cur, int lane)
+{
+    const int n = Lv.n, pitch = Lv.pitch;
+    Patch P;
+    make_patch<BF16>(P, Lv.T, n, pitch, c, r, u, dm.x, dm.y);
+    const bool cl = P.clx || P.cly;
+    // dThat/dx at a_y, dThat/dy at a_x and the mixed derivative of the base cell
+    const float sy = P.v0[0] + P.ax * (P.v0[1] - P.v0[0]);
+    const float A = dm.x * P.s0x + dm.y * sy;
+    const float B = dm.x * dm.y * (P.v0[1] - P.v0[0]);
+#pragma unroll
+    for (int j = 0; j < JM; j++) {
+        if (j < J) {
+            const float ex = tau[j] * dm.x, ey = tau[j] * dm.y;
+            const float ax1 = P.ax + ex, ay1 = P.ay + ey;
+            float del;
+            if (!cl && ax1 >= 0.f && ax1 < 1.f && ay1 >= 0.f && ay1 < 1.f) {
+                del = tau[j] * (A + tau[j] * B);
+            } else if (!patch_delta(P, n, ex, ey, del)) {
+                Texel4 q;
+                locate(n, c, r, (u.x + u.z) + ex, (u.y + u.w) + ey, q.jx, q.jy, q.ax, q.ay, q.clx, q.cly);
+                fetch<BF16>(q, Lv.T, pitch);
+                del = bil(q) - P.t0;
+            }
+            sh.dl[cur][j][lane] = del;
+            if (own) {
+                sh.sn[0][j][lane] += w * del;
+                sh.sn[1][j][lane] += dm.z * del;
+                sh.sn[2][j][lane] += dm.w * del;
+            }
+        }
+    }
+}
+
+// Trial sums of one strip tile for the step sizes tau_0..tau_{J-1}.  All step
+// sizes move a node along the same ray u + tau d, and while the moved point
+// stays in the base cell the change of the bilinear interpolant is exactly
+//   delta(tau) = tau A + tau^2 B,  A = d . grad That (at the base point),
+//   B = d_x d_y (t00 - t01 - t10 + t11),
+// so the sums over such nodes and cells are polynomials in tau of per-node
+// moments (sum omega A, sum omega B, ...; 18 A^T M~ A, 18 A^T M~ B, 18 B^T M~ B
+// per cell) that are gathered once for all step sizes.  A node whose largest
+// move leaves the cell, and every cell touching one, is summed exactly for each
+// step size (shared memory).  The node record of the next row is loaded while
+// the current row is worked on.
+template <bool BF16, int JM>
+__device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, float *v,
+                                           TrialScratch<JM> &sh, int lane)
 {
     const unsigned FULL = 0xffffffffu;
     const int J = min(s.ntr, JM);
     const bool withQ = (s.phase == PH_GRAD);
     const float4 *V = reinterpret_cast<const float4 *>(Lv.V[s.cur]);
-    float tau[JM], aS1[JM], aS2[JM], aS3[JM], pT[JM], pTR[JM];
+    float tau[JM];
+    float tmax = 0.f;
 #pragma unroll
     for (int j = 0; j < JM; j++) {
         tau[j] = (j < J) ? (float)s.trial_tau[j] : 0.f;
-        aS1[j] = aS2[j] = aS3[j] = pT[j] = pTR[j] = 0.f;
+        tmax = fmaxf(tmax, tau[j]);
+#pragma unroll
+        for (int k = 0; k < 3; k++) sh.sn[k][j][lane] = 0.f;
+        sh.sq[j][lane] = 0.f;
     }
+    // node moments (owned nodes that stay in their cell) and cell moments
+    float mWA = 0.f, mWB = 0.f, mTA = 0.f, mTB = 0.f, mRA = 0.f, mRB = 0.f;
+    float qaa = 0.f, qab = 0.f, qbb = 0.f;
+    // the previous row: A, B here and at the right neighbour, its row forms
+    float Ap = 0.f, ApR = 0.f, Bp = 0.f, BpR = 0.f, PaaP = 0.f, PabP = 0.f, PbbP = 0.f;
+    bool slowP = false, slowPR = false;
     float qdd = 0.f, pdx = 0.f, pdy = 0.f, dPx = 0.f, dPy = 0.f;
+    int cur = 0;
     float4 nu = make_float4(0.f, 0.f, 0.f, 0.f), ndm = nu;  // record of the next row
     if (g.colIn) {
         const int64_t idx = (int64_t)g.r0 * g.pitch + g.c;
@@ -985,59 +1062,69 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
             nu = V[2 * idx];
             ndm = V[2 * idx + 1];
         }
-        float del[JM];
-#pragma unroll
-        for (int j = 0; j < JM; j++) del[j] = 0.f;
+        const bool own = g.nodeCol && (r < g.r0 + g.h || r == g.n - 1);
+        const float w = g.wx * ((r == 0 || r == g.n - 1) ? 0.5f : 1.f);
+        float A = 0.f, B = 0.f;
+        bool slow = false;
         if (g.colIn) {
-            Patch P;
-            make_patch<BF16>(P, Lv.T, g.n, g.pitch, g.c, r, u, dm.x, dm.y);
-            unsigned fresh = 0;
-#pragma unroll
-            for (int j = 0; j < JM; j++)
-                if (j < J && !patch_delta(P, g.n, tau[j] * dm.x, tau[j] * dm.y, del[j])) fresh |= 1u << j;
-            // moves of a cell or more: a fresh sample at the new point, whose
-            // rounding (~1e-7 of That) is small against such a change
-            while (fresh) {
-                const int j = __ffs(fresh) - 1;
-                fresh &= fresh - 1;
-                float tj = 0.f;
-#pragma unroll
-                for (int k = 0; k < JM; k++)
-                    if (k == j) tj = tau[k];
-                Texel4 w;
-                locate(g.n, g.c, r, (u.x + u.z) + tj * dm.x, (u.y + u.w) + tj * dm.y, w.jx, w.jy, w.ax, w.ay, w.clx,
-                       w.cly);
-                fetch<BF16>(w, Lv.T, g.pitch);
-                const float x = bil(w) - P.t0;
-#pragma unroll
-                for (int k = 0; k < JM; k++)
-                    if (k == j) del[k] = x;
-            }
-        }
-        // aS2 is kept in units of 1/18 (integer weights; one division at the end)
-        if (g.nodeCol && (r < g.r0 + g.h || r == g.n - 1)) {
-            const float w = g.wx * ((r == 0 || r == g.n - 1) ? 0.5f : 1.f), mt36 = dm.z;
-#pragma unroll
-            for (int j = 0; j < JM; j++) {
-                aS1[j] += w * del[j];
-                aS2[j] += mt36 * del[j];
-                aS3[j] += dm.w * del[j];
-            }
-        }
-        const float wrow2 = (float)(2 * ((r > g.r0) + (r < g.rEnd)));
-#pragma unroll
-        for (int j = 0; j < JM; j++) {
-            if (j < J) {
-                const float dR = __shfl_down_sync(FULL, del[j], 1);
-                if (g.cellCol) {
-                    float q2 = wrow2 * pform(del[j], dR);
-                    if (r > g.r0) q2 += pT[j] * (2.f * del[j] + dR) + pTR[j] * (del[j] + 2.f * dR);
-                    aS2[j] += q2;
+            Texel4 q;
+            int ix, iy;
+            df_split(u.x, u.z, ix, q.ax);
+            df_split(u.y, u.w, iy, q.ay);
+            q.jx = g.c + ix;
+            q.jy = r + iy;
+            // a base point outside the grid, or a largest move that leaves the
+            // cell (then every smaller one along the ray stays inside)
+            const float ax1 = q.ax + tmax * dm.x, ay1 = q.ay + tmax * dm.y;
+            slow = q.jx < 0 || q.jx > g.n - 2 || q.jy < 0 || q.jy > g.n - 2 || !(ax1 >= 0.f && ax1 < 1.f) ||
+                   !(ay1 >= 0.f && ay1 < 1.f);
+            if (!slow) {
+                fetch<BF16>(q, Lv.T, g.pitch);
+                const float dtx = q.t01 - q.t00, dtx1 = q.t11 - q.t10;
+                const float sx = dtx + q.ay * (dtx1 - dtx);                            // dThat/dx
+                const float sy = (q.t10 - q.t00) + q.ax * ((q.t11 - q.t01) - (q.t10 - q.t00));  // dThat/dy
+                A = dm.x * sx + dm.y * sy;
+                B = dm.x * dm.y * (dtx1 - dtx);
+                if (own) {
+                    mWA += w * A; mWB += w * B;
+                    mTA += dm.z * A; mTB += dm.z * B;
+                    mRA += dm.w * A; mRB += dm.w * B;
                 }
-                pT[j] = del[j];
-                pTR[j] = dR;
             }
         }
+        __syncwarp();
+        if (slow) node_deltas_exact<BF16, JM>(Lv, tau, J, g.c, r, u, dm, w, own, sh, cur, lane);
+        __syncwarp();
+        // cells between rows r-1 and r, columns c and c+1
+        const float AR = __shfl_down_sync(FULL, A, 1), BR = __shfl_down_sync(FULL, B, 1);
+        const bool slowR = __shfl_down_sync(FULL, slow, 1);
+        const float Paa = pform(A, AR), Pbb = pform(B, BR);
+        const float Pab = A * B + AR * BR + 0.5f * (A * BR + AR * B);
+        if (g.cellCol && r > g.r0) {
+            if (!(slowP || slowPR || slow || slowR)) {
+                const float ha = 2.f * A + AR, haR = A + 2.f * AR, hb = 2.f * B + BR, hbR = B + 2.f * BR;
+                qaa += 2.f * (PaaP + Paa) + Ap * ha + ApR * haR;
+                qbb += 2.f * (PbbP + Pbb) + Bp * hb + BpR * hbR;
+                qab += 2.f * (PabP + Pab) + 0.5f * (Ap * hb + ApR * hbR + Bp * ha + BpR * haR);
+            } else {
+#pragma unroll
+                for (int j = 0; j < JM; j++) {
+                    if (j < J) {
+                        const float t = tau[j];
+                        const float tl = slowP ? sh.dl[cur ^ 1][j][lane] : t * (Ap + t * Bp);
+                        const float tr = slowPR ? sh.dl[cur ^ 1][j][lane + 1] : t * (ApR + t * BpR);
+                        const float bl = slow ? sh.dl[cur][j][lane] : t * (A + t * B);
+                        const float br = slowR ? sh.dl[cur][j][lane + 1] : t * (AR + t * BR);
+                        sh.sq[j][lane] += 2.f * (pform(tl, tr) + pform(bl, br)) + tl * (2.f * bl + br) +
+                                          tr * (bl + 2.f * br);
+                    }
+                }
+            }
+        }
+        Ap = A; ApR = AR; Bp = B; BpR = BR;
+        PaaP = Paa; PabP = Pab; PbbP = Pbb;
+        slowP = slow; slowPR = slowR;
+        cur ^= 1;
         if (withQ) {
             const float dRx = __shfl_down_sync(FULL, dm.x, 1), dRy = __shfl_down_sync(FULL, dm.y, 1);
             const float qx = dRx - dm.x, qy = dRy - dm.y;
@@ -1047,11 +1134,14 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
             pdx = qx; pdy = qy; dPx = dm.x; dPy = dm.y;
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int j = 0; j < JM; j++) {
-        v[3 * j] = aS1[j];
-        v[3 * j + 1] = aS2[j] / 18.f;
-        v[3 * j + 2] = aS3[j];
+        const float t = tau[j];
+        v[3 * j] = t * (mWA + t * mWB) + sh.sn[0][j][lane];
+        v[3 * j + 1] = (t * (mTA + t * mTB) + t * t * (qaa + t * (2.f * qab + t * qbb)) + sh.sn[1][j][lane] +
+                        sh.sq[j][lane]) / 18.f;
+        v[3 * j + 2] = t * (mRA + t * mRB) + sh.sn[2][j][lane];
     }
     v[3 * REG_MAX_TRIALS + 2] = qdd / 3.f;
 }
@@ -1074,8 +1164,9 @@ __device__ __forceinline__ void write_partials(const BatchDev &b, int item, cons
 }  // namespace
 
 template <bool BF16, int JM>
-__global__ void __launch_bounds__(REG_STRIP_THREADS, 6) k_trial(BatchDev b)
+__global__ void __launch_bounds__(REG_STRIP_THREADS, 5) k_trial(BatchDev b)
 {
+    __shared__ TrialScratch<JM> scratch[REG_STRIP_THREADS / 32];
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (REG_STRIP_THREADS / 32);
     const int nent = b.ctr[3], items = b.ctr[6];
@@ -1101,7 +1192,7 @@ __global__ void __launch_bounds__(REG_STRIP_THREADS, 6) k_trial(BatchDev b)
             float v[PT_STRIDE];
 #pragma unroll
             for (int k = 0; k < PT_STRIDE; k++) v[k] = 0.f;
-            steps_tile<BF16, JM>(s, Lv, g, v);
+            steps_tile<BF16, JM>(s, Lv, g, v, scratch[threadIdx.x >> 5], lane);
             write_partials<JM>(b, item, v, 3 * min(s.ntr, JM), lane);
         }
     }
@@ -1402,13 +1493,25 @@ void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b)
     else launch_trial_j<8>(bf16, grid, st, b);
 }
 
-// Resident blocks per SM of the step kernels.  The strip kernels use no shared
-// memory: they ask for the smallest carveout, which leaves the most L1 to the
-// template gathers.
+// Resident blocks per SM of the step kernels.  Each asks for the smallest
+// shared-memory carveout that still holds its register-limited number of
+// blocks, which leaves the rest of the on-chip memory to L1 (the template
+// gathers).
 template <class K>
 static int occupancy(K kernel, int threads, int carveout)
 {
     int occ = 0;
+    if (carveout < 0) {
+        cudaFuncAttributes fa;
+        int dev = 0, max_smem = 0, regs_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaFuncGetAttributes(&fa, kernel);
+        const int by_regs = fa.numRegs > 0 ? regs_sm / (fa.numRegs * threads) : 1;
+        const size_t need = (size_t)by_regs * (fa.sharedSizeBytes + 1024);  // 1 KB reserved per block
+        carveout = max_smem > 0 ? (int)std::min<size_t>(100, (need * 100 + max_smem - 1) / max_smem) : 100;
+    }
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
     return occ;
@@ -1423,10 +1526,10 @@ int step_blocks_per_sm(int which, int J)
         occupancy(k_grad<true>, REG_STRIP_THREADS, 0);
         occ = occupancy(k_grad<false>, REG_STRIP_THREADS, 0);
     } else {
-        if (J <= 1) { occupancy(k_trial<true, 1>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 1>, REG_STRIP_THREADS, 0); }
-        else if (J <= 2) { occupancy(k_trial<true, 2>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 2>, REG_STRIP_THREADS, 0); }
-        else if (J <= 4) { occupancy(k_trial<true, 4>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 4>, REG_STRIP_THREADS, 0); }
-        else { occupancy(k_trial<true, 8>, REG_STRIP_THREADS, 0); occ = occupancy(k_trial<false, 8>, REG_STRIP_THREADS, 0); }
+        if (J <= 1) { occupancy(k_trial<true, 1>, REG_STRIP_THREADS, -1); occ = occupancy(k_trial<false, 1>, REG_STRIP_THREADS, -1); }
+        else if (J <= 2) { occupancy(k_trial<true, 2>, REG_STRIP_THREADS, -1); occ = occupancy(k_trial<false, 2>, REG_STRIP_THREADS, -1); }
+        else if (J <= 4) { occupancy(k_trial<true, 4>, REG_STRIP_THREADS, -1); occ = occupancy(k_trial<false, 4>, REG_STRIP_THREADS, -1); }
+        else { occupancy(k_trial<true, 8>, REG_STRIP_THREADS, -1); occ = occupancy(k_trial<false, 8>, REG_STRIP_THREADS, -1); }
     }
     cudaGetLastError();
     return occ;
