@@ -401,11 +401,11 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
     k_plan<<<1, 1024, 0, s->stream>>>(b);
     CK(cudaGetLastError());
     s->fam[F_SETUP].launches += 4 + nl;
-    RET(build_graph(s));
+    const bool prof = (s->p.flags & REG_FLAG_PROFILE) && s->ev_ok;
+    if (!prof) RET(build_graph(s));  // profiling launches the same kernels directly
     int max_steps = s->p.max_steps > 0 ? s->p.max_steps
                                        : nl * (s->p.iter_max * (2 + 48 / std::max(1, s->p.trials_per_pass)) + 4) + 64;
     int steps = 0;
-    const bool prof = (s->p.flags & REG_FLAG_PROFILE) && s->ev_ok;
     for (;;) {
         if (prof) {
             // profiling: the same step kernels launched one by one between events
