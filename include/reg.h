@@ -223,7 +223,9 @@ reg_status reg_schedule(reg_scan_kind kind, int32_t n, int32_t chunks, reg_scan_
 
 /* Per-kernel-family statistics accumulated since creation (or the last reset):
  * launches, device time (ms, CUDA events, only with REG_FLAG_PROFILE) and
- * algorithmic bytes (counted on the device per processed node). */
+ * algorithmic bytes (counted on the device per processed node).  One more
+ * record, "trial_exact_nodes", counts in `items` the trial-pass nodes whose
+ * largest move left their cell (the exact path of the trial kernel). */
 typedef struct reg_kernel_stats {
     char name[24];
     int64_t launches;

@@ -1146,7 +1146,13 @@ reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t b
     unsigned long long w[16];
     CK(cudaMemcpyAsync(w, s->d_work, sizeof(w), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    *n_out = NFAM;
+    *n_out = NFAM + 1;
+    if (buf_len > NFAM) {
+        // nodes of trial passes that took the exact path (largest move leaves the cell)
+        memset(&buf[NFAM], 0, sizeof(reg_kernel_stats));
+        snprintf(buf[NFAM].name, sizeof(buf[NFAM].name), "trial_exact_nodes");
+        buf[NFAM].items = (int64_t)w[KW_TEXACT];
+    }
     for (int f = 0; f < NFAM && f < buf_len; f++) {
         reg_kernel_stats &k = buf[f];
         memset(&k, 0, sizeof(k));
@@ -1158,7 +1164,7 @@ reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t b
         // per node: u 16 B (float pair per component), d 8 B, R and T one image value each
         if (f == F_G) {
             k.items = (int64_t)w[KW_G];
-            // reads u, d, M~R~, the template; writes u, d, M~That
+            // needed fields: reads u, d, M~R~, the template; writes u, d, 36 M~That
             k.bytes = w[KW_G] * (16.0 + 8.0 + 4.0 + img + 16.0 + 8.0 + 4.0);
         } else if (f == F_T) {
             k.items = (int64_t)(w[KW_T] + w[KW_TSTART]);

@@ -614,20 +614,34 @@ __global__ void __launch_bounds__(REG_STRIP_THREADS, 8) k_grad(BatchDev b)
         float dyMx = 0.f, dyMy = 0.f, gxM = 0.f, gyM = 0.f, mrM = 0.f;
         float4 uM = make_float4(0.f, 0.f, 0.f, 0.f);
         float slope = 0.f, qud = 0.f;
+        // the record and M~R~ of the next row are loaded while a row is worked on
+        float4 nu = make_float4(0.f, 0.f, 0.f, 0.f), nd = nu;
+        float nmr = 0.f;
+        if (colIn && r0 - 1 >= 0) {
+            const int64_t idx = (int64_t)(r0 - 1) * pitch + c;
+            const float4 *rec = reinterpret_cast<const float4 *>(Vs + idx);
+            nu = rec[0];
+            nd = rec[1];
+            nmr = Lv.MR[idx];
+        }
         for (int r = r0 - 1; r <= rLast + 1; r++) {
             const bool in = colIn && r >= 0 && r < n;
-            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            float tv = 0.f, gx = 0.f, gy = 0.f, mr = 0.f;
-            if (in) {
-                const int64_t idx = (int64_t)r * pitch + c;
+            float4 u = nu;
+            const float2 dp = make_float2(nd.x, nd.y);
+            const float mr = nmr;
+            if (colIn && r + 1 < n && r + 1 <= rLast + 1) {
+                const int64_t idx = (int64_t)(r + 1) * pitch + c;
                 const float4 *rec = reinterpret_cast<const float4 *>(Vs + idx);
-                u = rec[0];
-                if (tau != 0.f) {
-                    const float4 dm = rec[1];
-                    u = df_add2(u, tau * dm.x, tau * dm.y);
-                }
-                mr = Lv.MR[idx];
+                nu = rec[0];
+                nd = rec[1];
+                nmr = Lv.MR[idx];
+            }
+            float tv = 0.f, gx = 0.f, gy = 0.f;
+            if (in) {
+                if (tau != 0.f) u = df_add2(u, tau * dp.x, tau * dp.y);
                 tv = sample_df<BF16, true>(Lv.T, n, pitch, c, r, u, &gx, &gy);
+            } else {
+                u = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             // u(r, c+1) - u(r, c) and u(r, c) - u(r-1, c), each from the hi and
             // lo parts (the stiffness terms are small differences of values of
@@ -1025,7 +1039,7 @@ __device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const flo
 // the current row is worked on.
 template <bool BF16, int JM>
 __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, float *v,
-                                           TrialScratch<JM> &sh, int lane)
+                                           TrialScratch<JM> &sh, int lane, unsigned &nexact)
 {
     const unsigned FULL = 0xffffffffu;
     const int J = min(s.ntr, JM);
@@ -1092,7 +1106,7 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
                 }
             }
         }
-        __syncwarp();
+        nexact += __popc(__ballot_sync(FULL, slow));
         if (slow) node_deltas_exact<BF16, JM>(Lv, tau, J, g.c, r, u, dm, w, own, sh, cur, lane);
         __syncwarp();
         // cells between rows r-1 and r, columns c and c+1
@@ -1192,8 +1206,10 @@ __global__ void __launch_bounds__(REG_STRIP_THREADS, 5) k_trial(BatchDev b)
             float v[PT_STRIDE];
 #pragma unroll
             for (int k = 0; k < PT_STRIDE; k++) v[k] = 0.f;
-            steps_tile<BF16, JM>(s, Lv, g, v, scratch[threadIdx.x >> 5], lane);
+            unsigned nexact = 0;
+            steps_tile<BF16, JM>(s, Lv, g, v, scratch[threadIdx.x >> 5], lane, nexact);
             write_partials<JM>(b, item, v, 3 * min(s.ntr, JM), lane);
+            if (lane == 0 && nexact) atomicAdd(&b.work[KW_TEXACT], (unsigned long long)nexact);
         }
     }
 }

@@ -44,7 +44,8 @@ enum { KW_G = 0,         // gradient pass nodes
        KW_TSAMPLES = 3,  // trial samples (nodes x step sizes)
        KW_PPROL = 4,     // prolongation: fine nodes written
        KW_PFIN = 5,      // final write: nodes
-       KW_COUNT = 6 };
+       KW_TEXACT = 6,    // trial nodes whose largest move leaves the cell (exact path)
+       KW_COUNT = 7 };
 
 // State of one operator at one node of a level, read and written as two
 // 16-byte words: the displacement in grid units of the level as a float pair
