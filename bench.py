@@ -133,6 +133,29 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed(seed, rank):
+    """Seed of the series that rank registers: every rank works on its own series
+    (independent problems, no collective on the data path)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over all ranks (the job takes as long as its slowest
+    rank); x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
 def cpu_baseline(frames, cfg, n_ops=None, budget_s=30.0):
     """The FP64 oracle as it stands, on a bounded sample: A(f_e, f_{e+1}) ops of
     the same series and parameters, run in parallel over the host cores."""
@@ -202,7 +225,7 @@ def main():
 
     # each rank registers its own series (independent problems)
     t0 = time.time()
-    frames = synth.series(cfg["seed"] + 1000 * rank, cfg["n_frames"], cfg["side"], spacing=cfg["spacing"],
+    frames = synth.series(rank_seed(cfg["seed"], rank), cfg["n_frames"], cfg["side"], spacing=cfg["spacing"],
                           sigma=cfg["sigma"], peak=cfg["peak"], drift_sd=cfg["drift_sd"], dist_amp=cfg["dist_amp"])
     gen_s = time.time() - t0
     params = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"],
@@ -241,12 +264,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stats = s.kernel_stats()
     ops_per_step = reports[-1]["ops"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_step = ms / a.steps
-    value = world * ops_per_step / (ms_step / 1e3)
+    value = job_rate(world, ops_per_step, ms_step / 1e3)
 
     # dominant kernel and its roofline
     peak, peak_kind = _peaks()
@@ -278,8 +298,8 @@ def main():
                 r2 = s2.prefix_scan(kind, a.chunks, reg.KOGGE_STONE)
                 s2.get_deformations(out=out)
         barrier()
-        e2e_s = (time.time() - t) / e2e_steps
-        e2e = {"value": world * r2["ops"] / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks((time.time() - t) / e2e_steps, world, dev)
+        e2e = {"value": job_rate(world, r2["ops"], e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(out.numel() * 4),
                "ms_per_step": round(e2e_s * 1e3, 2)}
     s.close()
