@@ -127,10 +127,12 @@ typedef enum reg_scan_kind {
 } reg_scan_kind;
 
 /* Create a handle holding `n_series` series (one segmented scan).
- * frames: the frames of all series back to back, series s holding
- *   frames_per_series[s] frames of side_px[s]^2 pixels with row pitch
- *   pitch_elems (>= max side; elements), float32.  Host memory unless
- *   frames_on_device != 0 (then a device pointer; it is only read).
+ * frames: the frames of all series back to back as rows of pitch_elems
+ *   (>= max side) float32 elements: series s holds frames_per_series[s]
+ *   frames of side_px[s] rows each (side_px[s] pixels used per row), so
+ *   series s starts at row sum_{j<s} frames_per_series[j] * side_px[j].
+ *   Host memory unless frames_on_device != 0 (then a device pointer; it is
+ *   only read).
  * The library copies the frames, builds each frame's pyramid (restriction
  * with the 1/16 [1 2 1; 2 4 2; 1 2 1] stencil, Section "Multilevel") and
  * keeps it until reg_destroy_series.  cuda_stream: a cudaStream_t (NULL =

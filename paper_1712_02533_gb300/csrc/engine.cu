@@ -571,7 +571,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         return cleanup(fail(REG_ECUDA, "memset"));
     // series geometry
     int fb = 0;
-    int64_t frame_off = 0;
+    int64_t row_off = 0;  // rows of pitch_elems before the current series
     for (int i = 0; i < n_series; i++) {
         SeriesInfo si;
         si.n_frames = frames_per_series[i];
@@ -623,7 +623,9 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         if (!frames_on_device && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
         for (int f0 = 0; f0 < si.n_frames; f0 += chunk) {
             int nf = std::min(chunk, si.n_frames - f0);
-            const float *src = frames + (frame_off + f0) * (int64_t)si.side * pitch_elems;
+            // series i starts after all rows of the series before it (side_j rows of
+            // pitch_elems per frame); frame f0 of it after f0 * side rows of its own
+            const float *src = frames + (row_off + (int64_t)f0 * si.side) * pitch_elems;
             int64_t fstride = (int64_t)si.side * pitch_elems, pitch = pitch_elems;
             if (!frames_on_device) {
                 cudaError_t e = cudaMemcpy2DAsync(stage, si.side * 4, src, pitch_elems * 4, si.side * 4,
@@ -660,7 +662,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         dfree(s, raw, raw_bytes);
         dfree(s, stats, 0);
         dfree(s, stage, stage_bytes);
-        frame_off += si.n_frames;
+        row_off += (int64_t)si.n_frames * si.side;
     }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid sync"));
     *out = s;

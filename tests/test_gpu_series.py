@@ -1,0 +1,61 @@
+"""Segmented scans over series of mixed sizes, and the BF16 storage form, on the
+GPU through the C-ABI."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def reg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as r
+    return r
+
+
+def _mixed(syn):
+    # three series of different sides and lengths (config 5's shape at small sizes)
+    return [syn.series(11, 6, 64, spacing=8.0, sigma=1.5, peak=20.0, drift_sd=0.5, dist_amp=1.0),
+            syn.series(12, 5, 128, spacing=10.0, sigma=2.0, peak=10.0, drift_sd=0.5, dist_amp=1.0),
+            syn.series(13, 4, 256, spacing=12.0, sigma=2.0, peak=10.0, drift_sd=0.5, dist_amp=1.0)]
+
+
+@pytest.mark.parametrize("kind_name", ["sklansky", "blelloch"])
+def test_mixed_sizes_in_one_segmented_scan_equal_separate_scans(reg, syn, kind_name):
+    """Each operator's sums are reduced in a fixed order over its own tiles, so
+    batching the scan levels of several series (of different sizes) together
+    must not change any result: bit-identical to scanning each series alone."""
+    kind = {v: k for k, v in reg.SCAN_NAMES.items()}[kind_name]
+    series = _mixed(syn)
+    p = reg.default_params(n_levels=3, iter_max=50, lam=10.0)
+    with reg.Series(series, p) as s:
+        rep = s.prefix_scan(kind)
+        together = [s.get_deformations(series=k) for k in range(len(series))]
+    assert rep["preprocessing_ops"] == sum(len(f) - 1 for f in series)
+    for k, f in enumerate(series):
+        with reg.Series(f, p) as s:
+            s.prefix_scan(kind)
+            alone = s.get_deformations()
+        assert np.array_equal(together[k], alone), (k, float(np.abs(together[k] - alone).max()))
+
+
+def test_bf16_storage_error_against_fp32(reg, syn):
+    """BF16 pyramid storage (FP32 arithmetic): its deviation from the FP32 form
+    is a property of the series, not bounded a priori; it must stay a fraction of
+    a pixel on the config-1 series, and the run must converge like the FP32 one."""
+    cfg = dict(syn.CONFIGS["c1_8x64"])
+    nl = cfg.pop("n_levels")
+    fr = syn.series(**cfg)
+    out = {}
+    for storage in (reg.STORAGE_F32, reg.STORAGE_BF16):
+        p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0, storage=storage)
+        with reg.Series(fr, p) as s:
+            s.prefix_scan(reg.SKLANSKY)
+            out[storage] = s.get_deformations()
+    err = np.abs(out[reg.STORAGE_BF16] - out[reg.STORAGE_F32])
+    assert np.isfinite(err).all()
+    assert err.max() < 0.5, float(err.max())
