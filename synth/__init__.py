@@ -119,3 +119,20 @@ def series(seed: int, n_frames: int, side: int, spacing: float = 8.0, sigma: flo
     if ground_truth:
         return frames, gt, tr
     return frames
+
+
+# Layer shapes (in channels, out channels) of the learned initialiser's six 3x3
+# convolutions, for drawing its initial parameters.
+CNN_SHAPES = [(2, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 2)]
+
+
+def cnn_params(seed: int) -> np.ndarray:
+    """Initial parameters of the learned initialiser as one flat float32 vector
+    (layer by layer: W as out x in x 3 x 3, then b): He-normal weights with
+    variance 2 / (9 in), zero biases, drawn from numpy's PCG64 with `seed`."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for c, o in CNN_SHAPES:
+        parts.append(rng.standard_normal(o * c * 9) * np.sqrt(2.0 / (9 * c)))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)

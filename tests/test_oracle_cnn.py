@@ -1,0 +1,118 @@
+"""Pins of the learned initialiser's FP64 oracle (oracle/cnn.py): the convolution
+against scipy's correlation and against its own stride-1 form, every gradient
+against central finite differences, and the output upsampling against exact
+cases."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+
+def test_layer_shapes_and_parameter_count_match_the_generator():
+    import synth
+    assert [(c, o) for c, o, _ in cnn.LAYERS] == synth.CNN_SHAPES
+    assert cnn.n_params() == 608 + 4 * 9248 + 578
+    assert synth.cnn_params(0).size == cnn.n_params()
+
+
+def test_single_channel_convolution_is_scipy_correlation():
+    sig = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 1, 9, 7))
+    W = rng.standard_normal((1, 1, 3, 3))
+    want = sig.correlate2d(np.pad(x[0, 0], 1), W[0, 0], mode="valid") + 0.25
+    got = cnn.conv_forward(x, W, np.array([0.25]), 1)[0, 0]
+    assert np.allclose(got, want, atol=1e-13)
+
+
+def test_multichannel_convolution_sums_channels():
+    sig = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 3, 6, 6))
+    W = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    got = cnn.conv_forward(x, W, b, 1)
+    for n in range(2):
+        for o in range(4):
+            want = b[o] + sum(sig.correlate2d(np.pad(x[n, c], 1), W[o, c], mode="valid") for c in range(3))
+            assert np.allclose(got[n, o], want, atol=1e-12)
+
+
+def test_stride_two_is_stride_one_at_even_positions():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 3, 12, 12))
+    W = rng.standard_normal((5, 3, 3, 3))
+    b = rng.standard_normal(5)
+    full = cnn.conv_forward(x, W, b, 1)
+    half = cnn.conv_forward(x, W, b, 2)
+    assert half.shape == (2, 5, 6, 6)
+    assert np.allclose(half, full[:, :, ::2, ::2], atol=1e-13)
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+def test_convolution_gradients_are_finite_differences(stride):
+    rng = np.random.default_rng(4 + stride)
+    x = rng.standard_normal((2, 2, 6, 6))
+    W = rng.standard_normal((3, 2, 3, 3))
+    b = rng.standard_normal(3)
+    G = rng.standard_normal(cnn.conv_forward(x, W, b, stride).shape)
+    f = lambda x_, W_, b_: float(np.sum(G * cnn.conv_forward(x_, W_, b_, stride)))
+    gx, gW, gb = cnn.conv_backward(x, W, stride, G)
+    eps = 1e-6
+    for arr, g, name in ((x, gx, "x"), (W, gW, "W"), (b, gb, "b")):
+        for idx in list(np.ndindex(arr.shape))[::5]:
+            d = np.zeros_like(arr)
+            d[idx] = eps
+            args_p = [x, W, b]
+            args_m = [x, W, b]
+            k = {"x": 0, "W": 1, "b": 2}[name]
+            args_p[k] = arr + d
+            args_m[k] = arr - d
+            fd = (f(*args_p) - f(*args_m)) / (2 * eps)
+            assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx, fd, g[idx])
+
+
+def test_network_gradient_is_finite_differences():
+    import synth
+    rng = np.random.default_rng(6)
+    theta = synth.cnn_params(7).astype(np.float64)
+    theta += 0.01 * rng.standard_normal(theta.size)  # nonzero biases too
+    x = rng.standard_normal((2, 2, 16, 16))
+    t = rng.standard_normal((2, 2, 4, 4))
+    L, g = cnn.loss_and_grad(theta, x, t)
+    assert L == pytest.approx(cnn.loss(theta, x, t), rel=1e-14)
+    eps = 1e-6
+    picks = rng.choice(theta.size, 60, replace=False)
+    for i in picks:
+        d = np.zeros_like(theta)
+        d[i] = eps
+        fd = (cnn.loss(theta + d, x, t) - cnn.loss(theta - d, x, t)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_relu_blocks_the_gradient_of_a_dead_layer():
+    # a first layer whose pre-activations are all negative passes no gradient
+    import synth
+    theta = synth.cnn_params(8).astype(np.float64)
+    layers = cnn.unpack(theta)
+    layers[0] = (np.zeros_like(layers[0][0]), np.full_like(layers[0][1], -1.0))
+    theta = cnn.pack(layers)
+    rng = np.random.default_rng(9)
+    _, g = cnn.loss_and_grad(theta, rng.standard_normal((1, 2, 8, 8)), rng.standard_normal((1, 2, 2, 2)))
+    assert np.all(cnn.unpack(g)[0][0] == 0.0) and np.all(cnn.unpack(g)[0][1] == 0.0)
+
+
+def test_upsampling_reproduces_constant_and_linear_fields():
+    q, side = 8, 128  # input 32 px, frames of 128 px: 4 frame px per input px
+    out = np.ones((2, q, q)) * np.array([1.5, -0.5])[:, None, None]
+    up = cnn.upsample(out, side)
+    assert up.shape == (2, side + 1, side + 1)
+    assert np.allclose(up[0], 1.5 * 4) and np.allclose(up[1], -0.5 * 4)
+    # a field linear in the output grid is reproduced exactly inside it
+    i = np.arange(q, dtype=np.float64)
+    lin = np.stack([np.add.outer(0 * i, i), np.add.outer(i, 0 * i)])
+    up = cnn.upsample(lin, side)
+    r = np.arange(side + 1) / 16.0
+    inside = r <= q - 1
+    assert np.allclose(up[0][:, inside], 4 * r[inside][None, :])
+    assert np.allclose(up[1][inside, :], 4 * r[inside][:, None])
