@@ -208,6 +208,52 @@ reg_status reg_eval_direction(reg_series_t s, int32_t series, int32_t frame_i, i
 reg_status reg_eval_trials(reg_series_t s, int32_t series, int32_t frame_i, int32_t frame_k, int32_t level,
                            const float *u_grid, int32_t n_tau, const double *taus, float *d_out, double *dE_out);
 
+/* ---------------------------------------------------------------------------
+ * Learned initialiser (not in the paper: a coarse initial displacement for a
+ * frame pair, predicted by a small convolutional network trained on
+ * displacements the plain method computes; the plain gradient flow refines it).
+ * Network: input 2 x S x S (channel 0 the reference frame, 1 the template,
+ * normalised), six 3x3 convolutions with zero padding 1 -- 2->32 stride 2,
+ * 32->32 stride 2, three 32->32 stride 1, 32->2 stride 1 -- with a ReLU after
+ * every layer but the last; output 2 x S/4 x S/4, the displacement in input
+ * pixels at input pixels (4i, 4j).  Loss: mean squared difference to a target.
+ * Parameters: one flat float vector of reg_cnn_num_params() values, layer by
+ * layer W (out x in x 3 x 3, row-major) then b.  All data pointers are device
+ * pointers unless stated; calls return when the work is done.
+ * ------------------------------------------------------------------------- */
+typedef struct reg_cnn *reg_cnn_t;
+int64_t reg_cnn_num_params(void);
+/* A network for inputs of side x side (a multiple of 4, 16..4096) and batches
+ * of up to max_batch pairs; parameters start at zero (set them). */
+reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, reg_cnn_t *out);
+/* Parameters from/to `theta` (host memory unless on_device); setting them also
+ * resets the optimiser state. */
+reg_status reg_cnn_set_params(reg_cnn_t h, const float *theta, int32_t on_device);
+reg_status reg_cnn_get_params(reg_cnn_t h, float *theta, int32_t on_device);
+/* y (batch x 2 x side/4 x side/4) = network(x (batch x 2 x side x side)).
+ * tensor_cores != 0: the 32-channel layers on the tensor cores (BF16 operands,
+ * FP32 accumulation), else every layer in FP32 on the CUDA cores. */
+reg_status reg_cnn_forward(reg_cnn_t h, const float *x, int32_t batch, float *y, int32_t tensor_cores);
+/* Loss against `target` (same shape as y) and its gradient (FP32, kept in the
+ * handle for reg_cnn_adam_step; also copied to grad_out, host, if not NULL);
+ * *loss (host) receives the mean squared error. */
+reg_status reg_cnn_loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                             float *grad_out);
+/* One Adam step (bias-corrected) with the last gradient. */
+reg_status reg_cnn_adam_step(reg_cnn_t h, double lr, double beta1, double beta2, double eps);
+reg_status reg_cnn_destroy(reg_cnn_t h);
+/* Network inputs of `count` neighbour pairs (first_pair .. first_pair+count-1:
+ * frames e and e+1) of a series, from its pyramid level of 257^2 nodes (the
+ * first 256 rows and columns), into x (count x 2 x 256 x 256).  REG_EINVAL if
+ * the pyramid has no such level. */
+reg_status reg_cnn_pairs(reg_series_t s, int32_t series, int32_t first_pair, int32_t count, float *x);
+/* Predict the initial displacement of every neighbour pair of a series with a
+ * network for 256^2 inputs, upsample it (bilinear in the output grid, clamped)
+ * onto the finest vertex grid in frame pixels, and store it in the pair's data
+ * slot; the next reg_prefix_scan starts those preprocessing operators from the
+ * slots instead of the identity. */
+reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int32_t tensor_cores);
+
 /* Schedule export (host only, no GPU work): writes the op list of a schedule
  * over n elements as reg_schedule_op records (level index, kind, slots) into
  * buf (up to buf_len records), the total count into *n_out (call with buf NULL

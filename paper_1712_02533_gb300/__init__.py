@@ -96,6 +96,16 @@ def _load():
         "reg_get_trace": ([vp, vp, i64, P(i64)], ctypes.c_int),
         "reg_eval_energy_noalloc": ([vp, vp, i32, i32, vp, d, vp, i32, vp], ctypes.c_int),
         "reg_destroy_series": ([vp], ctypes.c_int),
+        "reg_cnn_num_params": ([], i64),
+        "reg_cnn_create": ([i32, i32, vp, P(vp)], ctypes.c_int),
+        "reg_cnn_set_params": ([vp, vp, i32], ctypes.c_int),
+        "reg_cnn_get_params": ([vp, vp, i32], ctypes.c_int),
+        "reg_cnn_forward": ([vp, vp, i32, vp, i32], ctypes.c_int),
+        "reg_cnn_loss_grad": ([vp, vp, vp, i32, P(d), vp], ctypes.c_int),
+        "reg_cnn_adam_step": ([vp, d, d, d, d], ctypes.c_int),
+        "reg_cnn_destroy": ([vp], ctypes.c_int),
+        "reg_cnn_pairs": ([vp, i32, i32, i32, vp], ctypes.c_int),
+        "reg_cnn_init_series": ([vp, i32, vp, i32], ctypes.c_int),
         "reg_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "reg_last_error": ([], ctypes.c_char_p),
     }
@@ -158,6 +168,12 @@ def _torch_allocator(device):
     a = Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
     _keep.append(a)
     return a
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(st.cuda_stream)
 
 
 def _ptr(x):
@@ -329,6 +345,69 @@ def destroy_series(h):
     _check(_load().reg_destroy_series(h))
 
 
+class Cnn:
+    """The learned initialiser (C-ABI reg_cnn_*): a network for side x side input
+    pairs (side a multiple of 4) and batches of up to max_batch pairs.  Device
+    tensors in and out (torch CUDA tensors, float32, contiguous)."""
+
+    def __init__(self, params=None, side=256, max_batch=64, stream=None):
+        lib = _load()
+        h = ctypes.c_void_p()
+        _check(lib.reg_cnn_create(side, max_batch, _stream_ptr(stream), ctypes.byref(h)))
+        self.h, self.side, self.max_batch = h, side, max_batch
+        if params is not None:
+            self.set_params(params)
+
+    @staticmethod
+    def num_params():
+        return int(_load().reg_cnn_num_params())
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, np.float32)
+        assert theta.size == self.num_params()
+        _check(_load().reg_cnn_set_params(self.h, theta.ctypes.data, 0))
+
+    def get_params(self):
+        out = np.empty(self.num_params(), np.float32)
+        _check(_load().reg_cnn_get_params(self.h, out.ctypes.data, 0))
+        return out
+
+    def forward(self, x, y=None, tensor_cores=False):
+        torch = _torch()
+        b = int(x.shape[0])
+        if y is None:
+            y = torch.empty((b, 2, self.side // 4, self.side // 4), dtype=torch.float32, device=x.device)
+        _check(_load().reg_cnn_forward(self.h, x.data_ptr(), b, y.data_ptr(), int(bool(tensor_cores))))
+        return y
+
+    def loss_grad(self, x, target, want_grad=False):
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params(), np.float32) if want_grad else None
+        _check(_load().reg_cnn_loss_grad(self.h, x.data_ptr(), target.data_ptr(), int(x.shape[0]),
+                                         ctypes.byref(loss), g.ctypes.data if want_grad else None))
+        return (loss.value, g) if want_grad else loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(_load().reg_cnn_adam_step(self.h, lr, beta1, beta2, eps))
+
+    def close(self):
+        if self.h:
+            _load().reg_cnn_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Series:
     """A handle over one or several frame series (one segmented scan)."""
 
@@ -383,6 +462,17 @@ class Series:
 
     def eval_trials(self, frame_i, frame_k, level, u_grid, taus, series=0):
         return eval_trials(self.h, series, frame_i, frame_k, level, u_grid, taus)
+
+    def cnn_pairs(self, first, count, out, series=0):
+        """Network inputs of neighbour pairs first..first+count-1 into the CUDA
+        tensor out (count x 2 x 256 x 256)."""
+        _check(_load().reg_cnn_pairs(self.h, series, first, count, out.data_ptr()))
+        return out
+
+    def cnn_init(self, cnn, series=0, tensor_cores=False):
+        """Initial displacements of all neighbour pairs from the network; the next
+        prefix_scan starts its preprocessing operators from them."""
+        _check(_load().reg_cnn_init_series(self.h, series, cnn.h, int(bool(tensor_cores))))
 
     def set_trace(self, capacity):
         set_trace(self.h, capacity)

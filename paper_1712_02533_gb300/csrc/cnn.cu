@@ -1,0 +1,455 @@
+// The learned initialiser: a small convolutional network that predicts a coarse
+// initial displacement for a frame pair, trained on the GPU on displacements
+// that the plain method computes (its forward, backward and update kernels).
+//
+// Network: input 2 x S x S (reference, template; normalised), six 3x3
+// convolutions with zero padding 1 -- 2->32 stride 2, 32->32 stride 2, three
+// 32->32 stride 1, 32->2 stride 1 -- with a ReLU after every layer but the
+// last; output 2 x S/4 x S/4, the displacement in input pixels at input pixels
+// (4i, 4j).  Loss: mean squared difference to a target displacement.
+// Parameters: one flat float vector, layer by layer W (O x C x 3 x 3) then b.
+//
+// Layout: activations NCHW in float, one buffer per layer.  Training kernels
+// run on the CUDA cores in FP32; the inference path (k_conv_fwd_tc) runs the
+// 32-channel layers on the tensor cores (BF16 operands, FP32 accumulation).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/reg.h"
+#include "cnn_internal.h"
+
+namespace {
+
+constexpr int NL = 6;
+struct LayerShape {
+    int C, O, S;
+};
+constexpr LayerShape LAYERS[NL] = {{2, 32, 2}, {32, 32, 2}, {32, 32, 1}, {32, 32, 1}, {32, 32, 1}, {32, 2, 1}};
+
+constexpr int64_t layer_params(int k) { return (int64_t)LAYERS[k].O * LAYERS[k].C * 9 + LAYERS[k].O; }
+int64_t param_offset(int k)
+{
+    int64_t o = 0;
+    for (int j = 0; j < k; j++) o += layer_params(j);
+    return o;
+}
+int64_t total_params() { return param_offset(NL); }
+
+// ---------------------------------------------------------------------------
+// Forward: one thread per output pixel (b, y, x) computes all O channels.
+// ---------------------------------------------------------------------------
+template <int C, int O, int S, bool RELU>
+__global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, int H, const float *__restrict__ theta,
+                                                  float *__restrict__ out, int Ho, int total)
+{
+    __shared__ float w[O * C * 9];
+    __shared__ float bias[O];
+    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) w[i] = theta[i];
+    for (int i = threadIdx.x; i < O; i += blockDim.x) bias[i] = theta[O * C * 9 + i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int x = p % Ho, y = (p / Ho) % Ho, b = p / (Ho * Ho);
+    float acc[O];
+#pragma unroll
+    for (int o = 0; o < O; o++) acc[o] = bias[o];
+    for (int c = 0; c < C; c++) {
+        const float *src = in + ((int64_t)b * C + c) * H * H;
+        float v[9];
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 3; dx++) {
+                const int iy = S * y + dy - 1, ix = S * x + dx - 1;
+                v[dy * 3 + dx] = (iy >= 0 && iy < H && ix >= 0 && ix < H) ? src[iy * H + ix] : 0.f;
+            }
+#pragma unroll
+        for (int o = 0; o < O; o++) {
+            const float *wk = w + (o * C + c) * 9;
+#pragma unroll
+            for (int k = 0; k < 9; k++) acc[o] = fmaf(wk[k], v[k], acc[o]);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < O; o++) {
+        float r = acc[o];
+        if (RELU) r = fmaxf(r, 0.f);
+        out[(((int64_t)b * O + o) * Ho + y) * Ho + x] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward, data: gx[b, c, iy, ix] = sum over (o, dy, dx) with S oy + dy - 1 = iy
+// and S ox + dx - 1 = ix of W[o, c, dy, dx] gz[b, o, oy, ox], times the ReLU
+// mask of the layer below (its output a > 0).  One thread per input pixel.
+// ---------------------------------------------------------------------------
+template <int C, int O, int S>
+__global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__ gz, int Ho,
+                                                       const float *__restrict__ theta,
+                                                       const float *__restrict__ a_below, float *__restrict__ gx,
+                                                       int H, int total)
+{
+    __shared__ float w[O * C * 9];
+    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) w[i] = theta[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int ix = p % H, iy = (p / H) % H, b = p / (H * H);
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) acc[c] = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < 3; dy++) {
+        const int ty = iy + 1 - dy;
+        if (ty < 0 || ty % S != 0 || ty / S >= Ho) continue;
+        const int oy = ty / S;
+#pragma unroll
+        for (int dx = 0; dx < 3; dx++) {
+            const int tx = ix + 1 - dx;
+            if (tx < 0 || tx % S != 0 || tx / S >= Ho) continue;
+            const int ox = tx / S;
+            for (int o = 0; o < O; o++) {
+                const float g = gz[(((int64_t)b * O + o) * Ho + oy) * Ho + ox];
+                const float *wk = w + o * C * 9 + dy * 3 + dx;
+#pragma unroll
+                for (int c = 0; c < C; c++) acc[c] = fmaf(wk[c * 9], g, acc[c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const int64_t i = (((int64_t)b * C + c) * H + iy) * H + ix;
+        gx[i] = a_below[i] > 0.f ? acc[c] : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward, weights: gW[o, c, dy, dx] = sum_{b, y, x} gz[b, o, y, x]
+// in_pad[b, c, S y + dy, S x + dx] and gb[o] = sum gz[b, o, ., .].  One block per
+// (o, c), a fixed-order reduction (deterministic).
+// ---------------------------------------------------------------------------
+template <int C, int O, int S>
+__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict__ in, int H,
+                                                         const float *__restrict__ gz, int Ho, int B,
+                                                         float *__restrict__ grad)
+{
+    const int o = blockIdx.x / C, c = blockIdx.x % C;
+    float acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; k++) acc[k] = 0.f;
+    const int per = Ho * Ho, total = B * per;
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+        const int b = p / per, q = p % per, y = q / Ho, x = q % Ho;
+        const float g = gz[((int64_t)b * O + o) * per + q];
+        const float *src = in + ((int64_t)b * C + c) * H * H;
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 3; dx++) {
+                const int iy = S * y + dy - 1, ix = S * x + dx - 1;
+                const float v = (iy >= 0 && iy < H && ix >= 0 && ix < H) ? src[iy * H + ix] : 0.f;
+                acc[dy * 3 + dx] = fmaf(g, v, acc[dy * 3 + dx]);
+            }
+        acc[9] += g;
+    }
+    __shared__ float red[8][10];
+#pragma unroll
+    for (int k = 0; k < 10; k++) {
+        float v = acc[k];
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        float t = 0.f;
+        for (int w = 0; w < 8; w++) t += red[w][threadIdx.x];
+        if (threadIdx.x < 9) grad[(o * C + c) * 9 + threadIdx.x] = t;
+        else if (c == 0) grad[O * C * 9 + o] = t;
+    }
+}
+
+// Mean squared error: per-block partial sums (double), then one block adds them
+// in order; gy = 2 (y - t) / N.
+__global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, int64_t n, float *__restrict__ gy,
+                      double *__restrict__ partial)
+{
+    double s = 0.0;
+    const float inv = 2.f / (float)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        s += (double)d * d;
+        gy[i] = inv * d;
+    }
+    __shared__ double red[8];
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+        partial[blockIdx.x] = tot;
+    }
+}
+
+__global__ void k_sum_partials(const double *partial, int n, double scale, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; i++) s += partial[i];
+        *out = s * scale;
+    }
+}
+
+// Adam with bias correction (step t >= 1).
+__global__ void k_adam(float *__restrict__ theta, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+template <int C, int O, int S, bool RELU>
+void fwd(const float *in, int H, const float *theta, float *out, int B, cudaStream_t st)
+{
+    const int Ho = (H + 2 - 3) / S + 1, total = B * Ho * Ho;
+    k_conv_fwd<C, O, S, RELU><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
+}
+
+template <int C, int O, int S>
+void bwd(const float *in, int H, const float *gz, const float *theta, const float *a_below, float *gx, float *grad,
+         int B, cudaStream_t st)
+{
+    const int Ho = (H + 2 - 3) / S + 1;
+    k_conv_bwd_weight<C, O, S><<<O * C, 256, 0, st>>>(in, H, gz, Ho, B, grad);
+    if (gx) {
+        const int total = B * H * H;
+        k_conv_bwd_data<C, O, S><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
+    }
+}
+
+}  // namespace
+
+struct reg_cnn {
+    cudaStream_t stream = nullptr;
+    int side = 0, max_batch = 0;
+    int64_t n = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float *act[NL] = {nullptr};  // layer outputs (post-ReLU, the last one raw)
+    float *g0 = nullptr, *g1 = nullptr;  // gradient ping-pong (largest activation)
+    float *gy = nullptr;
+    double *partial = nullptr, *loss = nullptr;
+    int64_t step = 0;
+    int use_tc = 1;
+};
+
+namespace {
+
+reg_status cnn_fail(reg_status st, const char *msg) { return reg_internal_fail(st, msg); }
+
+#define CKC(x)                                                          \
+    do {                                                                \
+        cudaError_t e_ = (x);                                           \
+        if (e_ != cudaSuccess) return cnn_fail(REG_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+int out_side(int k, int side)
+{
+    int H = side;
+    for (int j = 0; j <= k; j++) H = (H + 2 - 3) / LAYERS[j].S + 1;
+    return H;
+}
+
+int in_side(int k, int side) { return k == 0 ? side : out_side(k - 1, side); }
+
+int64_t act_elems(int k, int side) { return (int64_t)LAYERS[k].O * out_side(k, side) * out_side(k, side); }
+
+}  // namespace
+
+int64_t cnn_output_side(const reg_cnn *h) { return out_side(NL - 1, h->side); }
+int cnn_input_side(const reg_cnn *h) { return h->side; }
+int cnn_max_batch(const reg_cnn *h) { return h->max_batch; }
+
+// Forward of a batch of pairs x (device, B x 2 x side x side) into y (device,
+// B x 2 x side/4 x side/4) on the given stream; the layer outputs stay in the
+// handle for a backward pass.
+reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t st, bool tc)
+{
+    const int S = h->side;
+    const float *a = x;
+    for (int k = 0; k < NL; k++) {
+        const int H = in_side(k, S);
+        const float *th = h->theta + param_offset(k);
+        float *out = (k == NL - 1 && y) ? y : h->act[k];
+        if (tc && k >= 1 && k <= 4) {
+            // 32 -> 32 layers on the tensor cores
+            reg_status rs = cnn_conv32_tc(a, H, th, out, B, LAYERS[k].S, st);
+            if (rs != REG_OK) return rs;
+        } else {
+            switch (k) {
+            case 0: fwd<2, 32, 2, true>(a, H, th, out, B, st); break;
+            case 1: fwd<32, 32, 2, true>(a, H, th, out, B, st); break;
+            case 2:
+            case 3:
+            case 4: fwd<32, 32, 1, true>(a, H, th, out, B, st); break;
+            default: fwd<32, 2, 1, false>(a, H, th, out, B, st); break;
+            }
+        }
+        if (k == NL - 1 && y && y != h->act[k])
+            CKC(cudaMemcpyAsync(h->act[k], y, sizeof(float) * act_elems(k, S) * B, cudaMemcpyDeviceToDevice, st));
+        a = out;
+    }
+    CKC(cudaGetLastError());
+    return REG_OK;
+}
+
+extern "C" {
+
+int64_t reg_cnn_num_params(void) { return total_params(); }
+
+reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, reg_cnn_t *out)
+{
+    if (!out || side < 16 || side % 4 != 0 || side > 4096 || max_batch < 1) return cnn_fail(REG_EINVAL, "bad argument");
+    reg_cnn *h = new reg_cnn();
+    h->stream = (cudaStream_t)cuda_stream;
+    h->side = side;
+    h->max_batch = max_batch;
+    h->n = total_params();
+    auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = alloc((void **)&h->theta, sizeof(float) * h->n) && alloc((void **)&h->grad, sizeof(float) * h->n) &&
+              alloc((void **)&h->m, sizeof(float) * h->n) && alloc((void **)&h->v, sizeof(float) * h->n);
+    int64_t big = 0;
+    for (int k = 0; k < NL && ok; k++) {
+        ok = alloc((void **)&h->act[k], sizeof(float) * act_elems(k, side) * max_batch);
+        big = std::max(big, act_elems(k, side));
+    }
+    big = std::max(big, (int64_t)2 * side * side);
+    ok = ok && alloc((void **)&h->g0, sizeof(float) * big * max_batch) &&
+         alloc((void **)&h->g1, sizeof(float) * big * max_batch) &&
+         alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
+         alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double));
+    if (!ok) {
+        reg_cnn_destroy(h);
+        return cnn_fail(REG_ENOMEM, "device allocation failed");
+    }
+    cudaMemsetAsync(h->theta, 0, sizeof(float) * h->n, h->stream);
+    cudaMemsetAsync(h->m, 0, sizeof(float) * h->n, h->stream);
+    cudaMemsetAsync(h->v, 0, sizeof(float) * h->n, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        reg_cnn_destroy(h);
+        return cnn_fail(REG_ECUDA, "init");
+    }
+    *out = h;
+    return REG_OK;
+}
+
+reg_status reg_cnn_set_params(reg_cnn_t h, const float *theta, int32_t on_device)
+{
+    if (!h || !theta) return cnn_fail(REG_EINVAL, "bad argument");
+    CKC(cudaMemcpyAsync(h->theta, theta, sizeof(float) * h->n,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CKC(cudaMemsetAsync(h->m, 0, sizeof(float) * h->n, h->stream));
+    CKC(cudaMemsetAsync(h->v, 0, sizeof(float) * h->n, h->stream));
+    h->step = 0;
+    CKC(cudaStreamSynchronize(h->stream));
+    return REG_OK;
+}
+
+reg_status reg_cnn_get_params(reg_cnn_t h, float *theta, int32_t on_device)
+{
+    if (!h || !theta) return cnn_fail(REG_EINVAL, "bad argument");
+    CKC(cudaMemcpyAsync(theta, h->theta, sizeof(float) * h->n,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+    return REG_OK;
+}
+
+reg_status reg_cnn_forward(reg_cnn_t h, const float *x, int32_t batch, float *y, int32_t tensor_cores)
+{
+    if (!h || !x || !y || batch < 1 || batch > h->max_batch) return cnn_fail(REG_EINVAL, "bad argument");
+    reg_status st = cnn_forward(h, x, batch, y, h->stream, tensor_cores != 0);
+    if (st != REG_OK) return st;
+    CKC(cudaStreamSynchronize(h->stream));
+    return REG_OK;
+}
+
+reg_status reg_cnn_loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                             float *grad_out)
+{
+    if (!h || !x || !target || batch < 1 || batch > h->max_batch) return cnn_fail(REG_EINVAL, "bad argument");
+    cudaStream_t st = h->stream;
+    const int S = h->side, B = batch;
+    reg_status rs = cnn_forward(h, x, B, nullptr, st, false);
+    if (rs != REG_OK) return rs;
+    const int64_t ny = act_elems(NL - 1, S) * B;
+    const int nb = (int)std::min<int64_t>(1024, (ny + 255) / 256);
+    k_mse<<<nb, 256, 0, st>>>(h->act[NL - 1], target, ny, h->gy, h->partial);
+    k_sum_partials<<<1, 32, 0, st>>>(h->partial, nb, 1.0 / (double)ny, h->loss);
+    const float *gz = h->gy;
+    float *bufs[2] = {h->g0, h->g1};
+    for (int k = NL - 1; k >= 0; k--) {
+        const int H = in_side(k, S);
+        const float *in = k == 0 ? x : h->act[k - 1];
+        const float *th = h->theta + param_offset(k);
+        float *gr = h->grad + param_offset(k);
+        float *gx = k == 0 ? nullptr : bufs[k & 1];
+        const float *below = k == 0 ? nullptr : h->act[k - 1];
+        switch (k) {
+        case 0: bwd<2, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
+        case 1: bwd<32, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
+        case 2:
+        case 3:
+        case 4: bwd<32, 32, 1>(in, H, gz, th, below, gx, gr, B, st); break;
+        default: bwd<32, 2, 1>(in, H, gz, th, below, gx, gr, B, st); break;
+        }
+        gz = gx;
+    }
+    CKC(cudaGetLastError());
+    if (loss) CKC(cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (grad_out) CKC(cudaMemcpyAsync(grad_out, h->grad, sizeof(float) * h->n, cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    return REG_OK;
+}
+
+reg_status reg_cnn_adam_step(reg_cnn_t h, double lr, double beta1, double beta2, double eps)
+{
+    if (!h || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+        return cnn_fail(REG_EINVAL, "bad argument");
+    h->step++;
+    const double c1 = 1.0 - std::pow(beta1, (double)h->step), c2 = 1.0 - std::pow(beta2, (double)h->step);
+    k_adam<<<(int)std::min<int64_t>(1024, (h->n + 255) / 256), 256, 0, h->stream>>>(
+        h->theta, h->grad, h->m, h->v, h->n, (float)lr, (float)beta1, (float)beta2, (float)eps, (float)c1, (float)c2);
+    CKC(cudaGetLastError());
+    CKC(cudaStreamSynchronize(h->stream));
+    return REG_OK;
+}
+
+reg_status reg_cnn_destroy(reg_cnn_t h)
+{
+    if (!h) return REG_OK;
+    cudaFree(h->theta);
+    cudaFree(h->grad);
+    cudaFree(h->m);
+    cudaFree(h->v);
+    for (int k = 0; k < NL; k++) cudaFree(h->act[k]);
+    cudaFree(h->g0);
+    cudaFree(h->g1);
+    cudaFree(h->gy);
+    cudaFree(h->partial);
+    cudaFree(h->loss);
+    delete h;
+    return REG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,20 @@
+// Internal interface between the learned initialiser (cnn.cu) and the series
+// engine (engine.cu); not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/reg.h"
+
+struct reg_cnn;
+// Forward of B pairs x (device, B x 2 x S x S) into y (device, B x 2 x S/4 x
+// S/4) on stream st; tc: the 32-channel layers on the tensor cores.
+reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t st, bool tc);
+int64_t cnn_output_side(const reg_cnn *h);
+int cnn_input_side(const reg_cnn *h);
+int cnn_max_batch(const reg_cnn *h);
+// 32 -> 32 channel 3x3 convolution with ReLU on the tensor cores (BF16 operands,
+// FP32 accumulation): in (B x 32 x H x H), out (B x 32 x Ho x Ho), stride S.
+reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st);
+// Record an error message for reg_last_error().
+reg_status reg_internal_fail(reg_status st, const char *msg);

@@ -15,6 +15,7 @@
 #include "../../include/reg.h"
 #include "reg_common.cuh"
 #include "schedule.h"
+#include "cnn_internal.h"
 
 // kernels (kernels.cu)
 __global__ void k_embed(const float *, int64_t, int64_t, int, float *, int64_t, int);
@@ -79,6 +80,7 @@ struct SeriesInfo {
     float2 *slots = nullptr;              // n_slots * slot_elems
     size_t slot_elems = 0;
     std::vector<SlotMeta> meta;
+    bool pre_from_slots = false;          // next scan: preprocessing starts from the data slots
     std::vector<size_t> ws_off;           // per level: offset (bytes) of U0 within an op workspace
     size_t ws_bytes = 0;                  // per op
     size_t rec_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(NodeRec); }
@@ -760,7 +762,10 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
     for (int si = 0; si < (int)s->S.size(); si++) {
         SeriesInfo &S = s->S[si];
         for (auto &m : S.meta) m = SlotMeta{};
-        for (int e = 0; e < S.n_data; e++) pre.push_back(OpReq{si, e, e + 1, 0, -1, -1, e});
+        // identity start, or (after reg_cnn_init_series) the slot's initial guess
+        for (int e = 0; e < S.n_data; e++)
+            pre.push_back(S.pre_from_slots ? OpReq{si, e, e + 1, 1, e, -1, e} : OpReq{si, e, e + 1, 0, -1, -1, e});
+        S.pre_from_slots = false;
     }
     std::vector<int32_t> stat(pre.size());
     RET(run_batch(s, pre, [] { return REG_OK; }, stat.data(), nullptr));
@@ -1232,3 +1237,109 @@ reg_status reg_reset_kernel_stats(reg_series_t s)
 }
 
 }  // extern "C"
+
+reg_status reg_internal_fail(reg_status st, const char *msg) { return fail(st, "%s", msg); }
+
+// ---------------------------------------------------------------------------
+// The learned initialiser on a series: input pairs from the pyramid level of
+// 257^2 nodes (256^2 of them: the last row and column dropped), predictions
+// upsampled onto the finest vertex grid (pixels) in the data slots.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_cnn_pairs(const void *pyr, int64_t frame_block, int64_t img_off, int pitch, int bf16, int first,
+                            int side, float *x)
+{
+    const int p = blockIdx.z, ch = blockIdx.y;  // pair p of the chunk, channel (0 reference, 1 template)
+    const int frame = first + p + ch;
+    const int64_t base = (int64_t)frame * frame_block + img_off;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < side * side; i += gridDim.x * blockDim.x) {
+        const int r = i / side, c = i % side;
+        const int64_t o = base + (int64_t)r * pitch + c;
+        const float v = bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(pyr)[o])
+                             : reinterpret_cast<const float *>(pyr)[o];
+        x[((int64_t)p * 2 + ch) * side * side + i] = v;
+    }
+}
+
+// Output (2 x q x q, input pixels at input pixels 4i, 4j) -> displacement in
+// frame pixels on the (side+1)^2 grid of the slot: bilinear in the output grid,
+// clamped at its border, scaled by k = side / (4 q) frame pixels per input pixel.
+__global__ void k_cnn_to_slot(const float *y, int q, int side, float2 *slot, int pitch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r > side || c > side) return;
+    const float k = (float)side / (4.f * q);
+    auto coord = [&](int i, int &i0, float &f) {
+        const float t = (float)i / (4.f * k);
+        i0 = min(max((int)floorf(t), 0), q - 2);
+        f = fminf(fmaxf(t - i0, 0.f), 1.f);
+    };
+    int r0, c0;
+    float fr, fc;
+    coord(r, r0, fr);
+    coord(c, c0, fc);
+    float2 o;
+    for (int ch = 0; ch < 2; ch++) {
+        const float *m = y + (int64_t)ch * q * q;
+        const float top = (1.f - fc) * m[r0 * q + c0] + fc * m[r0 * q + c0 + 1];
+        const float bot = (1.f - fc) * m[(r0 + 1) * q + c0] + fc * m[(r0 + 1) * q + c0 + 1];
+        const float v = k * ((1.f - fr) * top + fr * bot);
+        if (ch == 0) o.x = v; else o.y = v;
+    }
+    slot[(int64_t)r * pitch + c] = o;
+}
+
+// Index of the pyramid level with 257^2 nodes, or -1.
+int cnn_level(const SeriesInfo &si)
+{
+    for (int k = 0; k < si.nl; k++)
+        if (si.n[k] == 257) return k;
+    return -1;
+}
+
+}  // namespace
+
+reg_status reg_cnn_pairs(reg_series_t s, int32_t series, int32_t first_pair, int32_t count, float *x)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size() || !x || count < 1) return fail(REG_EINVAL, "bad argument");
+    const SeriesInfo &si = s->S[series];
+    if (first_pair < 0 || first_pair + count > si.n_data) return fail(REG_EINVAL, "pair range outside the series");
+    const int k = cnn_level(si);
+    if (k < 0) return fail(REG_EINVAL, "the pyramid has no level of 257^2 nodes");
+    k_cnn_pairs<<<dim3(64, 2, count), 256, 0, s->stream>>>(si.pyr, (int64_t)si.frame_block, (int64_t)si.img_off[k],
+                                                            si.pitch[k], s->bf16, first_pair, 256, x);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int32_t tensor_cores)
+{
+    g_err.clear();
+    if (!s || !h || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad argument");
+    SeriesInfo &si = s->S[series];
+    if (cnn_input_side(h) != 256) return fail(REG_EINVAL, "the network must take 256^2 inputs");
+    const int k = cnn_level(si);
+    if (k < 0) return fail(REG_EINVAL, "the pyramid has no level of 257^2 nodes");
+    const int B = cnn_max_batch(h), q = (int)cnn_output_side(h), nL = si.n[si.nl - 1];
+    float *x = nullptr, *y = nullptr;
+    RET(dalloc(s, (void **)&x, sizeof(float) * (size_t)B * 2 * 256 * 256));
+    reg_status st = dalloc(s, (void **)&y, sizeof(float) * (size_t)B * 2 * q * q);
+    for (int p0 = 0; st == REG_OK && p0 < si.n_data; p0 += B) {
+        const int cnt = std::min(B, si.n_data - p0);
+        k_cnn_pairs<<<dim3(64, 2, cnt), 256, 0, s->stream>>>(si.pyr, (int64_t)si.frame_block,
+                                                              (int64_t)si.img_off[k], si.pitch[k], s->bf16, p0, 256, x);
+        st = cnn_forward(h, x, cnt, y, s->stream, tensor_cores != 0);
+        for (int e = 0; st == REG_OK && e < cnt; e++)
+            k_cnn_to_slot<<<dim3(cdiv(nL, 32), cdiv(nL, 8)), dim3(32, 8), 0, s->stream>>>(
+                y + (size_t)e * 2 * q * q, q, nL - 1, si.slots + (size_t)(p0 + e) * si.slot_elems, si.pitch[si.nl - 1]);
+        if (st == REG_OK && cudaGetLastError() != cudaSuccess) st = fail(REG_ECUDA, "learned initialiser kernels");
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess && st == REG_OK) st = fail(REG_ECUDA, "sync");
+    dfree(s, x, 0);
+    dfree(s, y, 0);
+    if (st == REG_OK) si.pre_from_slots = true;
+    return st;
+}

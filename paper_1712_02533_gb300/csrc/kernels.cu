@@ -129,15 +129,6 @@ __device__ __forceinline__ float2 sample2(const float2 *f, int n, int pitch, int
     return o;
 }
 
-// 1D FE mass weight (in units of h) at node i for neighbour offset a in {-1,0,1}
-// of piecewise-linear hats with natural boundary.
-__device__ __forceinline__ float m1w(int i, int a, int n)
-{
-    if (a == 0) return (i == 0 || i == n - 1) ? (2.f / 6.f) : (4.f / 6.f);
-    int j = i + a;
-    return (j >= 0 && j < n) ? (1.f / 6.f) : 0.f;
-}
-
 __device__ __forceinline__ int find_entry(const int *pref, int nent, int item)
 {
     // largest e with pref[e] <= item

@@ -1,0 +1,97 @@
+"""The learned initialiser on the GPU through the C-ABI: forward pass, loss and
+gradients against the FP64 oracle (oracle/cnn.py), the Adam step against its
+definition, the network inputs against the normalised frames, and what the
+trained network gains over the identity start."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def reg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as r
+    return r
+
+
+def test_forward_loss_and_gradients_match_the_oracle(reg):
+    import torch
+    import synth
+    from oracle import cnn as ocnn
+    rng = np.random.default_rng(0)
+    theta = (synth.cnn_params(3) + 0.01 * rng.standard_normal(ocnn.n_params())).astype(np.float32)
+    x = rng.standard_normal((2, 2, 64, 64)).astype(np.float32)
+    t = rng.standard_normal((2, 2, 16, 16)).astype(np.float32)
+    with reg.Cnn(theta, side=64, max_batch=4) as net:
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        y = net.forward(xd).cpu().numpy()
+        loss, g = net.loss_grad(xd, td, want_grad=True)
+    th, x64, t64 = theta.astype(np.float64), x.astype(np.float64), t.astype(np.float64)
+    yo = ocnn.forward(th, x64)
+    lo, go = ocnn.loss_and_grad(th, x64, t64)
+    assert np.abs(y - yo).max() <= 1e-5 * np.abs(yo).max()
+    assert abs(loss - lo) <= 1e-6 * lo
+    for k, ((gw, gb), (ow, ob)) in enumerate(zip(ocnn.unpack(g.astype(np.float64)), ocnn.unpack(go))):
+        assert np.abs(gw - ow).max() <= 1e-5 * np.abs(ow).max(), k
+        assert np.abs(gb - ob).max() <= 1e-5 * np.abs(ob).max(), k
+
+
+def test_adam_step_follows_its_definition(reg):
+    import torch
+    import synth
+    rng = np.random.default_rng(1)
+    theta = synth.cnn_params(4)
+    x = torch.from_numpy(rng.standard_normal((2, 2, 32, 32)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((2, 2, 8, 8)).astype(np.float32)).cuda()
+    with reg.Cnn(theta, side=32, max_batch=2) as net:
+        _, g = net.loss_grad(x, t, want_grad=True)
+        net.adam_step(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8)
+        got = net.get_params()
+    g = g.astype(np.float64)
+    m, v = 0.1 * g, 0.001 * g * g
+    want = theta - 1e-2 * (m / 0.1) / (np.sqrt(v / 0.001) + 1e-8)
+    assert np.abs(got - want).max() <= 1e-6 * max(1.0, np.abs(want).max())
+
+
+def test_network_inputs_are_the_normalised_257_level(reg, orc, syn):
+    import torch
+    fr = syn.series(21, 3, 256, spacing=12.0, sigma=2.0, peak=10.0)
+    x = torch.empty((2, 2, 256, 256), dtype=torch.float32, device="cuda")
+    with reg.Series(fr, reg.default_params(n_levels=3)) as s:
+        s.cnn_pairs(0, 2, x)
+    x = x.cpu().numpy()
+    for e in range(2):
+        for ch in range(2):
+            F = orc.embed(fr[e + ch])
+            w = orc.lumped(F.shape[0])
+            Fc = F - float(np.sum(w * F))
+            want = Fc / np.sqrt(float(np.sum(Fc * orc.mass_apply(Fc))))
+            assert np.abs(x[e, ch] - want[:256, :256]).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_trained_network_gains_over_the_identity_start(reg, syn):
+    """Trained on 512 pairs of large-motion series (plain-method targets), the
+    network's initial displacements bring the registered series of a held-out
+    series closer to the generator's ground truth than the identity start."""
+    import torch
+    from paper_1712_02533_gb300 import learned
+    X, T = learned.training_set(512, seed=100)
+    with reg.Cnn(syn.cnn_params(1), side=256, max_batch=64) as net:
+        hist = learned.train(net, X, T, epochs=12, batch=32, lr=1e-3)
+        assert hist[-1] < 0.5 * hist[0]
+        fr, gt, _ = syn.series(999, 24, 256, ground_truth=True, **learned.TRAIN_SERIES)
+        p = reg.default_params(n_levels=3, iter_max=50, lam=10.0)
+        err = {}
+        for name in ("identity", "learned"):
+            with reg.Series(fr, p) as s:
+                if name == "learned":
+                    s.cnn_init(net)
+                s.prefix_scan(reg.SKLANSKY)
+                d = s.get_deformations()
+            err[name] = float(np.abs(d[1:] - gt[1:])[:, :, 16:-16, 16:-16].mean())
+    assert err["learned"] < 0.8 * err["identity"], err
