@@ -13,7 +13,11 @@ The network predicts a coarse initial displacement for a frame pair:
 
 A convolution of stride s computes, for output channel o at (y, x),
     out[o, y, x] = b[o] + sum_{c, dy, dx} W[o, c, dy, dx] in_pad[c, s y + dy, s x + dx]
-with in_pad the input with one ring of zeros.  The loss is the mean of the
+with in_pad the input with one ring of zeros.  The tensor-core form of the
+forward rounds the operands of the 32 -> 32 layers (their input activations and
+weights, not the biases) to BF16 (8 significant bits, round to nearest, ties to
+even) and contracts them exactly; ``forward(..., bf16_layers=(1, 2, 3, 4))``
+models that.  The loss is the mean of the
 squared differences to a target displacement.  Parameters are one flat vector:
 layer by layer, W (O x C x 3 x 3, row-major) then b (O).
 """
@@ -82,13 +86,27 @@ def conv_backward(x, W, stride, gout):
     return gxp[:, :, 1:-1, 1:-1], gW, gout.sum(axis=(0, 2, 3))
 
 
-def forward(theta, x, keep=False):
+def round_bf16(v):
+    """v rounded to the nearest BF16 value (the float32 value's top 16 bits after
+    rounding to nearest, ties to even), returned in float64; v is first rounded
+    to float32."""
+    f = np.ascontiguousarray(np.asarray(v, np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, x, keep=False, bf16_layers=()):
     """Network output for inputs x (B, 2, S, S); with keep, also the layer inputs
-    and pre-activations for backward()."""
+    and pre-activations for backward(); layers listed in bf16_layers take BF16
+    operands."""
     layers = unpack(theta)
     a, cache = np.asarray(x, np.float64), []
     for k, ((W, b), (_, _, s)) in enumerate(zip(layers, LAYERS)):
-        z = conv_forward(a, W, b, s)
+        if k in bf16_layers:
+            z = conv_forward(round_bf16(a), round_bf16(W), b, s)
+        else:
+            z = conv_forward(a, W, b, s)
         cache.append((a, z))
         a = z if k == len(LAYERS) - 1 else np.maximum(z, 0.0)
     return (a, cache) if keep else a

@@ -10,8 +10,8 @@
 // Parameters: one flat float vector, layer by layer W (O x C x 3 x 3) then b.
 //
 // Layout: activations NCHW in float, one buffer per layer.  Training kernels
-// run on the CUDA cores in FP32; the inference path (k_conv_fwd_tc) runs the
-// 32-channel layers on the tensor cores (BF16 operands, FP32 accumulation).
+// run on the CUDA cores in FP32; the inference path can run the four
+// 32 -> 32 layers on the tensor cores (BF16 operands, FP32 accumulation).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -251,7 +251,6 @@ struct reg_cnn {
     float *gy = nullptr;
     double *partial = nullptr, *loss = nullptr;
     int64_t step = 0;
-    int use_tc = 1;
 };
 
 namespace {

@@ -41,6 +41,36 @@ def test_forward_loss_and_gradients_match_the_oracle(reg):
         assert np.abs(gb - ob).max() <= 1e-5 * np.abs(ob).max(), k
 
 
+@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3)])
+def test_tensor_core_forward_matches_the_bf16_operand_oracle(reg, side, batch):
+    """The 32 -> 32 layers on the tensor cores take BF16 operands and accumulate
+    in FP32: against the oracle with the same operand rounding the output agrees
+    to FP32 accumulation plus the rare operand that rounds the other way (its
+    FP32 input differs from the FP64 one in the last bits); against the exact
+    oracle it differs by the BF16 operand error.  Side 36 leaves 81 pixels per
+    pair in the 32-channel layers, a ragged last tile."""
+    import torch
+    import synth
+    from oracle import cnn as ocnn
+    rng = np.random.default_rng(side)
+    theta = synth.cnn_params(6)
+    x = rng.standard_normal((batch, 2, side, side)).astype(np.float32)
+    with reg.Cnn(theta, side=side, max_batch=batch) as net:
+        xd = torch.from_numpy(x).cuda()
+        y_tc = net.forward(xd, tensor_cores=True).cpu().numpy().astype(np.float64)
+        y_f32 = net.forward(xd).cpu().numpy().astype(np.float64)
+    th, x64 = theta.astype(np.float64), x.astype(np.float64)
+    y_exact = ocnn.forward(th, x64)
+    y_bf16 = ocnn.forward(th, x64, bf16_layers=(1, 2, 3, 4))
+    scale = np.abs(y_exact).max()
+    assert np.abs(y_tc - y_bf16).max() <= 2e-3 * scale
+    assert np.median(np.abs(y_tc - y_bf16)) <= 1e-5 * scale
+    assert np.abs(y_tc - y_exact).max() <= 5e-2 * scale
+    # the FP32 path is the exact one; the tensor-core path is not the same code
+    assert np.abs(y_f32 - y_exact).max() <= 1e-5 * scale
+    assert np.abs(y_tc - y_f32).max() > 1e-4 * scale
+
+
 def test_adam_step_follows_its_definition(reg):
     import torch
     import synth
@@ -87,11 +117,12 @@ def test_trained_network_gains_over_the_identity_start(reg, syn):
         fr, gt, _ = syn.series(999, 24, 256, ground_truth=True, **learned.TRAIN_SERIES)
         p = reg.default_params(n_levels=3, iter_max=50, lam=10.0)
         err = {}
-        for name in ("identity", "learned"):
+        for name in ("identity", "learned", "learned_tc"):
             with reg.Series(fr, p) as s:
-                if name == "learned":
-                    s.cnn_init(net)
+                if name != "identity":
+                    s.cnn_init(net, tensor_cores=name == "learned_tc")
                 s.prefix_scan(reg.SKLANSKY)
                 d = s.get_deformations()
             err[name] = float(np.abs(d[1:] - gt[1:])[:, :, 16:-16, 16:-16].mean())
     assert err["learned"] < 0.8 * err["identity"], err
+    assert err["learned_tc"] < 0.8 * err["identity"], err

@@ -116,3 +116,41 @@ def test_upsampling_reproduces_constant_and_linear_fields():
     inside = r <= q - 1
     assert np.allclose(up[0][:, inside], 4 * r[inside][None, :])
     assert np.allclose(up[1][inside, :], 4 * r[inside][:, None])
+
+
+def test_bf16_rounding_exact_cases():
+    """BF16 keeps 8 significant bits: 1 + 2^-7 is representable, 1 + 2^-8 lies
+    halfway between 1 and 1 + 2^-7 and rounds to the even neighbour 1, 1 + 3 2^-8
+    rounds up to 1 + 2^-6, and sign, zero and powers of two pass unchanged."""
+    v = np.array([1 + 2.0 ** -7, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -12,
+                  -(1 + 2.0 ** -8 + 2.0 ** -12), 0.0, 2.0 ** -40, -1024.0])
+    want = [1 + 2.0 ** -7, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, -(1 + 2.0 ** -7), 0.0, 2.0 ** -40, -1024.0]
+    assert cnn.round_bf16(v).tolist() == want
+
+
+def test_bf16_rounding_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    v = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.round_bf16(v), want)
+
+
+def test_bf16_forward_error_is_within_the_operand_rounding_bound():
+    """Rounding to 8 significant bits moves each operand by at most 2^-8 of its
+    size, so each product by at most (1 + 2^-8)^2 - 1 = 2^-7 + 2^-16 of its size
+    and a layer output by at most that times the sum of its absolute products;
+    the untouched layers give identical results."""
+    import synth
+    rng = np.random.default_rng(10)
+    theta = synth.cnn_params(5).astype(np.float64)
+    x = rng.standard_normal((1, 2, 16, 16))
+    assert np.array_equal(cnn.forward(theta, x), cnn.forward(theta, x, bf16_layers=()))
+    layers = cnn.unpack(theta)
+    a = cnn.forward(theta, x, keep=True)[1][1][0]  # input of layer 1
+    W, b = layers[1]
+    exact = cnn.conv_forward(a, W, b, 2)
+    rounded = cnn.conv_forward(cnn.round_bf16(a), cnn.round_bf16(W), b, 2)
+    bound = cnn.conv_forward(np.abs(a), np.abs(W), 0 * b, 2) * (2.0 ** -7 + 2.0 ** -16)
+    assert np.all(np.abs(rounded - exact) <= bound)
+    assert np.abs(rounded - exact).max() > 0
