@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--levels", type=int, default=WORKLOAD["n_levels"])
     ap.add_argument("--preprocess-only", action="store_true",
                     help="a step is the preprocessing batch only (profiling case)")
+    ap.add_argument("--autotune", type=int, default=64,
+                    help="pairs in the tile autotuner's sample batch before timing (0: default tiles)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -239,6 +241,11 @@ def main():
 
     n_pre = cfg["n_frames"] - 1
     pre_ops = [(0, -1, -1, e, e, e + 1) for e in range(n_pre)]
+    tiles = None
+    if a.autotune > 0:
+        t0 = time.time()
+        tiles = s.autotune(n_pairs=min(a.autotune, n_pre), repeats=1)
+        tiles["tune_s"] = round(time.time() - t0, 1)
 
     def step():
         if a.preprocess_only:
@@ -290,11 +297,15 @@ def main():
         host = torch.from_numpy(frames).pin_memory()
         out = torch.empty((cfg["n_frames"], 2, cfg["side"], cfg["side"]), dtype=torch.float32).pin_memory()
         p2 = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"])
+        if tiles:
+            p2.trials_per_pass = tiles["trials_per_pass"]
         e2e_steps = max(1, min(a.steps, 2))
         barrier()
         t = time.time()
         for _ in range(e2e_steps):
             with reg.Series([host], p2) as s2:
+                for lv in (tiles or {}).get("levels", []):  # the tuned table, as a user reuses it
+                    s2.set_tile_rows(lv["level"], lv["grad_rows"], lv["trial_rows"])
                 r2 = s2.prefix_scan(kind, a.chunks, reg.KOGGE_STONE)
                 s2.get_deformations(out=out)
         barrier()
@@ -319,6 +330,7 @@ def main():
                        "ops_per_step": ops_per_step, "preprocessing_ops": rep["preprocessing_ops"],
                        "scan_ops": rep["scan_ops"], "scan_batches": rep["scan_batches"],
                        "iters_per_step": rep["iters"], "l2": "working set (GBs) larger than L2; no flush",
+                       "tiles": tiles,
                        "generator_s": round(gen_s, 1), "create_ms": round(create_s * 1e3, 1)},
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks,

@@ -76,7 +76,12 @@ typedef struct reg_allocator {
  * criteria per level; lambda: regulariser weight; armijo_sigma, tau_*: step
  * rule (Section "Gradient flow").  trials_per_pass (1..8): how many step
  * sizes of the Armijo sequence one energy pass evaluates at once (does not
- * change the accepted step).  storage: pyramid storage precision. */
+ * change the accepted step).  storage: pyramid storage precision.
+ * init_levels: pyramid levels (the finest ones) that a preprocessing operator
+ * runs when it starts from a learned initial displacement
+ * (reg_cnn_init_series); 0 means n_levels.  The coarse levels exist to bring
+ * a far start into the basin of the fine ones; a start that is already there
+ * can skip them. */
 typedef struct reg_params {
     int32_t n_levels;
     int32_t iter_max;
@@ -90,6 +95,7 @@ typedef struct reg_params {
     int32_t trials_per_pass;
     int32_t max_steps;        /* device step budget per batch; <= 0: automatic */
     int32_t flags;            /* REG_FLAG_* */
+    int32_t init_levels;      /* 0 or 1..n_levels, see above */
     reg_allocator allocator;
 } reg_params;
 
@@ -97,7 +103,7 @@ typedef struct reg_params {
 
 /* Fills *p with the defaults: n_levels 3, iter_max 50, epsilon 1e-7,
  * lambda 10, sigma 0.5, tau_init 1, tau_max 1e4, tau_min 1e-12, F32 storage,
- * 4 trials per pass. */
+ * 4 trials per pass, init_levels 0. */
 void reg_default_params(reg_params *p);
 
 /* One operator application (Section "Registration for series of images").
@@ -250,9 +256,31 @@ reg_status reg_cnn_pairs(reg_series_t s, int32_t series, int32_t first_pair, int
 /* Predict the initial displacement of every neighbour pair of a series with a
  * network for 256^2 inputs, upsample it (bilinear in the output grid, clamped)
  * onto the finest vertex grid in frame pixels, and store it in the pair's data
- * slot; the next reg_prefix_scan starts those preprocessing operators from the
- * slots instead of the identity. */
+ * slot (reg_get_slot reads it back); the next reg_prefix_scan starts those
+ * preprocessing operators from the slots instead of the identity, on the
+ * finest reg_params.init_levels levels. */
 reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int32_t tensor_cores);
+
+/* Tiles of the step kernels.  The gradient and trial passes walk strip tiles
+ * of 30 node columns (gradient) or 31 cell columns (trial) by a number of rows
+ * chosen per pyramid level l (2^l + 1 nodes per side); defaults 8 (l <= 6),
+ * 16 (l <= 8), 32.  Rows must be 4, 8, 16, 32 or 64 (REG_EINVAL otherwise).
+ * The rows change which FP32 partial sums are formed before the FP64 sum over
+ * tiles, so results can differ at the rounding level. */
+reg_status reg_set_tile_rows(reg_series_t s, int32_t level, int32_t grad_rows, int32_t trial_rows);
+reg_status reg_get_tile_rows(reg_series_t s, int32_t level, int32_t *grad_rows, int32_t *trial_rows);
+/* Tile autotuner: times a sample batch of function A on the neighbour pairs
+ * 0..n_pairs-1 of `series` (best of `repeats` runs) and picks, level by level
+ * from the finest (levels of at least 129 nodes), the gradient and trial tile
+ * rows with the shortest time per device step, then the step sizes per trial
+ * pass (2, 4 or 8) with the shortest batch time; a change must gain 2%.  The
+ * result stays in the handle (reg_get_tile_rows, and reg_params'
+ * trials_per_pass as the handle uses it).  It overwrites the data slots
+ * 0..n_pairs-1 (and drops a pending learned start): call it before
+ * reg_prefix_scan, reg_set_slot or reg_cnn_init_series.  report (may be NULL):
+ * a JSON object with the chosen table and the sample's time before and after. */
+reg_status reg_autotune(reg_series_t s, int32_t series, int32_t n_pairs, int32_t repeats, char *report,
+                        size_t buf_len);
 
 /* Schedule export (host only, no GPU work): writes the op list of a schedule
  * over n elements as reg_schedule_op records (level index, kind, slots) into

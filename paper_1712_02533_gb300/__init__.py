@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("armijo_sigma", ctypes.c_double), ("tau_init", ctypes.c_double),
                 ("tau_max", ctypes.c_double), ("tau_min", ctypes.c_double), ("storage", ctypes.c_int32),
                 ("trials_per_pass", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("allocator", Allocator)]
+                ("init_levels", ctypes.c_int32), ("allocator", Allocator)]
 
 
 class OpDesc(ctypes.Structure):
@@ -82,6 +82,9 @@ def _load():
         "reg_create_series": ([vp, i32, vp, vp, i64, i32, P(Params), vp, P(vp)], ctypes.c_int),
         "reg_apply_operator_batch": ([vp, i32, vp, vp, vp], ctypes.c_int),
         "reg_prefix_scan": ([vp, ctypes.c_int, i32, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+        "reg_set_tile_rows": ([vp, i32, i32, i32], ctypes.c_int),
+        "reg_get_tile_rows": ([vp, i32, P(i32), P(i32)], ctypes.c_int),
+        "reg_autotune": ([vp, i32, i32, i32, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "reg_get_deformations": ([vp, i32, i32, i32, vp, i32], ctypes.c_int),
         "reg_get_slot": ([vp, i32, i32, vp, i32, vp], ctypes.c_int),
         "reg_set_slot": ([vp, i32, i32, vp, i32, i32, i32], ctypes.c_int),
@@ -468,6 +471,21 @@ class Series:
         tensor out (count x 2 x 256 x 256)."""
         _check(_load().reg_cnn_pairs(self.h, series, first, count, out.data_ptr()))
         return out
+
+    def set_tile_rows(self, level, grad_rows, trial_rows):
+        _check(_load().reg_set_tile_rows(self.h, level, grad_rows, trial_rows))
+
+    def get_tile_rows(self, level):
+        g, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(_load().reg_get_tile_rows(self.h, level, ctypes.byref(g), ctypes.byref(t)))
+        return g.value, t.value
+
+    def autotune(self, n_pairs=16, repeats=1, series=0):
+        """Tile rows per level and step sizes per pass picked by timing a sample
+        batch (overwrites data slots 0..n_pairs-1); returns the report."""
+        buf = ctypes.create_string_buffer(4096)
+        _check(_load().reg_autotune(self.h, series, n_pairs, repeats, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def cnn_init(self, cnn, series=0, tensor_cores=False):
         """Initial displacements of all neighbour pairs from the network; the next

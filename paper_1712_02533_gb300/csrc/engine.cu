@@ -98,9 +98,19 @@ struct FamilyStats {
 struct OpReq {
     int series, frame_i, frame_k, init;
     int left, right, dst;  // slot indices (-1 none)
+    int skip = 0;          // coarse pyramid levels the operator leaves out
 };
 
 constexpr int GRAPH_STEPS = 8;
+constexpr int REG_TILE_LEVELS = 16;
+
+// l with n = 2^l + 1
+inline int level_of(int n)
+{
+    int l = 0;
+    while ((1 << l) + 1 < n) l++;
+    return l;
+}
 constexpr int NFAM = 6;  // P, G, T, C, plan, setup
 enum { F_P = 0, F_G, F_T, F_C, F_PLAN, F_SETUP };
 
@@ -113,6 +123,8 @@ struct reg_series {
     int bf16 = 0;
     int nsm = 0;
     int grid_P = 0, grid_G = 0, grid_T = 0;  // resident-block grids of the step kernels
+    // strip rows of the gradient and trial tiles per level l (2^l + 1 nodes)
+    int tile_hg[REG_TILE_LEVELS] = {0}, tile_ht[REG_TILE_LEVELS] = {0};
     std::vector<SeriesInfo> S;
     std::vector<void *> allocs;
     // batch buffers
@@ -232,13 +244,32 @@ BatchDev make_batch(reg_series *s)
 
 // Work items per operator at a level of n nodes per side: the largest of the
 // prolongation block tiles and the gradient and trial strip tiles.
-int max_tiles(int n)
+int max_tiles(const reg_series *s, int n)
 {
+    const int l = level_of(n);
     int p = cdiv(n, REG_TX) * cdiv(n, REG_TY);
-    int h = strip_rows(n);
-    int g = cdiv(n, REG_GW) * cdiv(n, h);
-    int t = cdiv(n - 1, REG_CW) * cdiv(n - 1, h);
+    int g = cdiv(n, REG_GW) * cdiv(n, s->tile_hg[l]);
+    int t = cdiv(n - 1, REG_CW) * cdiv(n - 1, s->tile_ht[l]);
     return std::max(p, std::max(g, t));
+}
+
+// The largest max_tiles over the levels of a series (from level index k0).
+int max_tiles_series(const reg_series *s, const SeriesInfo &si, int k0 = 0)
+{
+    int m = 0;
+    for (int k = k0; k < si.nl; k++) m = std::max(m, max_tiles(s, si.n[k]));
+    return m;
+}
+
+void fill_level(const reg_series *s, LevelDesc &L, int n, int pitch)
+{
+    L.n = n;
+    L.pitch = pitch;
+    L.hg = s->tile_hg[level_of(n)];
+    L.ht = s->tile_ht[level_of(n)];
+    const double h = 1.0 / (n - 1);
+    L.h2d = h * h;
+    L.h2 = (float)L.h2d;
 }
 
 reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t items_per_op)
@@ -346,7 +377,7 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
     for (auto &o : ops) {
         const SeriesInfo &si = s->S[o.series];
         ws = std::max(ws, si.ws_bytes);
-        items = std::max<int64_t>(items, max_tiles(si.n[si.nl - 1]));
+        items = std::max<int64_t>(items, max_tiles_series(s, si, o.skip));
         nl = std::max(nl, si.nl);
         nLmax = std::max(nLmax, si.n[si.nl - 1]);
     }
@@ -356,20 +387,17 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
         const SeriesInfo &si = s->S[o.series];
         OpDesc &d = s->h_ops[i];
         memset(&d, 0, sizeof(d));
-        d.nl = si.nl;
+        d.nl = si.nl - o.skip;
         d.init = o.init;
         d.left = o.left >= 0 ? si.slots + (size_t)o.left * si.slot_elems : nullptr;
         d.right = o.right >= 0 ? si.slots + (size_t)o.right * si.slot_elems : nullptr;
         d.out = si.slots + (size_t)o.dst * si.slot_elems;
         d.slot_pitch = si.pitch[si.nl - 1];
         char *w = s->d_ws + (size_t)i * ws;
-        for (int k = 0; k < si.nl; k++) {
-            LevelDesc &L = d.lv[k];
-            L.n = si.n[k];
-            L.pitch = si.pitch[k];
-            double h = 1.0 / (L.n - 1);
-            L.h2d = h * h;
-            L.h2 = (float)L.h2d;
+        for (int j = 0; j < d.nl; j++) {
+            const int k = o.skip + j;  // level index within the series' pyramid
+            LevelDesc &L = d.lv[j];
+            fill_level(s, L, si.n[k], si.pitch[k]);
             L.R = img_ptr(s, si, o.frame_i, k);
             L.T = img_ptr(s, si, o.frame_k, k);
             L.MR = si.mr + (size_t)o.frame_i * si.frame_block + si.img_off[k];
@@ -457,6 +485,19 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
     return REG_OK;
 }
 
+// Resident-block grids of the step kernels (the trial kernel's depends on the
+// step sizes per pass).
+void set_grids(reg_series *s)
+{
+    auto grid_of = [&](int which) {
+        int occ = step_blocks_per_sm(which, s->p.trials_per_pass);
+        return s->nsm * std::max(1, std::min(occ, 32));
+    };
+    s->grid_P = grid_of(0);
+    s->grid_G = grid_of(1);
+    s->grid_T = grid_of(2);
+}
+
 reg_status validate_params(const reg_params *p)
 {
     if (p->iter_max < 1 || p->iter_max > 100000) return fail(REG_EINVAL, "iter_max out of range");
@@ -467,6 +508,8 @@ reg_status validate_params(const reg_params *p)
     if (p->trials_per_pass < 1 || p->trials_per_pass > REG_MAX_TRIALS)
         return fail(REG_EINVAL, "trials_per_pass must be in [1, %d]", REG_MAX_TRIALS);
     if (p->storage != REG_STORAGE_F32 && p->storage != REG_STORAGE_BF16) return fail(REG_EINVAL, "bad storage");
+    if (p->init_levels < 0 || p->init_levels > p->n_levels)
+        return fail(REG_EINVAL, "init_levels must be in [0, n_levels]");
     return REG_OK;
 }
 
@@ -548,13 +591,8 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
     s->p = *p;
     s->bf16 = p->storage == REG_STORAGE_BF16;
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
-    auto grid_of = [&](int which) {
-        int occ = step_blocks_per_sm(which, p->trials_per_pass);
-        return s->nsm * std::max(1, std::min(occ, 32));
-    };
-    s->grid_P = grid_of(0);
-    s->grid_G = grid_of(1);
-    s->grid_T = grid_of(2);
+    set_grids(s);
+    for (int l = 0; l < REG_TILE_LEVELS; l++) s->tile_hg[l] = s->tile_ht[l] = strip_rows((1 << l) + 1);
     CK(cudaMallocHost((void **)&s->h_ctr, sizeof(int) * 16));
     s->ev_ok = true;
     for (int k = 0; k < GRAPH_STEPS && s->ev_ok; k++) {
@@ -764,11 +802,15 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
         for (auto &m : S.meta) m = SlotMeta{};
         // identity start, or (after reg_cnn_init_series) the slot's initial guess
         for (int e = 0; e < S.n_data; e++)
-            pre.push_back(S.pre_from_slots ? OpReq{si, e, e + 1, 1, e, -1, e} : OpReq{si, e, e + 1, 0, -1, -1, e});
+            pre.push_back(S.pre_from_slots
+                              ? OpReq{si, e, e + 1, 1, e, -1, e, s->p.init_levels ? S.nl - s->p.init_levels : 0}
+                              : OpReq{si, e, e + 1, 0, -1, -1, e});
         S.pre_from_slots = false;
     }
     std::vector<int32_t> stat(pre.size());
-    RET(run_batch(s, pre, [] { return REG_OK; }, stat.data(), nullptr));
+    RET(run_batch(s, pre, [] { return REG_OK; }, stat.data(), nullptr));  // returns after a sync
+    const double pre_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int64_t pre_iters = s->tot_iters - it0;
     int counts[5] = {0, 0, 0, 0, 0};
     for (auto v : stat) counts[std::min(std::max(v, 0), 4)]++;
     for (auto &o : pre) s->S[o.series].meta[o.dst] = SlotMeta{o.frame_i, o.frame_k};
@@ -832,11 +874,12 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
             if (S.meta[e].start != 0 || S.meta[e].end != e + 1) return fail(REG_EKERNEL, "scan did not produce phi_{0,%d}", e + 1);
     if (report && buf_len > 0) {
         snprintf(report, buf_len,
-                 "{\"kind\": %d, \"preprocessing_ops\": %zu, \"scan_ops\": %d, \"scan_batches\": %d, "
+                 "{\"kind\": %d, \"preprocessing_ops\": %zu, \"preprocessing_ms\": %.3f, "
+                 "\"preprocessing_iters\": %lld, \"scan_ops\": %d, \"scan_batches\": %d, "
                  "\"ops\": %lld, \"iters\": %lld, \"trials\": %lld, \"evals\": %lld, \"steps\": %lld, \"ms\": %.3f, "
                  "\"grids\": [%d, %d, %d], "
                  "\"status\": {\"converged\": %d, \"maxiter\": %d, \"stalled\": %d, \"nonfinite\": %d, \"zero_gradient\": %d}}",
-                 (int)kind, pre.size(), scan_ops, batches, (long long)(s->tot_ops - ops0),
+                 (int)kind, pre.size(), pre_ms, (long long)pre_iters, scan_ops, batches, (long long)(s->tot_ops - ops0),
                  (long long)(s->tot_iters - it0), (long long)(s->tot_trials - tr0), (long long)(s->tot_evals - ev0),
                  (long long)(s->tot_steps - st0), ms, s->grid_P, s->grid_G, s->grid_T, counts[0], counts[1], counts[2],
                  counts[3], counts[4]);
@@ -959,7 +1002,7 @@ static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int leve
     if (k < 0 || k >= si.nl) return fail(REG_EINVAL, "level outside the pyramid");
     if (!u_grid) return fail(REG_EINVAL, "null displacement");
     std::vector<OpReq> one{OpReq{series, fi, fk, 0, -1, -1, 0}};
-    RET(ensure_capacity(s, 1, si.ws_bytes, max_tiles(si.n[si.nl - 1])));
+    RET(ensure_capacity(s, 1, si.ws_bytes, max_tiles_series(s, si)));
     OpDesc &d = s->h_ops[0];
     memset(&d, 0, sizeof(d));
     d.nl = si.nl;
@@ -967,11 +1010,7 @@ static reg_status diag_setup(reg_series *s, int series, int fi, int fk, int leve
     d.out = nullptr;
     for (int q = 0; q < si.nl; q++) {
         LevelDesc &L = d.lv[q];
-        L.n = si.n[q];
-        L.pitch = si.pitch[q];
-        double h = 1.0 / (L.n - 1);
-        L.h2d = h * h;
-        L.h2 = (float)L.h2d;
+        fill_level(s, L, si.n[q], si.pitch[q]);
         L.R = img_ptr(s, si, fi, q);
         L.T = img_ptr(s, si, fk, q);
         L.MR = si.mr + (size_t)fi * si.frame_block + si.img_off[q];
@@ -1236,6 +1275,119 @@ reg_status reg_reset_kernel_stats(reg_series_t s)
     return REG_OK;
 }
 
+reg_status reg_set_tile_rows(reg_series_t s, int32_t level, int32_t grad_rows, int32_t trial_rows)
+{
+    g_err.clear();
+    if (!s || level < 1 || level >= REG_TILE_LEVELS) return fail(REG_EINVAL, "bad handle or level");
+    auto ok = [](int r) { return r == 4 || r == 8 || r == 16 || r == 32 || r == 64; };
+    if (!ok(grad_rows) || !ok(trial_rows)) return fail(REG_EINVAL, "tile rows must be 4, 8, 16, 32 or 64");
+    s->tile_hg[level] = grad_rows;
+    s->tile_ht[level] = trial_rows;
+    return REG_OK;
+}
+
+reg_status reg_get_tile_rows(reg_series_t s, int32_t level, int32_t *grad_rows, int32_t *trial_rows)
+{
+    g_err.clear();
+    if (!s || level < 1 || level >= REG_TILE_LEVELS || !grad_rows || !trial_rows)
+        return fail(REG_EINVAL, "bad argument");
+    *grad_rows = s->tile_hg[level];
+    *trial_rows = s->tile_ht[level];
+    return REG_OK;
+}
+
+reg_status reg_autotune(reg_series_t s, int32_t series, int32_t n_pairs, int32_t repeats, char *report,
+                        size_t buf_len)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad handle or series");
+    SeriesInfo &si = s->S[series];
+    if (n_pairs < 1 || n_pairs > si.n_data || repeats < 1) return fail(REG_EINVAL, "need 1 <= n_pairs <= frames - 1");
+    std::vector<OpReq> ops;
+    for (int e = 0; e < n_pairs; e++) ops.push_back(OpReq{series, e, e + 1, 0, -1, -1, e});
+    int runs = 0;
+    // best of `repeats` runs of the sample batch: wall time per device step
+    // (tile shapes change the per-step cost; the step count follows the Armijo
+    // decisions) and in total (step sizes per pass change the step count)
+    auto measure = [&](double &per_step, double &total) -> reg_status {
+        per_step = total = 1e300;
+        for (int r = 0; r < repeats; r++) {
+            const int64_t st0 = s->tot_steps;
+            const auto t0 = std::chrono::steady_clock::now();
+            RET(run_batch(s, ops, [] { return REG_OK; }, nullptr, nullptr));  // returns after a sync
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            total = std::min(total, ms);
+            per_step = std::min(per_step, ms / (double)std::max<int64_t>(1, s->tot_steps - st0));
+            runs++;
+        }
+        return REG_OK;
+    };
+    double ps, tot, ps0, tot0;
+    RET(run_batch(s, ops, [] { return REG_OK; }, nullptr, nullptr));  // warm-up: buffers, graph
+    RET(measure(ps0, tot0));
+    // coordinate descent, finest level first; a change must gain 2%
+    const int cand[] = {8, 16, 32, 64};
+    for (int k = si.nl - 1; k >= 0; k--) {
+        if (si.n[k] < 129) continue;  // launch-bound levels: the defaults
+        const int l = level_of(si.n[k]);
+        for (int which = 0; which < 2; which++) {
+            int *tab = which ? s->tile_ht : s->tile_hg;
+            const int keep0 = tab[l];
+            RET(measure(ps, tot));
+            double best = ps;
+            int keep = keep0;
+            for (int c : cand) {
+                if (c == keep0 || c > si.n[k]) continue;
+                tab[l] = c;
+                RET(measure(ps, tot));
+                if (ps < 0.98 * best) { best = ps; keep = c; }
+            }
+            tab[l] = keep;
+        }
+    }
+    // step sizes per Armijo pass
+    {
+        const int keep0 = s->p.trials_per_pass;
+        RET(measure(ps, tot));
+        double best = tot;
+        int keep = keep0;
+        for (int J : {2, 4, 8}) {
+            if (J == keep0) continue;
+            s->p.trials_per_pass = J;
+            set_grids(s);
+            s->buf_gen++;  // the captured graph launches the trial kernel for J
+            RET(measure(ps, tot));
+            if (tot < 0.98 * best) { best = tot; keep = J; }
+        }
+        s->p.trials_per_pass = keep;
+        set_grids(s);
+        s->buf_gen++;
+    }
+    double ps1, tot1;
+    RET(measure(ps1, tot1));
+    // the sample overwrote these data slots
+    for (int e = 0; e < n_pairs; e++) si.meta[e] = SlotMeta{};
+    si.pre_from_slots = false;
+    if (report && buf_len > 0) {
+        std::string js = "{\"levels\": [";
+        for (int k = 0; k < si.nl; k++) {
+            const int l = level_of(si.n[k]);
+            char b[128];
+            snprintf(b, sizeof b, "%s{\"level\": %d, \"n\": %d, \"grad_rows\": %d, \"trial_rows\": %d}", k ? ", " : "",
+                     l, si.n[k], s->tile_hg[l], s->tile_ht[l]);
+            js += b;
+        }
+        char b[256];
+        snprintf(b, sizeof b,
+                 "], \"trials_per_pass\": %d, \"sample_ops\": %d, \"runs\": %d, \"ms_before\": %.3f, "
+                 "\"ms_after\": %.3f}",
+                 s->p.trials_per_pass, n_pairs, runs, tot0, tot1);
+        js += b;
+        snprintf(report, buf_len, "%s", js.c_str());
+    }
+    return REG_OK;
+}
+
 }  // extern "C"
 
 reg_status reg_internal_fail(reg_status st, const char *msg) { return fail(st, "%s", msg); }
@@ -1332,9 +1484,11 @@ reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int3
         k_cnn_pairs<<<dim3(64, 2, cnt), 256, 0, s->stream>>>(si.pyr, (int64_t)si.frame_block,
                                                               (int64_t)si.img_off[k], si.pitch[k], s->bf16, p0, 256, x);
         st = cnn_forward(h, x, cnt, y, s->stream, tensor_cores != 0);
-        for (int e = 0; st == REG_OK && e < cnt; e++)
+        for (int e = 0; st == REG_OK && e < cnt; e++) {
             k_cnn_to_slot<<<dim3(cdiv(nL, 32), cdiv(nL, 8)), dim3(32, 8), 0, s->stream>>>(
                 y + (size_t)e * 2 * q * q, q, nL - 1, si.slots + (size_t)(p0 + e) * si.slot_elems, si.pitch[si.nl - 1]);
+            si.meta[p0 + e] = SlotMeta{p0 + e, p0 + e + 1};  // an initial guess of phi_{e,e+1}
+        }
         if (st == REG_OK && cudaGetLastError() != cudaSuccess) st = fail(REG_ECUDA, "learned initialiser kernels");
     }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess && st == REG_OK) st = fail(REG_ECUDA, "sync");

@@ -359,15 +359,13 @@ __global__ void k_init_state(BatchDev b, int n_ops)
 
 // work items per operator: prolongation block tiles, gradient and trial strip tiles
 __device__ __forceinline__ int node_tiles(int n) { return ((n + REG_TX - 1) / REG_TX) * ((n + REG_TY - 1) / REG_TY); }
-__device__ __forceinline__ int grad_tiles(int n)
+__device__ __forceinline__ int grad_tiles(const LevelDesc &L)
 {
-    const int h = strip_rows(n);
-    return ((n + REG_GW - 1) / REG_GW) * ((n + h - 1) / h);
+    return ((L.n + REG_GW - 1) / REG_GW) * ((L.n + L.hg - 1) / L.hg);
 }
-__device__ __forceinline__ int trial_tiles(int n)
+__device__ __forceinline__ int trial_tiles(const LevelDesc &L)
 {
-    const int h = strip_rows(n);
-    return ((n - 1 + REG_CW - 1) / REG_CW) * ((n - 1 + h - 1) / h);
+    return ((L.n - 1 + REG_CW - 1) / REG_CW) * ((L.n - 1 + L.ht - 1) / L.ht);
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
@@ -412,12 +410,12 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev b)
         if (o < n_ops) {
             const OpState &s = b.st[o];
             const OpDesc &op = b.ops[o];
-            int n = op.lv[s.lvl].n;
+            const LevelDesc &L = op.lv[s.lvl];
             if (s.phase != PH_DONE) active++;
-            if (s.phase == PH_PROLONG || s.phase == PH_FINAL) { inP = 1; tP = node_tiles(n); }
-            if (s.phase == PH_GRAD) { inG = 1; tG = grad_tiles(n); }
+            if (s.phase == PH_PROLONG || s.phase == PH_FINAL) { inP = 1; tP = node_tiles(L.n); }
+            if (s.phase == PH_GRAD) { inG = 1; tG = grad_tiles(L); }
             if (s.phase == PH_START || s.phase == PH_GRAD || s.phase == PH_TRIAL || s.phase == PH_PROLONG) {
-                inT = 1; tT = trial_tiles(n);
+                inT = 1; tT = trial_tiles(L);
             }
         }
         int tot;
@@ -566,7 +564,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
 // shuffles; the scale 1/36 or 1/6 is folded into per-tile coefficients, so that
 // no rounded weight biases every node alike.  M~ R~ comes with the pyramid;
 // 36 M~ That is stored for the trial passes of the search.  Strip tile: 30
-// owned node columns by strip_rows(n) owned rows, one halo node around them.
+// owned node columns by Lv.hg owned rows, one halo node around them.
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(REG_STRIP_THREADS, 8) k_grad(BatchDev b)
@@ -581,7 +579,7 @@ __global__ void __launch_bounds__(REG_STRIP_THREADS, 8) k_grad(BatchDev b)
         const int t = item - b.prefG[e];
         const OpState &s = b.st[o];
         const LevelDesc &Lv = b.ops[o].lv[s.lvl];
-        const int n = Lv.n, pitch = Lv.pitch, ntx = (n + REG_GW - 1) / REG_GW, h = strip_rows(n);
+        const int n = Lv.n, pitch = Lv.pitch, ntx = (n + REG_GW - 1) / REG_GW, h = Lv.hg;
         const int r0 = (t / ntx) * h, c = (t % ntx) * REG_GW - 1 + lane;
         const int rLast = min(r0 + h - 1, n - 1);
         const bool colIn = c >= 0 && c < n;
@@ -777,7 +775,7 @@ __device__ __forceinline__ StripGeom strip_geom(const LevelDesc &Lv, int t, int 
     g.n = Lv.n;
     g.pitch = Lv.pitch;
     const int ntx = (g.n - 1 + REG_CW - 1) / REG_CW;
-    g.h = strip_rows(g.n);
+    g.h = Lv.ht;
     g.r0 = (t / ntx) * g.h;
     g.c = (t % ntx) * REG_CW + lane;
     g.rEnd = min(g.r0 + g.h, g.n - 1);

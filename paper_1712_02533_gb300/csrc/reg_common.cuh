@@ -21,6 +21,9 @@
 // gradient tile, owned cell rows of a trial tile): short strips on the coarse
 // levels, where a tile's row walk is latency bound, long ones on the fine
 // levels, where the halo rows cost bandwidth.
+// Default strip rows of a level of n nodes per side (the tile autotuner may
+// pick others per level): short strips where a tile's row walk is latency
+// bound, long ones where there are enough tiles.
 __host__ __device__ __forceinline__ int strip_rows(int n) { return n <= 65 ? 8 : (n <= 257 ? 16 : 32); }
 #define PT_STRIDE (3 * REG_MAX_TRIALS + 3)  // doubles per trial-tile partial record
 #define PG_STRIDE 2                         // doubles per gradient-tile partial record
@@ -62,6 +65,7 @@ struct __align__(16) NodeRec {
 struct LevelDesc {
     int n;            // nodes per side (2^l + 1)
     int pitch;        // row pitch in elements (float2 for U/D, scalar for images)
+    int hg, ht;       // strip rows of the gradient and trial tiles at this level
     float h2;         // h^2 = 4^-l (as float for scaling, exact)
     double h2d;       // h^2 in double
     const void *R;    // normalised reference frame (mean 0, FE sigma 1) at this level

@@ -104,6 +104,55 @@ def test_network_inputs_are_the_normalised_257_level(reg, orc, syn):
             assert np.abs(x[e, ch] - want[:256, :256]).max() <= 1e-5 * np.abs(want).max()
 
 
+def _oracle_inputs(orc, fr):
+    """Network inputs of the pair (fr[0], fr[1]) of 256^2 frames, from the
+    oracle: each frame's grid function centred and scaled to unit FE norm, its
+    first 256 rows and columns."""
+    x = []
+    for f in fr[:2]:
+        F = orc.embed(f)
+        Fc = F - float(np.sum(orc.lumped(F.shape[0]) * F))
+        x.append((Fc / np.sqrt(float(np.sum(Fc * orc.mass_apply(Fc)))))[:256, :256])
+    return np.stack(x)[None]
+
+
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
+    """The learned start of a preprocessing operator is the network's output
+    upsampled onto the finest grid (oracle: FP64 network, BF16 operands in the
+    32-channel layers on the tensor-core path); the operator then runs function
+    A from it on the finest init_levels levels, which the oracle's A with that
+    many levels and that start reproduces (decision by decision)."""
+    import synth
+    from oracle import cnn as ocnn
+    from paper_1712_02533_gb300 import learned
+    from test_gpu_parity import _assert_op_parity, _gpu_traces_by_op
+    fr = syn.series(31, 2, 256, **learned.TRAIN_SERIES)
+    theta = synth.cnn_params(7)
+    y = ocnn.forward(theta.astype(np.float64), _oracle_inputs(orc, fr),
+                     bf16_layers=(1, 2, 3, 4) if tensor_cores else ())
+    u0 = ocnn.upsample(y[0], 256)
+    p = reg.default_params(n_levels=3, init_levels=2, iter_max=50, lam=10.0)
+    with reg.Cnn(theta, side=256, max_batch=4) as net, reg.Series(fr, p) as s:
+        s.cnn_init(net, tensor_cores=tensor_cores)
+        init, se = s.get_slot(0)
+        assert tuple(se) == (0, 1)
+        s.set_trace(1 << 20)
+        s.prefix_scan(reg.SERIAL)
+        gtr = _gpu_traces_by_op(s.get_trace(), 1)[0]
+        d, se = s.get_slot(0)  # phi_{0,1} on the vertex grid
+        assert tuple(se) == (0, 1)
+    tol = 2e-3 if tensor_cores else 2e-5
+    assert np.abs(init - u0).max() <= tol * np.abs(u0).max()
+    if tensor_cores:
+        return  # the start differs by the BF16 rounding flips; the FP32 case pins the operator
+    g0, g1 = orc.embed(fr[0]), orc.embed(fr[1])
+    with orc.trace() as t:
+        u, _, stl = orc.register(g0, g1, orc.params(n_levels=2, iter_max=50, lam=10.0), u_init=u0 / 256)
+    assert len(stl) == 2
+    _assert_op_parity(d, u * 256, gtr, t.rows, "A(0,1) from the learned start", g0, g1)
+
+
 def test_trained_network_gains_over_the_identity_start(reg, syn):
     """Trained on 512 pairs of large-motion series (plain-method targets), the
     network's initial displacements bring the registered series of a held-out
