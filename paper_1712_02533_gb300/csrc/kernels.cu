@@ -961,14 +961,24 @@ __device__ __forceinline__ void start_tile(const OpState &s, const LevelDesc &Lv
     v[3] = quu * (1.0 / 3.0);
 }
 
-// Shared memory of one warp in the trial pass: the exact changes of the
-// nodes of the previous and the current row that left their cell, and the
-// per-lane sums over those nodes and their cells, for every step size.
+// Shared memory of one warp in the trial pass.  The row walk sums the nodes
+// and cells that the polynomial moments cover and queues the rest: nodes whose
+// largest move leaves their cell (or whose base point lies outside the grid),
+// and cells with such a corner.  A window of up to TW rows is then finished
+// cooperatively, one queued node or cell per lane, so that the exact path
+// runs on full warps instead of on the few lanes of a row that need it.
+constexpr int TW = 8;    // rows per window
+constexpr int TQ = 64;   // queued nodes (a row adds at most 32)
+constexpr int TC = 128;  // queued cells (a row adds at most 31)
 template <int JM>
 struct TrialScratch {
-    float dl[2][JM][32];  // delta_j of such nodes, rows alternating
-    float sn[3][JM][32];  // node sums: omega delta, 36 M~That delta, M~R~ delta
-    float sq[JM][32];     // cell sums of 18 delta^T M~_e delta
+    float A[TW + 1][32], B[TW + 1][32];  // A, B of the window's rows; slot 0: the row before the window
+    unsigned char qi[TW + 1][32];        // 1 + queue index of a node on the exact path, else 0
+    unsigned short qn[TQ];               // queued nodes: slot << 5 | lane
+    unsigned short qc[TC];               // queued cells: slot << 5 | lane (between slots slot-1 and slot)
+    float dl[JM][TQ];                    // delta_j of the queued nodes
+    float sn[3][JM][32];                 // per-lane node sums: omega delta, 36 M~That delta, M~R~ delta
+    float sq[JM][32];                    // per-lane cell sums of 18 delta^T M~_e delta
 };
 
 // Exact change of the interpolant at one node for every step size, for a
@@ -976,12 +986,12 @@ struct TrialScratch {
 // the grid): the moves that stay in the cell take the polynomial of the base
 // cell, the others the texel patch, or a fresh sample for moves of a cell or
 // more (whose rounding, ~1e-7 of That, is small against such a change).  The
-// changes go to the warp's scratch row and, for an owned node, into its node
-// sums.
+// changes go to queue entry q and, for an owned node, into the node sums of
+// the lane that computes them.
 template <bool BF16, int JM>
 __device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const float *tau, int J, int c, int r,
                                                   float4 u, float4 dm, float w, bool own, TrialScratch<JM> &sh,
-                                                  int cur, int lane)
+                                                  int q, int lane)
 {
     const int n = Lv.n, pitch = Lv.pitch;
     Patch P;
@@ -1000,12 +1010,12 @@ __device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const flo
             if (!cl && ax1 >= 0.f && ax1 < 1.f && ay1 >= 0.f && ay1 < 1.f) {
                 del = tau[j] * (A + tau[j] * B);
             } else if (!patch_delta(P, n, ex, ey, del)) {
-                Texel4 q;
-                locate(n, c, r, (u.x + u.z) + ex, (u.y + u.w) + ey, q.jx, q.jy, q.ax, q.ay, q.clx, q.cly);
-                fetch<BF16>(q, Lv.T, pitch);
-                del = bil(q) - P.t0;
+                Texel4 t;
+                locate(n, c, r, (u.x + u.z) + ex, (u.y + u.w) + ey, t.jx, t.jy, t.ax, t.ay, t.clx, t.cly);
+                fetch<BF16>(t, Lv.T, pitch);
+                del = bil(t) - P.t0;
             }
-            sh.dl[cur][j][lane] = del;
+            sh.dl[j][q] = del;
             if (own) {
                 sh.sn[0][j][lane] += w * del;
                 sh.sn[1][j][lane] += dm.z * del;
@@ -1013,6 +1023,71 @@ __device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const flo
             }
         }
     }
+}
+
+// Finish a window whose rows rlast-nrow+1 .. rlast sit in slots 1..nrow: the
+// queued nodes from entry q0 on (one per lane), then the queued cells, whose
+// corners take either a queued node's exact change or the polynomial of their
+// A and B.  The last row moves to slot 0 with the changes of its queued nodes,
+// for the cells between it and the next window.
+template <bool BF16, int JM>
+__device__ __forceinline__ void trial_flush(const LevelDesc &Lv, const StripGeom &g, const float4 *V,
+                                            const float *tau, int J, TrialScratch<JM> &sh, int lane, int rlast,
+                                            int nrow, int &q0, int &qn, int &qc)
+{
+    const unsigned FULL = 0xffffffffu;
+    __syncwarp();
+    for (int q = q0 + lane; q < qn; q += 32) {
+        const int e = sh.qn[q], slot = e >> 5, ln = e & 31;
+        const int r = rlast - nrow + slot, c = g.c - lane + ln;
+        const int64_t idx = (int64_t)r * g.pitch + c;
+        const float4 u = V[2 * idx], dm = V[2 * idx + 1];
+        const bool own = (ln < REG_CW || c == g.n - 1) && (r < g.r0 + g.h || r == g.n - 1);
+        const float w = ((c == 0 || c == g.n - 1) ? 0.5f : 1.f) * ((r == 0 || r == g.n - 1) ? 0.5f : 1.f);
+        node_deltas_exact<BF16, JM>(Lv, tau, J, c, r, u, dm, w, own, sh, q, lane);
+    }
+    __syncwarp();
+    for (int q = lane; q < qc; q += 32) {
+        const int e = sh.qc[q], slot = e >> 5, ln = e & 31;
+        const int itl = sh.qi[slot - 1][ln], itr = sh.qi[slot - 1][ln + 1];
+        const int ibl = sh.qi[slot][ln], ibr = sh.qi[slot][ln + 1];
+        const float Atl = sh.A[slot - 1][ln], Btl = sh.B[slot - 1][ln];
+        const float Atr = sh.A[slot - 1][ln + 1], Btr = sh.B[slot - 1][ln + 1];
+        const float Abl = sh.A[slot][ln], Bbl = sh.B[slot][ln];
+        const float Abr = sh.A[slot][ln + 1], Bbr = sh.B[slot][ln + 1];
+#pragma unroll
+        for (int j = 0; j < JM; j++) {
+            if (j < J) {
+                const float t = tau[j];
+                const float tl = itl ? sh.dl[j][itl - 1] : t * (Atl + t * Btl);
+                const float tr = itr ? sh.dl[j][itr - 1] : t * (Atr + t * Btr);
+                const float bl = ibl ? sh.dl[j][ibl - 1] : t * (Abl + t * Bbl);
+                const float br = ibr ? sh.dl[j][ibr - 1] : t * (Abr + t * Bbr);
+                sh.sq[j][lane] += 2.f * (pform(tl, tr) + pform(bl, br)) + tl * (2.f * bl + br) + tr * (bl + 2.f * br);
+            }
+        }
+    }
+    __syncwarp();
+    // the last row becomes slot 0
+    const int iq = sh.qi[nrow][lane];
+    const unsigned m = __ballot_sync(FULL, iq != 0);
+    const int np = __popc(m & ((1u << lane) - 1u));
+    float keep[JM];
+#pragma unroll
+    for (int j = 0; j < JM; j++) keep[j] = (iq && j < J) ? sh.dl[j][iq - 1] : 0.f;
+    const float a = sh.A[nrow][lane], b = sh.B[nrow][lane];
+    __syncwarp();
+    sh.A[0][lane] = a;
+    sh.B[0][lane] = b;
+    sh.qi[0][lane] = iq ? (unsigned char)(np + 1) : 0;
+    if (iq) {
+#pragma unroll
+        for (int j = 0; j < JM; j++)
+            if (j < J) sh.dl[j][np] = keep[j];
+    }
+    qn = q0 = __popc(m);
+    qc = 0;
+    __syncwarp();
 }
 
 // Trial sums of one strip tile for the step sizes tau_0..tau_{J-1}.  All step
@@ -1024,13 +1099,14 @@ __device__ __forceinline__ void node_deltas_exact(const LevelDesc &Lv, const flo
 // moments (sum omega A, sum omega B, ...; 18 A^T M~ A, 18 A^T M~ B, 18 B^T M~ B
 // per cell) that are gathered once for all step sizes.  A node whose largest
 // move leaves the cell, and every cell touching one, is summed exactly for each
-// step size (shared memory).  The node record of the next row is loaded while
-// the current row is worked on.
+// step size, in windows of rows finished by the whole warp (trial_flush).  The
+// node record of the next row is loaded while the current row is worked on.
 template <bool BF16, int JM>
 __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv, const StripGeom &g, float *v,
                                            TrialScratch<JM> &sh, int lane, unsigned &nexact)
 {
     const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
     const int J = min(s.ntr, JM);
     const bool withQ = (s.phase == PH_GRAD);
     const float4 *V = reinterpret_cast<const float4 *>(Lv.V[s.cur]);
@@ -1051,7 +1127,7 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
     float Ap = 0.f, ApR = 0.f, Bp = 0.f, BpR = 0.f, PaaP = 0.f, PabP = 0.f, PbbP = 0.f;
     bool slowP = false, slowPR = false;
     float qdd = 0.f, pdx = 0.f, pdy = 0.f, dPx = 0.f, dPy = 0.f;
-    int cur = 0;
+    int q0 = 0, qn = 0, qc = 0, nrow = 0;  // queue state (warp-uniform)
     float4 nu = make_float4(0.f, 0.f, 0.f, 0.f), ndm = nu;  // record of the next row
     if (g.colIn) {
         const int64_t idx = (int64_t)g.r0 * g.pitch + g.c;
@@ -1095,14 +1171,22 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
                 }
             }
         }
-        nexact += __popc(__ballot_sync(FULL, slow));
-        if (slow) node_deltas_exact<BF16, JM>(Lv, tau, J, g.c, r, u, dm, w, own, sh, cur, lane);
-        __syncwarp();
+        // this row's slot in the window; queue its nodes on the exact path
+        const int slot = nrow + 1;
+        const unsigned ms = __ballot_sync(FULL, slow);
+        nexact += __popc(ms);
+        const int pos = qn + __popc(ms & lt);
+        sh.A[slot][lane] = A;
+        sh.B[slot][lane] = B;
+        sh.qi[slot][lane] = slow ? (unsigned char)(pos + 1) : 0;
+        if (slow) sh.qn[pos] = (unsigned short)((slot << 5) | lane);
+        qn += __popc(ms);
         // cells between rows r-1 and r, columns c and c+1
         const float AR = __shfl_down_sync(FULL, A, 1), BR = __shfl_down_sync(FULL, B, 1);
         const bool slowR = __shfl_down_sync(FULL, slow, 1);
         const float Paa = pform(A, AR), Pbb = pform(B, BR);
         const float Pab = A * B + AR * BR + 0.5f * (A * BR + AR * B);
+        bool mixed = false;
         if (g.cellCol && r > g.r0) {
             if (!(slowP || slowPR || slow || slowR)) {
                 const float ha = 2.f * A + AR, haR = A + 2.f * AR, hb = 2.f * B + BR, hbR = B + 2.f * BR;
@@ -1110,24 +1194,15 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
                 qbb += 2.f * (PbbP + Pbb) + Bp * hb + BpR * hbR;
                 qab += 2.f * (PabP + Pab) + 0.5f * (Ap * hb + ApR * hbR + Bp * ha + BpR * haR);
             } else {
-#pragma unroll
-                for (int j = 0; j < JM; j++) {
-                    if (j < J) {
-                        const float t = tau[j];
-                        const float tl = slowP ? sh.dl[cur ^ 1][j][lane] : t * (Ap + t * Bp);
-                        const float tr = slowPR ? sh.dl[cur ^ 1][j][lane + 1] : t * (ApR + t * BpR);
-                        const float bl = slow ? sh.dl[cur][j][lane] : t * (A + t * B);
-                        const float br = slowR ? sh.dl[cur][j][lane + 1] : t * (AR + t * BR);
-                        sh.sq[j][lane] += 2.f * (pform(tl, tr) + pform(bl, br)) + tl * (2.f * bl + br) +
-                                          tr * (bl + 2.f * br);
-                    }
-                }
+                mixed = true;
             }
         }
+        const unsigned mc = __ballot_sync(FULL, mixed);
+        if (mixed) sh.qc[qc + __popc(mc & lt)] = (unsigned short)((slot << 5) | lane);
+        qc += __popc(mc);
         Ap = A; ApR = AR; Bp = B; BpR = BR;
         PaaP = Paa; PabP = Pab; PbbP = Pbb;
         slowP = slow; slowPR = slowR;
-        cur ^= 1;
         if (withQ) {
             const float dRx = __shfl_down_sync(FULL, dm.x, 1), dRy = __shfl_down_sync(FULL, dm.y, 1);
             const float qx = dRx - dm.x, qy = dRy - dm.y;
@@ -1135,6 +1210,22 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
             const float sx = __shfl_down_sync(FULL, rx, 1), sy = __shfl_down_sync(FULL, ry, 1);
             if (g.cellCol && r > g.r0) qdd += pform(pdx, qx) + pform(rx, sx) + pform(pdy, qy) + pform(ry, sy);
             pdx = qx; pdy = qy; dPx = dm.x; dPy = dm.y;
+        }
+        nrow++;
+        if (nrow == TW || qn > TQ - 32 || qc > TC - 32 || r == g.rEnd) {
+            if (qn > q0 || qc > 0) trial_flush<BF16, JM>(Lv, g, V, tau, J, sh, lane, r, nrow, q0, qn, qc);
+            else {
+                // nothing new queued (so the last row has no exact nodes): only
+                // its A, B move to slot 0
+                const float a = sh.A[nrow][lane], b = sh.B[nrow][lane];
+                __syncwarp();
+                sh.A[0][lane] = a;
+                sh.B[0][lane] = b;
+                sh.qi[0][lane] = 0;
+                q0 = qn = 0;
+                __syncwarp();
+            }
+            nrow = 0;
         }
     }
     __syncwarp();

@@ -159,7 +159,19 @@ def main(argv=None):
     ap.add_argument("--init-levels", default="5,4,3,1")
     ap.add_argument("--weights-out", default=None, help="save the trained parameters (.npy)")
     ap.add_argument("--weights-in", default=None, help="skip training, load parameters (.npy)")
+    ap.add_argument("--forward-rate", type=int, default=0, metavar="BATCH",
+                    help="only time the forward pass (FP32 and tensor cores) on BATCH random pairs")
     a = ap.parse_args(argv)
+    if a.forward_rate:
+        with Cnn(synth.cnn_params(1), side=256, max_batch=a.forward_rate) as net:
+            res = {}
+            for tc in (False, True):
+                ms, tf = forward_rate(net, batch=a.forward_rate, tensor_cores=tc)
+                res["tensor_cores" if tc else "fp32"] = dict(ms_per_forward=ms, tflops_network=tf,
+                                                             pairs_per_s=a.forward_rate / ms * 1e3)
+        print(json.dumps(dict(batch=a.forward_rate, flop_per_pair=FLOP_PER_PAIR,
+                              tc_flop_per_pair=TC_FLOP_PER_PAIR, **res)))
+        return
     gen = {k: v for k, v in synth.CONFIGS["c3_400x1024"].items() if k not in ("seed", "n_frames", "side", "n_levels")}
     out = dict(workload=f"{a.frames}x{a.side}^2", generator=gen)
     net = Cnn(synth.cnn_params(1), side=256, max_batch=64)
