@@ -250,6 +250,7 @@ struct reg_cnn {
     float *g0 = nullptr, *g1 = nullptr;  // gradient ping-pong (largest activation)
     float *gy = nullptr;
     double *partial = nullptr, *loss = nullptr;
+    uint32_t *wpack = nullptr;  // the 32 -> 32 layers' weights in the tensor-core layout
     int64_t step = 0;
 };
 
@@ -293,7 +294,7 @@ reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t
         float *out = (k == NL - 1 && y) ? y : h->act[k];
         if (tc && k >= 1 && k <= 4) {
             // 32 -> 32 layers on the tensor cores
-            reg_status rs = cnn_conv32_tc(a, H, th, out, B, LAYERS[k].S, st);
+            reg_status rs = cnn_conv32_tc(a, H, th, out, B, LAYERS[k].S, st, h->wpack + (k - 1) * cnn_conv32_tc_words());
             if (rs != REG_OK) return rs;
         } else {
             switch (k) {
@@ -337,7 +338,8 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
     ok = ok && alloc((void **)&h->g0, sizeof(float) * big * max_batch) &&
          alloc((void **)&h->g1, sizeof(float) * big * max_batch) &&
          alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
-         alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double));
+         alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double)) &&
+         alloc((void **)&h->wpack, sizeof(uint32_t) * 4 * cnn_conv32_tc_words());
     if (!ok) {
         reg_cnn_destroy(h);
         return cnn_fail(REG_ENOMEM, "device allocation failed");
@@ -445,6 +447,7 @@ reg_status reg_cnn_destroy(reg_cnn_t h)
     cudaFree(h->g0);
     cudaFree(h->g1);
     cudaFree(h->gy);
+    cudaFree(h->wpack);
     cudaFree(h->partial);
     cudaFree(h->loss);
     delete h;

@@ -14,7 +14,11 @@ int64_t cnn_output_side(const reg_cnn *h);
 int cnn_input_side(const reg_cnn *h);
 int cnn_max_batch(const reg_cnn *h);
 // 32 -> 32 channel 3x3 convolution with ReLU on the tensor cores (BF16 operands,
-// FP32 accumulation): in (B x 32 x H x H), out (B x 32 x Ho x Ho), stride S.
-reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st);
+// FP32 accumulation): in (B x 32 x H x H), out (B x 32 x Ho x Ho), stride S;
+// theta: the layer's W then b; wpack: device scratch of cnn_conv32_tc_words()
+// words for the packed weights.
+reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
+                         uint32_t *wpack);
+int cnn_conv32_tc_words();
 // Record an error message for reg_last_error().
 reg_status reg_internal_fail(reg_status st, const char *msg);

@@ -1,11 +1,21 @@
 // Tensor-core forward of the learned initialiser's 32 -> 32 channel layers:
 // a 3x3 convolution (zero padding 1, stride 1 or 2) with bias and ReLU as an
-// implicit GEMM, D[pixel][o] = sum_k A[pixel][k] W[o][k] with
-// k = (c, dy, dx) = 9 c + 3 dy + dx (K = 288 = 18 steps of 16).  Operands are
-// BF16 (activations rounded when loaded, weights rounded into shared memory),
-// accumulation FP32 (mma.sync m16n8k16).  One warp computes 16 output pixels
-// (consecutive in the flattened batch x row x column order) for all 32 output
-// channels (four n-tiles of 8).
+// implicit GEMM, D[pixel][o] = sum_k A[pixel][k] W[o][k], with the reduction
+// index ordered k = (3 dy + dx) * 32 + c (K = 288 = 18 steps of 16).
+// Operands are BF16, accumulation FP32 (mma.sync m16n8k16).
+//
+// A block computes an output tile of 8 rows x 16 columns of one image for all
+// 32 output channels; each of its 4 warps takes two rows (two m-tiles of 16
+// pixels) and all four n-tiles of 8 channels.  The block first stages, in
+// shared memory as BF16 pairs of channels (channels innermost):
+//   - the input tile with its halo, (S*7 + 3) x (S*15 + 3) pixels, read from
+//     the FP32 NCHW activations (zero outside the image);
+//   - the layer's weights, W[3 dy + dx][o][c].
+// Every fragment register is then one 32-bit shared load.  Pixel and weight
+// rows are padded (20 or 18 words) so that the eight rows a fragment load
+// touches fall into distinct banks.  The weights are packed into that layout
+// once per layer and call (k_pack_w32), and each block copies them with
+// 16-byte loads.
 #include <cuda_bf16.h>
 
 #include "cnn_internal.h"
@@ -13,10 +23,17 @@
 namespace {
 
 constexpr int TC_C = 32, TC_O = 32, TC_K = TC_C * 9;
-// Shared-memory row of one output channel's weights, in BF16 pairs: 144 pairs
-// padded to 148 so that the eight rows a fragment load touches (o = 8j + g)
-// fall into distinct banks.
-constexpr int TC_WROW = TC_K / 2 + 4;
+constexpr int TC_TH = 8, TC_TW = 16;  // output tile (rows, columns)
+constexpr int TC_WS = 20;             // words per (tap, output channel) weight row: 16 channel pairs + pad
+
+__host__ __device__ constexpr int in_rows(int S) { return S * (TC_TH - 1) + 3; }
+__host__ __device__ constexpr int in_cols(int S) { return S * (TC_TW - 1) + 3; }
+// words per staged input pixel: 16 channel pairs + pad (bank spread for the stride)
+__host__ __device__ constexpr int pix_words(int S) { return S == 1 ? 20 : 18; }
+// the staged input tile, rounded up to 16 bytes so that the weights after it
+// can be written with 16-byte stores
+__host__ __device__ constexpr int xs_words(int S) { return (in_rows(S) * in_cols(S) * pix_words(S) + 3) / 4 * 4; }
+__host__ __device__ constexpr int smem_words(int S) { return xs_words(S) + 9 * TC_O * TC_WS + TC_O; }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -34,83 +51,132 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Input value at reduction index k for output pixel (b, y, x) (zero outside).
-__device__ __forceinline__ float a_elem(const float *in, int H, int S, int b, int y, int x, int k, bool valid)
+// W[o][c][dy][dx] (FP32) -> [3 dy + dx][o][c pair] (BF16 pairs, rows of TC_WS
+// words, the padding zero).
+__global__ void k_pack_w32(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
 {
-    const int c = k / 9, r = k - 9 * c, dy = r / 3, dx = r - 3 * dy;
-    const int iy = S * y + dy - 1, ix = S * x + dx - 1;
-    if (!valid || iy < 0 || iy >= H || ix < 0 || ix >= H) return 0.f;
-    return in[(((int64_t)b * TC_C + c) * H + iy) * H + ix];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * TC_O * TC_WS) return;
+    const int cp = i % TC_WS, r2 = i / TC_WS, o = r2 % TC_O, tap = r2 / TC_O;
+    uint32_t v = 0;
+    if (cp < TC_C / 2) {
+        const float *w = theta + (int64_t)o * TC_K + (2 * cp) * 9 + tap;
+        v = pack_bf16(w[0], w[9]);
+    }
+    wpack[i] = v;
 }
 
+template <int S>
 __global__ void __launch_bounds__(128) k_conv32_tc(const float *__restrict__ in, int H,
-                                                   const float *__restrict__ theta, float *__restrict__ out, int Ho,
-                                                   int S, int B)
+                                                   const float *__restrict__ theta, const uint32_t *__restrict__ wpack,
+                                                   float *__restrict__ out, int Ho, int tiles_x, int tiles_y)
 {
-    __shared__ uint32_t wsm[TC_O * TC_WROW];  // W[o][k] as BF16 pairs (k, k+1)
-    __shared__ float bias[TC_O];
-    for (int i = threadIdx.x; i < TC_O * TC_K / 2; i += blockDim.x) {
-        const int o = i / (TC_K / 2), q = i - o * (TC_K / 2);
-        wsm[o * TC_WROW + q] = pack_bf16(theta[2 * i], theta[2 * i + 1]);
+    constexpr int IR = in_rows(S), IC = in_cols(S), PW = pix_words(S);
+    extern __shared__ uint32_t smem[];
+    uint32_t *xs = smem;               // [IR][IC][PW]
+    uint32_t *ws = xs + xs_words(S);   // [9][32][TC_WS], 16-byte aligned
+    float *bias = reinterpret_cast<float *>(ws + 9 * TC_O * TC_WS);
+    const int tid = threadIdx.x;
+    const int tx = blockIdx.x % tiles_x, rest = blockIdx.x / tiles_x;
+    const int ty = rest % tiles_y, b = rest / tiles_y;
+    const int oy0 = ty * TC_TH, ox0 = tx * TC_TW;
+    const int iy0 = S * oy0 - 1, ix0 = S * ox0 - 1;
+    // the packed weights and the biases
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws);
+        for (int i = tid; i < 9 * TC_O * TC_WS / 4; i += blockDim.x) dst[i] = src[i];
     }
-    for (int i = threadIdx.x; i < TC_O; i += blockDim.x) bias[i] = theta[TC_O * TC_K + i];
+    if (tid < TC_O) bias[tid] = theta[TC_O * TC_K + tid];
+    // stage the input tile: one channel pair of one pixel per item (columns fastest)
+    const float *img = in + (int64_t)b * TC_C * H * H;
+#pragma unroll 4
+    for (int i = tid; i < (TC_C / 2) * IR * IC; i += blockDim.x) {
+        const int ix = i % IC, r2 = i / IC, iy = r2 % IR, cp = r2 / IR;
+        const int gy = iy0 + iy, gx = ix0 + ix;
+        float v0 = 0.f, v1 = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < H) {
+            const int64_t o = ((int64_t)(2 * cp) * H + gy) * H + gx;
+            v0 = img[o];
+            v1 = img[o + (int64_t)H * H];
+        }
+        xs[(iy * IC + ix) * PW + cp] = pack_bf16(v0, v1);
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int total = B * Ho * Ho;
-    const int p0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16;
-    if (p0 >= total) return;  // warp-uniform
-    // the two pixels of this lane's A rows: g and g + 8
-    int pb[2], py[2], px[2];
-    bool pv[2];
+
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int p = p0 + g + 8 * h;
-        pv[h] = p < total;
-        const int q = pv[h] ? p : 0;
-        px[h] = q % Ho;
-        py[h] = (q / Ho) % Ho;
-        pb[h] = q / (Ho * Ho);
-    }
-    float acc[4][4];
+    for (int m = 0; m < 2; m++)
 #pragma unroll
-    for (int j = 0; j < 4; j++)
+        for (int j = 0; j < 4; j++)
 #pragma unroll
-        for (int i = 0; i < 4; i++) acc[j][i] = 0.f;
-    for (int k0 = 0; k0 < TC_K; k0 += 16) {
-        uint32_t a[4];
-        const int ka = k0 + 2 * t, kb = ka + 8;
-        a[0] = pack_bf16(a_elem(in, H, S, pb[0], py[0], px[0], ka, pv[0]),
-                         a_elem(in, H, S, pb[0], py[0], px[0], ka + 1, pv[0]));
-        a[1] = pack_bf16(a_elem(in, H, S, pb[1], py[1], px[1], ka, pv[1]),
-                         a_elem(in, H, S, pb[1], py[1], px[1], ka + 1, pv[1]));
-        a[2] = pack_bf16(a_elem(in, H, S, pb[0], py[0], px[0], kb, pv[0]),
-                         a_elem(in, H, S, pb[0], py[0], px[0], kb + 1, pv[0]));
-        a[3] = pack_bf16(a_elem(in, H, S, pb[1], py[1], px[1], kb, pv[1]),
-                         a_elem(in, H, S, pb[1], py[1], px[1], kb + 1, pv[1]));
+            for (int i = 0; i < 4; i++) acc[m][j][i] = 0.f;
+#pragma unroll 2
+    for (int ks = 0; ks < 18; ks++) {
+        const int tap = ks >> 1, ch = (ks & 1) * 8;  // channel-pair offset of this k-step
+        const int dy = tap / 3, dx = tap - 3 * dy;
+        uint32_t bf[4][2];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int o = 8 * j + g;
-            mma_bf16(acc[j], a, wsm[o * TC_WROW + (ka >> 1)], wsm[o * TC_WROW + (kb >> 1)]);
+            const uint32_t *wr = ws + (tap * TC_O + 8 * j + g) * TC_WS + ch + t;
+            bf[j][0] = wr[0];
+            bf[j][1] = wr[4];
+        }
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            const int oy = 2 * warp + m;  // output row within the tile
+            const uint32_t *p0 = xs + ((S * oy + dy) * IC + S * g + dx) * PW + ch + t;  // pixel g
+            const uint32_t *p1 = p0 + S * 8 * PW;                                      // pixel g + 8
+            uint32_t a[4];
+            a[0] = p0[0];
+            a[1] = p1[0];
+            a[2] = p0[4];
+            a[3] = p1[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) mma_bf16(acc[m][j], a, bf[j][0], bf[j][1]);
         }
     }
     // D fragment: (row g, cols 2t, 2t+1) and (row g+8, same cols) of each n-tile
 #pragma unroll
-    for (int j = 0; j < 4; j++)
+    for (int m = 0; m < 2; m++) {
+        const int oy = oy0 + 2 * warp + m;
+        if (oy >= Ho) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int h = i >> 1, o = 8 * j + 2 * t + (i & 1);
-            if (!pv[h]) continue;
-            out[(((int64_t)pb[h] * TC_O + o) * Ho + py[h]) * Ho + px[h]] = fmaxf(acc[j][i] + bias[o], 0.f);
-        }
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int ox = ox0 + g + 8 * (i >> 1), o = 8 * j + 2 * t + (i & 1);
+                if (ox < Ho)
+                    out[(((int64_t)b * TC_O + o) * Ho + oy) * Ho + ox] = fmaxf(acc[m][j][i] + bias[o], 0.f);
+            }
+    }
+}
+
+template <int S>
+reg_status launch(const float *in, int H, const float *theta, float *out, int B, cudaStream_t st,
+                  uint32_t *wpack)
+{
+    const int nw = 9 * TC_O * TC_WS;
+    k_pack_w32<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
+    const size_t bytes = sizeof(uint32_t) * smem_words(S);
+    if (cudaFuncSetAttribute(k_conv32_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return reg_internal_fail(REG_ECUDA, "tensor-core convolution: shared memory attribute");
+    const int Ho = (H + 2 - 3) / S + 1;
+    const int tx = (Ho + TC_TW - 1) / TC_TW, ty = (Ho + TC_TH - 1) / TC_TH;
+    k_conv32_tc<S><<<B * tx * ty, 128, bytes, st>>>(in, H, theta, wpack, out, Ho, tx, ty);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core convolution launch");
+    return REG_OK;
 }
 
 }  // namespace
 
-reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st)
+int cnn_conv32_tc_words() { return 9 * TC_O * TC_WS; }
+
+reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
+                         uint32_t *wpack)
 {
-    const int Ho = (H + 2 - 3) / S + 1;
-    const int tiles = (B * Ho * Ho + 15) / 16;
-    k_conv32_tc<<<(tiles + 3) / 4, 128, 0, st>>>(in, H, theta, out, Ho, S, B);
-    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core convolution launch");
-    return REG_OK;
+    if (S == 1) return launch<1>(in, H, theta, out, B, st, wpack);
+    if (S == 2) return launch<2>(in, H, theta, out, B, st, wpack);
+    return reg_internal_fail(REG_EINVAL, "tensor-core convolution: stride must be 1 or 2");
 }
