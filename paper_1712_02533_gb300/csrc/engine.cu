@@ -272,7 +272,9 @@ void fill_level(const reg_series *s, LevelDesc &L, int n, int pitch)
     L.h2 = (float)L.h2d;
 }
 
-reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t items_per_op)
+// Batch buffers for n_ops operators with ws_total bytes of workspace and up to
+// items_total work items in one step.
+reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_total, int64_t items_total)
 {
     bool changed = false;
     if (n_ops > s->cap_ops) {
@@ -288,7 +290,7 @@ reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t i
         s->cap_ops = c;
         changed = true;
     }
-    int64_t items = (int64_t)n_ops * items_per_op;
+    const int64_t items = items_total;
     if (items > s->cap_items) {
         int64_t c = std::max(items, (int64_t)(1.25 * s->cap_items));
         untrack(s, s->d_partG);
@@ -298,7 +300,7 @@ reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_per_op, int64_t i
         s->cap_items = c;
         changed = true;
     }
-    size_t ws = (size_t)n_ops * ws_per_op;
+    const size_t ws = ws_total;
     if (ws > s->cap_ws) {
         untrack(s, s->d_ws);
         RET(track(s, (void **)&s->d_ws, ws));
@@ -371,13 +373,19 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
 {
     int n = (int)ops.size();
     if (n == 0) return pre_iter();
+    // each op's workspace at its own offset (series of different sides share a
+    // batch without every op taking the largest one's room); the step's work
+    // items are at most the sum of the ops' largest tile counts
+    std::vector<size_t> ws_off(n);
     size_t ws = 0;
     int64_t items = 0;
     int nl = 0, nLmax = 0;
-    for (auto &o : ops) {
+    for (int i = 0; i < n; i++) {
+        const OpReq &o = ops[i];
         const SeriesInfo &si = s->S[o.series];
-        ws = std::max(ws, si.ws_bytes);
-        items = std::max<int64_t>(items, max_tiles_series(s, si, o.skip));
+        ws_off[i] = ws;
+        ws += (si.ws_bytes + 255) / 256 * 256;
+        items += max_tiles_series(s, si, o.skip);
         nl = std::max(nl, si.nl);
         nLmax = std::max(nLmax, si.n[si.nl - 1]);
     }
@@ -393,7 +401,7 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
         d.right = o.right >= 0 ? si.slots + (size_t)o.right * si.slot_elems : nullptr;
         d.out = si.slots + (size_t)o.dst * si.slot_elems;
         d.slot_pitch = si.pitch[si.nl - 1];
-        char *w = s->d_ws + (size_t)i * ws;
+        char *w = s->d_ws + ws_off[i];
         for (int j = 0; j < d.nl; j++) {
             const int k = o.skip + j;  // level index within the series' pyramid
             LevelDesc &L = d.lv[j];
