@@ -7,9 +7,9 @@
  * paper's definitions; it shares no code with the CUDA path.  Only the tests,
  * the package's smoke check and the benchmark's CPU-baseline leg may call it.
  *
- * Conventions (readings of the paper, each also listed in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *  - Level l is the vertex grid of (2^l+1)^2 nodes on Omega = [0,1]^2 (Section
- *    "Multilevel": "we focus on the latter"); node (r, c) sits at
+ *    "Multilevel" picks the grid with a node on both borders); node (r, c) sits at
  *    x = (c h, r h), h = 2^-l; arrays are row-major, index r*n + c.
  *  - A deformation is stored as its displacement u = phi - id in Omega units,
  *    two planes: u[0..n^2) is the x_0 (column) part, u[n^2..2n^2) the x_1 (row)
