@@ -81,7 +81,10 @@ typedef struct reg_allocator {
  * runs when it starts from a learned initial displacement
  * (reg_cnn_init_series); 0 means n_levels.  The coarse levels exist to bring
  * a far start into the basin of the fine ones; a start that is already there
- * can skip them. */
+ * can skip them.  learned_fallback_px: the plain method judges a learned
+ * start that skips levels by how far it moves it (mean |u_final - u_start|
+ * over the finest nodes, x + y, px); an operator that moves it further is run
+ * again from the identity on every level (reg_prefix_scan reports the count). */
 typedef struct reg_params {
     int32_t n_levels;
     int32_t iter_max;
@@ -96,6 +99,7 @@ typedef struct reg_params {
     int32_t max_steps;        /* device step budget per batch; <= 0: automatic */
     int32_t flags;            /* REG_FLAG_* */
     int32_t init_levels;      /* 0 or 1..n_levels, see above */
+    double learned_fallback_px; /* see above; 0: never fall back */
     reg_allocator allocator;
 } reg_params;
 
@@ -103,7 +107,7 @@ typedef struct reg_params {
 
 /* Fills *p with the defaults: n_levels 3, iter_max 50, epsilon 1e-7,
  * lambda 10, sigma 0.5, tau_init 1, tau_max 1e4, tau_min 1e-12, F32 storage,
- * 4 trials per pass, init_levels 0. */
+ * 4 trials per pass, init_levels 0, learned_fallback_px 2. */
 void reg_default_params(reg_params *p);
 
 /* One operator application (Section "Registration for series of images").
@@ -273,7 +277,7 @@ reg_status reg_get_tile_rows(reg_series_t s, int32_t level, int32_t *grad_rows, 
  * 0..n_pairs-1 of `series` (best of `repeats` runs) and picks, level by level
  * from the finest (levels of at least 129 nodes), the gradient and trial tile
  * rows with the shortest time per device step, then the step sizes per trial
- * pass (2, 4 or 8) with the shortest batch time; a change must gain 2%.  The
+ * pass (2, 3, 4 or 8) with the shortest batch time; a change must gain 2%.  The
  * result stays in the handle (reg_get_tile_rows, and reg_params'
  * trials_per_pass as the handle uses it).  It overwrites the data slots
  * 0..n_pairs-1 (and drops a pending learned start): call it before

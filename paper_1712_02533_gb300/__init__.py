@@ -47,7 +47,8 @@ class Params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("armijo_sigma", ctypes.c_double), ("tau_init", ctypes.c_double),
                 ("tau_max", ctypes.c_double), ("tau_min", ctypes.c_double), ("storage", ctypes.c_int32),
                 ("trials_per_pass", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("init_levels", ctypes.c_int32), ("allocator", Allocator)]
+                ("init_levels", ctypes.c_int32), ("learned_fallback_px", ctypes.c_double),
+                ("allocator", Allocator)]
 
 
 class OpDesc(ctypes.Structure):

@@ -99,6 +99,7 @@ struct OpReq {
     int series, frame_i, frame_k, init;
     int left, right, dst;  // slot indices (-1 none)
     int skip = 0;          // coarse pyramid levels the operator leaves out
+    int judge = 0;         // learned start: measure how far the operator moves it
 };
 
 constexpr int GRAPH_STEPS = 8;
@@ -401,6 +402,7 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
         d.right = o.right >= 0 ? si.slots + (size_t)o.right * si.slot_elems : nullptr;
         d.out = si.slots + (size_t)o.dst * si.slot_elems;
         d.slot_pitch = si.pitch[si.nl - 1];
+        d.judge = o.judge;
         char *w = s->d_ws + ws_off[i];
         for (int j = 0; j < d.nl; j++) {
             const int k = o.skip + j;  // level index within the series' pyramid
@@ -518,6 +520,7 @@ reg_status validate_params(const reg_params *p)
     if (p->storage != REG_STORAGE_F32 && p->storage != REG_STORAGE_BF16) return fail(REG_EINVAL, "bad storage");
     if (p->init_levels < 0 || p->init_levels > p->n_levels)
         return fail(REG_EINVAL, "init_levels must be in [0, n_levels]");
+    if (!(p->learned_fallback_px >= 0.0)) return fail(REG_EINVAL, "learned_fallback_px must be >= 0");
     return REG_OK;
 }
 
@@ -549,6 +552,7 @@ void reg_default_params(reg_params *p)
     p->tau_min = 1e-12;
     p->storage = REG_STORAGE_F32;
     p->trials_per_pass = 4;
+    p->learned_fallback_px = 2.0;
     p->max_steps = 0;
     p->flags = 0;
 }
@@ -811,12 +815,45 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
         // identity start, or (after reg_cnn_init_series) the slot's initial guess
         for (int e = 0; e < S.n_data; e++)
             pre.push_back(S.pre_from_slots
-                              ? OpReq{si, e, e + 1, 1, e, -1, e, s->p.init_levels ? S.nl - s->p.init_levels : 0}
+                              ? OpReq{si, e, e + 1, 1, e, -1, e, s->p.init_levels ? S.nl - s->p.init_levels : 0,
+                                      s->p.init_levels && s->p.init_levels < S.nl}
                               : OpReq{si, e, e + 1, 0, -1, -1, e});
         S.pre_from_slots = false;
     }
     std::vector<int32_t> stat(pre.size());
     RET(run_batch(s, pre, [] { return REG_OK; }, stat.data(), nullptr));  // returns after a sync
+    // A learned start that skips coarse levels is judged by the plain method:
+    // the mean move of the operator away from it over the finest nodes (px).
+    // An operator that had to move it by more than learned_fallback_px started
+    // outside the basin its fine levels can reach: it is run again from the
+    // identity on every level.  (A learned start on every level needs no
+    // fallback: its coarse levels already had their say.)
+    int n_judged = 0, n_fallback = 0;
+    double corr_sum = 0.0, corr_max = 0.0;
+    {
+        std::vector<OpReq> again;
+        std::vector<size_t> again_idx;
+        for (size_t i = 0; i < pre.size(); i++) {
+            if (!pre[i].judge) continue;
+            const SeriesInfo &S = s->S[pre[i].series];
+            const double nn = (double)S.n[S.nl - 1] * S.n[S.nl - 1];
+            const double c = s->h_st[i].corr / nn;
+            n_judged++;
+            corr_sum += c;
+            corr_max = std::max(corr_max, c);
+            if (s->p.learned_fallback_px > 0.0 && !(c <= s->p.learned_fallback_px)) {
+                const OpReq &o = pre[i];
+                again.push_back(OpReq{o.series, o.frame_i, o.frame_k, 0, -1, -1, o.dst});
+                again_idx.push_back(i);
+            }
+        }
+        if (!again.empty()) {
+            std::vector<int32_t> st2(again.size());
+            RET(run_batch(s, again, [] { return REG_OK; }, st2.data(), nullptr));
+            for (size_t j = 0; j < again.size(); j++) stat[again_idx[j]] = st2[j];
+            n_fallback = (int)again.size();
+        }
+    }
     const double pre_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t pre_iters = s->tot_iters - it0;
     int counts[5] = {0, 0, 0, 0, 0};
@@ -883,11 +920,13 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
     if (report && buf_len > 0) {
         snprintf(report, buf_len,
                  "{\"kind\": %d, \"preprocessing_ops\": %zu, \"preprocessing_ms\": %.3f, "
-                 "\"preprocessing_iters\": %lld, \"scan_ops\": %d, \"scan_batches\": %d, "
+                 "\"preprocessing_iters\": %lld, \"learned\": {\"ops\": %d, \"mean_correction_px\": %.5f, "
+                 "\"max_correction_px\": %.5f, \"fallbacks\": %d}, \"scan_ops\": %d, \"scan_batches\": %d, "
                  "\"ops\": %lld, \"iters\": %lld, \"trials\": %lld, \"evals\": %lld, \"steps\": %lld, \"ms\": %.3f, "
                  "\"grids\": [%d, %d, %d], "
                  "\"status\": {\"converged\": %d, \"maxiter\": %d, \"stalled\": %d, \"nonfinite\": %d, \"zero_gradient\": %d}}",
-                 (int)kind, pre.size(), pre_ms, (long long)pre_iters, scan_ops, batches, (long long)(s->tot_ops - ops0),
+                 (int)kind, pre.size(), pre_ms, (long long)pre_iters, n_judged,
+                 n_judged ? corr_sum / n_judged : 0.0, corr_max, n_fallback, scan_ops, batches, (long long)(s->tot_ops - ops0),
                  (long long)(s->tot_iters - it0), (long long)(s->tot_trials - tr0), (long long)(s->tot_evals - ev0),
                  (long long)(s->tot_steps - st0), ms, s->grid_P, s->grid_G, s->grid_T, counts[0], counts[1], counts[2],
                  counts[3], counts[4]);
@@ -1359,7 +1398,7 @@ reg_status reg_autotune(reg_series_t s, int32_t series, int32_t n_pairs, int32_t
         RET(measure(ps, tot));
         double best = tot;
         int keep = keep0;
-        for (int J : {2, 4, 8}) {
+        for (int J : {2, 3, 4, 8}) {
             if (J == keep0) continue;
             s->p.trials_per_pass = J;
             set_grids(s);

@@ -507,6 +507,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
         const int r0 = (t / tx) * REG_TY, c = (t % tx) * REG_TX + lx;
         const float tau = (float)s.tau_acc;
         const bool fin = (s.phase == PH_FINAL);
+        float corr = 0.f;  // judged ops: |final - learned start| over this thread's nodes
 #pragma unroll
         for (int k = 0; k < REG_RPT; k++) {
             const int r = r0 + ly + k * REG_ROWSTEP;
@@ -518,7 +519,13 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
                     float2 d = v.d;
                     u = df_add2(u, tau * d.x, tau * d.y);
                 }
-                op.out[(int64_t)r * op.slot_pitch + c] = make_float2(u.x + u.z, u.y + u.w);
+                const float2 res = make_float2(u.x + u.z, u.y + u.w);
+                float2 &dst = op.out[(int64_t)r * op.slot_pitch + c];
+                if (op.judge) {
+                    const float2 g0 = dst;
+                    corr += fabsf(res.x - g0.x) + fabsf(res.y - g0.y);
+                }
+                dst = res;
             } else {
                 const LevelDesc &Cv = op.lv[s.lvl - 1];
                 const NodeRec *V = Cv.V[s.src];
@@ -545,6 +552,10 @@ __global__ void __launch_bounds__(REG_THREADS, 4) k_prolong(BatchDev b)
                     }
                 Lv.V[0][(int64_t)r * Lv.pitch + c].u = acc;
             }
+        }
+        if (fin && op.judge) {  // block-uniform: the whole block works on this item
+            const float w = warp_sum(corr);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&b.st[o].corr, (double)w);
         }
     }
 }

@@ -81,7 +81,7 @@ struct OpDesc {
     const float2 *right;
     float2 *out;            // destination slot (finest level)
     int slot_pitch;
-    int pad;
+    int judge;              // the output slot holds a learned start: measure the correction
     LevelDesc lv[REG_MAX_LEVELS];  // index 0 = coarsest level m0
 };
 
@@ -100,6 +100,7 @@ struct OpState {
     double slope;
     double Qud, Qdd;  // Dirichlet forms u^T K d and d^T K d of the current search
     double trial_tau[REG_MAX_TRIALS];
+    double corr;  // judged ops: sum over finest nodes of |u_final - u_start| (x + y, px)
 };
 
 // Device-side batch: everything the step kernels need, passed by value.

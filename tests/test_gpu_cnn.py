@@ -132,7 +132,7 @@ def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
     y = ocnn.forward(theta.astype(np.float64), _oracle_inputs(orc, fr),
                      bf16_layers=(1, 2, 3, 4) if tensor_cores else ())
     u0 = ocnn.upsample(y[0], 256)
-    p = reg.default_params(n_levels=3, init_levels=2, iter_max=50, lam=10.0)
+    p = reg.default_params(n_levels=3, init_levels=2, iter_max=50, lam=10.0, learned_fallback_px=0.0)
     with reg.Cnn(theta, side=256, max_batch=4) as net, reg.Series(fr, p) as s:
         s.cnn_init(net, tensor_cores=tensor_cores)
         init, se = s.get_slot(0)
@@ -151,6 +151,37 @@ def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
         u, _, stl = orc.register(g0, g1, orc.params(n_levels=2, iter_max=50, lam=10.0), u_init=u0 / 256)
     assert len(stl) == 2
     _assert_op_parity(d, u * 256, gtr, t.rows, "A(0,1) from the learned start", g0, g1)
+
+
+def test_plain_method_judges_the_learned_start_and_falls_back(reg, syn):
+    """The plain method judges each learned start by how far it has to move it.
+    A network whose predictions are far off (its weights scaled up) makes every
+    operator exceed the threshold; each is then run again from the identity on
+    every level, so the series equals the plain scan bit for bit.  With the
+    threshold at 0 the judgement is reported but nothing falls back."""
+    import synth
+    from paper_1712_02533_gb300 import learned
+    fr = syn.series(41, 6, 256, **learned.TRAIN_SERIES)
+    theta = synth.cnn_params(8)
+    theta[-2 - 32 * 9 * 2:] *= 200.0  # last layer: predictions of tens of pixels
+    p = reg.default_params(n_levels=3, init_levels=1, iter_max=50, lam=10.0)
+    with reg.Series(fr, p) as s:
+        s.prefix_scan(reg.SKLANSKY)
+        plain = s.get_deformations()
+    with reg.Cnn(theta, side=256, max_batch=8) as net:
+        with reg.Series(fr, p) as s:
+            s.cnn_init(net)
+            rep = s.prefix_scan(reg.SKLANSKY)
+            got = s.get_deformations()
+        assert rep["learned"]["ops"] == 5 and rep["learned"]["fallbacks"] == 5, rep["learned"]
+        assert rep["learned"]["mean_correction_px"] > 2.0
+        assert np.array_equal(got, plain)
+        p0 = reg.default_params(n_levels=3, init_levels=1, iter_max=50, lam=10.0, learned_fallback_px=0.0)
+        with reg.Series(fr, p0) as s:
+            s.cnn_init(net)
+            rep0 = s.prefix_scan(reg.SKLANSKY)
+        assert rep0["learned"]["ops"] == 5 and rep0["learned"]["fallbacks"] == 0
+        assert rep0["learned"]["max_correction_px"] > 2.0
 
 
 def test_trained_network_gains_over_the_identity_start(reg, syn):
