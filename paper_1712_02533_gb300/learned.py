@@ -126,7 +126,7 @@ def compare(cnn: Cnn, frames, gt, n_levels=5, iter_max=50, lam=10.0, kind=None, 
         err = np.abs(d[1:] - gt[1:])[:, :, margin:-margin, margin:-margin]
         row = dict(form="plain" if il is None else "learned", init_levels=n_levels if il is None else il,
                    series_s=t2 - t0, cnn_ms=1e3 * (t1 - t0), preprocessing_ms=rep["preprocessing_ms"],
-                   iters=rep["iters"], status=rep["status"], gt_err_px=float(err.mean()))
+                   iters=rep["iters"], status=rep["status"], judged=rep.get("learned"), gt_err_px=float(err.mean()))
         if plain is None:
             plain = d
         else:
