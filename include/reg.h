@@ -262,7 +262,8 @@ reg_status reg_cnn_pairs(reg_series_t s, int32_t series, int32_t first_pair, int
  * onto the finest vertex grid in frame pixels, and store it in the pair's data
  * slot (reg_get_slot reads it back); the next reg_prefix_scan starts those
  * preprocessing operators from the slots instead of the identity, on the
- * finest reg_params.init_levels levels. */
+ * finest reg_params.init_levels levels, and judges each start that skips
+ * levels (reg_params.learned_fallback_px). */
 reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int32_t tensor_cores);
 
 /* Tiles of the step kernels.  The gradient and trial passes walk strip tiles
