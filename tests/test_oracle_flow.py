@@ -146,3 +146,24 @@ def test_function_b_is_a_with_composed_initial_guess(orc, syn):
     outs, st, it, tr, en = orc.apply_batch([dict(R=g[0], T=g[2], left=u01, right=u12)], p)
     direct, s, _ = orc.register(g[0], g[2], p, u_init=orc.compose(u01, u12))
     assert np.array_equal(outs[0], direct)
+
+
+def test_exact_start_stays_put_on_the_finest_level(orc, syn):
+    """Started from the exact solution of a noise-free translated pair (a
+    constant field: the regulariser vanishes and the data term is stationary
+    there up to boundary effects), function A on the finest level alone -- the
+    learned form that skips every coarse level -- moves it by < 0.01 px
+    inside.  (Coarse levels have their own, slightly different optimum, which
+    is why a start that keeps them is not expected to stay put.)"""
+    t = np.array([1.3, -0.7])
+    side = 128
+    f = syn.series(1, 2, side, noise=False, drift=[[0, 0], t], dist_amp=0, sigma=5.0, spacing=20.0)
+    R, T = orc.embed(f[0]), orc.embed(f[1])
+    u0 = np.empty((2, side + 1, side + 1))
+    u0[0], u0[1] = -t[0] / side, -t[1] / side
+    p = orc.params(n_levels=1, iter_max=200, lam=10.0, epsilon=1e-10)
+    u, status, st = orc.register(R, T, p, u_init=u0)
+    assert len(st) == 1
+    m = 16
+    err = np.abs(u * side + t[:, None, None])[:, m:-m, m:-m]
+    assert err.max() < 0.01, err.max()
