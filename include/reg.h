@@ -133,7 +133,9 @@ typedef enum reg_scan_kind {
     REG_SCAN_BRENT_KUNG = 3,  /* Algorithm "Brent-Kung" */
     REG_SCAN_BLELLOCH = 4,    /* Algorithm "Blelloch" (exclusive, shifted) */
     REG_SCAN_CHUNKED = 5,     /* general strategy, Algorithm "Distributed parallel prefix sum" */
-    REG_SCAN_CHUNKED_ALT = 6  /* alternative strategy (reduce-then-scan) */
+    REG_SCAN_CHUNKED_ALT = 6, /* alternative strategy (reduce-then-scan) */
+    REG_SCAN_HAN_CARLSON = 7  /* Section "Other work": Brent-Kung/Kogge-Stone hybrid,
+                                 parameter k (passed as `chunks`, k >= 1) */
 } reg_scan_kind;
 
 /* Create a handle holding `n_series` series (one segmented scan).
@@ -163,8 +165,10 @@ reg_status reg_apply_operator_batch(reg_series_t s, int32_t n_ops, const reg_op_
 
 /* Image series registration: preprocessing (all A ops of all series in one
  * batch) followed by the prefix scan with the chosen schedule; each scan level
- * is one reg_apply_operator_batch over all series (segmented scan).  chunks
- * and global_kind are used by the chunked strategies only.  report_json_buf
+ * is one reg_apply_operator_batch over all series (segmented scan).  chunks:
+ * the chunk count of the chunked strategies (1..64), or k of Han-Carlson
+ * (1..30; values above log2 N give Brent-Kung); global_kind: the chunked
+ * strategies' global scan (a non-chunked kind up to Blelloch).  report_json_buf
  * (nullable): receives a NUL-terminated JSON summary (levels, op counts,
  * iterations, per-kernel timings when REG_FLAG_PROFILE is set). */
 reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, reg_scan_kind global_kind,

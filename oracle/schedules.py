@@ -18,10 +18,10 @@ prefix sum"; readings of garbled loop bounds are noted per function.
 """
 from __future__ import annotations
 
-SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT = range(7)
+SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON = range(8)
 NAMES = {SERIAL: "serial", SKLANSKY: "sklansky", KOGGE_STONE: "kogge_stone",
          BRENT_KUNG: "brent_kung", BLELLOCH: "blelloch", CHUNKED: "chunked",
-         CHUNKED_ALT: "chunked_alt"}
+         CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson"}
 
 
 def _clog2(n: int) -> int:
@@ -130,6 +130,31 @@ def blelloch(n, base=0, aux=None):
     shift.append(("copy", base + n - 1, total))
     levels.append(shift)
     return levels
+
+
+def han_carlson(n, k=1, base=0):
+    """Han-Carlson hybrid of Brent-Kung and Kogge-Stone (Section "Other work";
+    span log2 N + k).  Blocks of B = 2^k elements: the tree's first k levels
+    leave each block's reduction in its last element; Kogge-Stone over those
+    last elements of the complete blocks turns them into prefixes; the tree's
+    down-sweep, levels k-1 .. 0, then gives every other element its prefix
+    (those of an incomplete last block included).  k is clamped to [1, log2 N]."""
+    L = _clog2(n)
+    k = max(1, min(k, L))
+    levels = []
+    for i in range(k):
+        st = 1 << i
+        levels.append([("op", base + j, base + j - st, base + j) for j in range(2 * st - 1, n, 2 * st)])
+    B = 1 << k
+    ends = [base + (t + 1) * B - 1 for t in range(n // B)]
+    for i in range(_clog2(len(ends))):
+        st = 1 << i
+        levels.append([("op", ends[t], ends[t - st], ends[t]) for t in range(st, len(ends))])
+    for i in reversed(range(k)):
+        st = 1 << i
+        levels.append([("op", base + j + st - 1, base + j - 1, base + j + st - 1)
+                       for j in range(2 * st, n - st + 1, 2 * st)])
+    return [lv for lv in levels if lv]
 
 
 def aux_slots(kind, n, chunks=0, global_kind=KOGGE_STONE):
@@ -253,6 +278,8 @@ def schedule(kind, n, chunks=0, global_kind=KOGGE_STONE, base=0):
         return chunked(n, chunks, global_kind, base)
     if kind == CHUNKED_ALT:
         return chunked_alt(n, chunks, global_kind, base)
+    if kind == HAN_CARLSON:
+        return han_carlson(n, chunks if chunks else 1, base)
     raise ValueError(kind)
 
 

@@ -28,9 +28,9 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, EKERNEL = range(7)
 # reg_op_status
 OP_CONVERGED, OP_MAXITER, OP_LS_STALLED, OP_NONFINITE, OP_ZERO_GRADIENT = range(5)
 # reg_scan_kind
-SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT = range(7)
+SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON = range(8)
 SCAN_NAMES = {SERIAL: "serial", SKLANSKY: "sklansky", KOGGE_STONE: "kogge_stone", BRENT_KUNG: "brent_kung",
-              BLELLOCH: "blelloch", CHUNKED: "chunked", CHUNKED_ALT: "chunked_alt"}
+              BLELLOCH: "blelloch", CHUNKED: "chunked", CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson"}
 STORAGE_F32, STORAGE_BF16 = 0, 1
 FLAG_PROFILE = 1
 
@@ -224,7 +224,11 @@ def apply_operator_batch(h, ops):
     return st, it
 
 
-def prefix_scan(h, kind=SERIAL, chunks=16, global_kind=KOGGE_STONE):
+def prefix_scan(h, kind=SERIAL, chunks=None, global_kind=KOGGE_STONE):
+    """chunks: chunk count of the chunked kinds (default 16), k of Han-Carlson
+    (default 1)."""
+    if chunks is None:
+        chunks = 1 if kind == HAN_CARLSON else 16
     buf = ctypes.create_string_buffer(4096)
     _check(_load().reg_prefix_scan(h, kind, chunks, global_kind, buf, len(buf)))
     return json.loads(buf.value.decode())
@@ -444,7 +448,7 @@ class Series:
     def apply_operator_batch(self, ops):
         return apply_operator_batch(self.h, ops)
 
-    def prefix_scan(self, kind=SERIAL, chunks=16, global_kind=KOGGE_STONE):
+    def prefix_scan(self, kind=SERIAL, chunks=None, global_kind=KOGGE_STONE):
         return prefix_scan(self.h, kind, chunks, global_kind)
 
     def get_deformations(self, series=0, first=0, count=None, out=None):

@@ -4,8 +4,9 @@
 // one level read the values held before the level (level-synchronous, i.e. the
 // double buffering the paper prescribes for Kogge-Stone).  Slots >= N are
 // auxiliary.  Algorithms from Chapter "Prefix sum" (serial, Blelloch,
-// Brent-Kung, Kogge-Stone, Sklansky) and Chapter "Distributed prefix sum"
-// (general strategy, inclusive global scan, alternative strategy).
+// Brent-Kung, Kogge-Stone, Sklansky, and the Han-Carlson hybrid of Section
+// "Other work") and Chapter "Distributed prefix sum" (general strategy,
+// inclusive global scan, alternative strategy).
 #include "schedule.h"
 
 #include <algorithm>
@@ -131,6 +132,33 @@ static void blelloch(Schedule &s, int n, int base)
     add(s, lv, OP_COPY, base + n - 1, total, -1);
 }
 
+// Han-Carlson hybrid (Section "Other work": Brent-Kung and Kogge-Stone merged,
+// parameter k, span log2 N + k): the first k up-sweep levels of the tree reduce
+// blocks of 2^k elements; Kogge-Stone runs over the last elements of the
+// complete blocks, which then hold their prefixes; the last k down-sweep levels
+// of the tree fill in the rest (the elements of an incomplete last block too).
+// k = 1 is the classic adder; k >= log2 N gives Brent-Kung.
+static void han_carlson(Schedule &s, int n, int k, int base)
+{
+    k = std::max(1, std::min(k, clog2(n)));
+    for (int i = 0; i < k; i++) {
+        const int st = 1 << i, lv = (int)s.levels.size();
+        for (int j = 2 * st - 1; j < n; j += 2 * st) add(s, lv, OP_COMBINE, base + j, base + j - st, base + j);
+    }
+    const int blk = 1 << k, m = n / blk;  // block t (t < m) ends at (t + 1) blk - 1
+    for (int i = 0; i < clog2(m); i++) {
+        const int st = 1 << i, lv = (int)s.levels.size();
+        for (int t = st; t < m; t++) {
+            const int e = (t + 1) * blk - 1, f = (t - st + 1) * blk - 1;
+            add(s, lv, OP_COMBINE, base + e, base + f, base + e);
+        }
+    }
+    for (int i = k - 1; i >= 0; i--) {
+        const int st = 1 << i, lv = (int)s.levels.size();
+        for (int j = 2 * st; j + st - 1 < n; j += 2 * st) add(s, lv, OP_COMBINE, base + j + st - 1, base + j - 1, base + j + st - 1);
+    }
+}
+
 static int pow2ceil(int n) { return 1 << clog2(n); }
 
 int aux_slots(int kind, int n, int chunks, int global_kind)
@@ -254,6 +282,7 @@ bool make_schedule(int kind, int n, int chunks, int global_kind, Schedule &out)
     case K_KOGGE_STONE: kogge_stone(out, n, 0); break;
     case K_BRENT_KUNG: brent_kung(out, n, 0); break;
     case K_BLELLOCH: blelloch(out, n, 0); break;
+    case K_HAN_CARLSON: han_carlson(out, n, chunks, 0); break;
     case K_CHUNKED:
         if (global_kind < 0 || global_kind > K_BLELLOCH) return false;
         chunked(out, n, chunks, global_kind, 0);

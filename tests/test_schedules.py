@@ -108,3 +108,34 @@ def test_level_synchronous_semantics_needed_for_kogge_stone():
             for o in level:
                 inplace[o[1]] = _op(inplace[o[2]], inplace[o[3]])
     assert S.run(lv, data, _op) == _fold(n)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_han_carlson_equals_serial_fold(k):
+    for n in range(1, 65):
+        lv = S.schedule(S.HAN_CARLSON, n, k)
+        assert S.aux_slots(S.HAN_CARLSON, n, k) == 0
+        out = S.run(lv, [_mat(i) for i in range(n)], _op)
+        assert out == _fold(n), (k, n)
+
+
+def test_han_carlson_span_and_work_closed_forms():
+    """For N = 2^L and 1 <= k <= L: span L + k (Section "Other work"); work =
+    up-sweep (N - M) + Kogge-Stone over M = N / 2^k block ends (M (L-k) - M + 1)
+    + down-sweep (N - M - k), i.e. 2N - 3M - k + M (L - k) + 1.  At k = L this
+    is Brent-Kung's 2N - log2 N - 2, and the op lists coincide."""
+    for L in range(1, 9):
+        n = 1 << L
+        for k in range(1, L + 1):
+            ops, steps = S.counts(S.han_carlson(n, k))
+            m = n >> k
+            assert steps == L + k - (1 if k == L else 0), (n, k, steps)
+            assert ops == 2 * n - 3 * m - k + m * (L - k) + 1, (n, k, ops)
+        assert S.han_carlson(n, L) == S.brent_kung(n)
+    # between Kogge-Stone's work and span and Brent-Kung's
+    for L in range(3, 9):
+        n = 1 << L
+        ks_ops, ks_steps = S.counts(S.kogge_stone(n))
+        bk_ops, bk_steps = S.counts(S.brent_kung(n))
+        hc_ops, hc_steps = S.counts(S.han_carlson(n, 1))
+        assert bk_ops < hc_ops < ks_ops and ks_steps < hc_steps < bk_steps
