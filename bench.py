@@ -38,9 +38,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kind", default="sklansky",
                     choices=["serial", "sklansky", "kogge_stone", "brent_kung", "blelloch", "chunked", "chunked_alt",
-                             "han_carlson"])
+                             "han_carlson", "ladner_fischer"])
     ap.add_argument("--chunks", type=int, default=None,
-                    help="chunk count of the chunked kinds (default 16), k of han_carlson (default 1)")
+                    help="chunk count of the chunked kinds (default 16), k of han_carlson and ladner_fischer (default 1)")
     ap.add_argument("--frames", type=int, default=WORKLOAD["n_frames"])
     ap.add_argument("--side", type=int, default=WORKLOAD["side"])
     ap.add_argument("--levels", type=int, default=WORKLOAD["n_levels"])
@@ -330,7 +330,8 @@ def main():
                        "levels": cfg["n_levels"], "iter_max": cfg["iter_max"], "lambda": cfg["lam"],
                        "schedule": a.kind,
                        "chunks": (a.chunks or 16) if "chunked" in a.kind else None,
-                       "han_carlson_k": (a.chunks or 1) if a.kind == "han_carlson" else None,
+                       "hybrid_k": (a.chunks if a.chunks is not None else 1)
+                       if a.kind in ("han_carlson", "ladner_fischer") else None,
                        "ops_per_step": ops_per_step, "preprocessing_ops": rep["preprocessing_ops"],
                        "scan_ops": rep["scan_ops"], "scan_batches": rep["scan_batches"],
                        "iters_per_step": rep["iters"], "l2": "working set (GBs) larger than L2; no flush",

@@ -134,8 +134,10 @@ typedef enum reg_scan_kind {
     REG_SCAN_BLELLOCH = 4,    /* Algorithm "Blelloch" (exclusive, shifted) */
     REG_SCAN_CHUNKED = 5,     /* general strategy, Algorithm "Distributed parallel prefix sum" */
     REG_SCAN_CHUNKED_ALT = 6, /* alternative strategy (reduce-then-scan) */
-    REG_SCAN_HAN_CARLSON = 7  /* Section "Other work": Brent-Kung/Kogge-Stone hybrid,
+    REG_SCAN_HAN_CARLSON = 7, /* Section "Other work": Brent-Kung/Kogge-Stone hybrid,
                                  parameter k (passed as `chunks`, k >= 1) */
+    REG_SCAN_LADNER_FISCHER = 8 /* Section "Other work": Brent-Kung/Sklansky hybrid,
+                                   parameter k (passed as `chunks`, k >= 0; 0 is Sklansky) */
 } reg_scan_kind;
 
 /* Create a handle holding `n_series` series (one segmented scan).
@@ -167,7 +169,8 @@ reg_status reg_apply_operator_batch(reg_series_t s, int32_t n_ops, const reg_op_
  * batch) followed by the prefix scan with the chosen schedule; each scan level
  * is one reg_apply_operator_batch over all series (segmented scan).  chunks:
  * the chunk count of the chunked strategies (1..64), or k of Han-Carlson
- * (1..30; values above log2 N give Brent-Kung); global_kind: the chunked
+ * (1..30) and Ladner-Fischer (0..30) (values above log2 N give Brent-Kung);
+ * global_kind: the chunked
  * strategies' global scan (a non-chunked kind up to Blelloch).  report_json_buf
  * (nullable): receives a NUL-terminated JSON summary (levels, op counts,
  * iterations, per-kernel timings when REG_FLAG_PROFILE is set). */

@@ -18,10 +18,10 @@ prefix sum"; readings of garbled loop bounds are noted per function.
 """
 from __future__ import annotations
 
-SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON = range(8)
+SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON, LADNER_FISCHER = range(9)
 NAMES = {SERIAL: "serial", SKLANSKY: "sklansky", KOGGE_STONE: "kogge_stone",
          BRENT_KUNG: "brent_kung", BLELLOCH: "blelloch", CHUNKED: "chunked",
-         CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson"}
+         CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson", LADNER_FISCHER: "ladner_fischer"}
 
 
 def _clog2(n: int) -> int:
@@ -157,6 +157,29 @@ def han_carlson(n, k=1, base=0):
     return [lv for lv in levels if lv]
 
 
+def ladner_fischer(n, k=0, base=0):
+    """Ladner-Fischer(k), Sklansky and Brent-Kung combined (Section "Other
+    work"): as Han-Carlson, with Sklansky's tree instead of Kogge-Stone over
+    the last elements of the complete blocks of 2^k elements; span
+    log2 N + k; k = 0 is Sklansky.  k is clamped to [0, log2 N]."""
+    L = _clog2(n)
+    k = max(0, min(k, L))
+    B = 1 << k
+    up = [[("op", base + j, base + j - (1 << i), base + j) for j in range((2 << i) - 1, n, 2 << i)]
+          for i in range(k)]
+    ends = [base + (t + 1) * B - 1 for t in range(n // B)]
+    middle = []
+    for i in range(_clog2(len(ends))):
+        st = 1 << i
+        lv = []
+        for src in range(st - 1, len(ends), 2 * st):
+            lv += [("op", ends[t], ends[src], ends[t]) for t in range(src + 1, min(src + st, len(ends) - 1) + 1)]
+        middle.append(lv)
+    down = [[("op", base + j + (1 << i) - 1, base + j - 1, base + j + (1 << i) - 1)
+             for j in range(2 << i, n - (1 << i) + 1, 2 << i)] for i in reversed(range(k))]
+    return [lv for lv in up + middle + down if lv]
+
+
 def aux_slots(kind, n, chunks=0, global_kind=KOGGE_STONE):
     """Number of auxiliary slots a schedule uses beyond the N data slots."""
     if kind == BLELLOCH:
@@ -280,6 +303,8 @@ def schedule(kind, n, chunks=0, global_kind=KOGGE_STONE, base=0):
         return chunked_alt(n, chunks, global_kind, base)
     if kind == HAN_CARLSON:
         return han_carlson(n, chunks if chunks else 1, base)
+    if kind == LADNER_FISCHER:
+        return ladner_fischer(n, chunks, base)
     raise ValueError(kind)
 
 

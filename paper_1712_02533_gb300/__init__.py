@@ -28,9 +28,10 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, EKERNEL = range(7)
 # reg_op_status
 OP_CONVERGED, OP_MAXITER, OP_LS_STALLED, OP_NONFINITE, OP_ZERO_GRADIENT = range(5)
 # reg_scan_kind
-SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON = range(8)
+SERIAL, SKLANSKY, KOGGE_STONE, BRENT_KUNG, BLELLOCH, CHUNKED, CHUNKED_ALT, HAN_CARLSON, LADNER_FISCHER = range(9)
 SCAN_NAMES = {SERIAL: "serial", SKLANSKY: "sklansky", KOGGE_STONE: "kogge_stone", BRENT_KUNG: "brent_kung",
-              BLELLOCH: "blelloch", CHUNKED: "chunked", CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson"}
+              BLELLOCH: "blelloch", CHUNKED: "chunked", CHUNKED_ALT: "chunked_alt", HAN_CARLSON: "han_carlson",
+              LADNER_FISCHER: "ladner_fischer"}
 STORAGE_F32, STORAGE_BF16 = 0, 1
 FLAG_PROFILE = 1
 
@@ -226,9 +227,9 @@ def apply_operator_batch(h, ops):
 
 def prefix_scan(h, kind=SERIAL, chunks=None, global_kind=KOGGE_STONE):
     """chunks: chunk count of the chunked kinds (default 16), k of Han-Carlson
-    (default 1)."""
+    and Ladner-Fischer (default 1)."""
     if chunks is None:
-        chunks = 1 if kind == HAN_CARLSON else 16
+        chunks = 1 if kind in (HAN_CARLSON, LADNER_FISCHER) else 16
     buf = ctypes.create_string_buffer(4096)
     _check(_load().reg_prefix_scan(h, kind, chunks, global_kind, buf, len(buf)))
     return json.loads(buf.value.decode())

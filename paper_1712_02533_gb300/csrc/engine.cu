@@ -801,8 +801,10 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
 {
     g_err.clear();
     if (!s) return fail(REG_EINVAL, "null handle");
-    if (kind < REG_SCAN_SERIAL || kind > REG_SCAN_HAN_CARLSON) return fail(REG_EINVAL, "unknown scan kind");
+    if (kind < REG_SCAN_SERIAL || kind > REG_SCAN_LADNER_FISCHER) return fail(REG_EINVAL, "unknown scan kind");
     if (kind == REG_SCAN_HAN_CARLSON && (chunks < 1 || chunks > 30)) return fail(REG_EINVAL, "Han-Carlson needs 1 <= k <= 30");
+    if (kind == REG_SCAN_LADNER_FISCHER && (chunks < 0 || chunks > 30))
+        return fail(REG_EINVAL, "Ladner-Fischer needs 0 <= k <= 30");
     if ((kind == REG_SCAN_CHUNKED || kind == REG_SCAN_CHUNKED_ALT) &&
         (chunks < 1 || chunks > 64 || global_kind < REG_SCAN_SERIAL || global_kind > REG_SCAN_BLELLOCH))
         return fail(REG_EINVAL, "chunked scans need 1 <= chunks <= 64 and a non-chunked global kind");

@@ -138,19 +138,27 @@ static void blelloch(Schedule &s, int n, int base)
 // complete blocks, which then hold their prefixes; the last k down-sweep levels
 // of the tree fill in the rest (the elements of an incomplete last block too).
 // k = 1 is the classic adder; k >= log2 N gives Brent-Kung.
-static void han_carlson(Schedule &s, int n, int k, int base)
+//
+// Ladner-Fischer(k) (the same section: Sklansky and Brent-Kung combined) is the
+// same construction with Sklansky's tree over the block ends instead of
+// Kogge-Stone: span log2 N + k at less work than Sklansky; k = 0 is Sklansky.
+static void block_hybrid(Schedule &s, int n, int k, int base, bool sklansky_middle)
 {
-    k = std::max(1, std::min(k, clog2(n)));
+    k = std::max(sklansky_middle ? 0 : 1, std::min(k, clog2(n)));
     for (int i = 0; i < k; i++) {
         const int st = 1 << i, lv = (int)s.levels.size();
         for (int j = 2 * st - 1; j < n; j += 2 * st) add(s, lv, OP_COMBINE, base + j, base + j - st, base + j);
     }
     const int blk = 1 << k, m = n / blk;  // block t (t < m) ends at (t + 1) blk - 1
+    auto end = [&](int t) { return base + (t + 1) * blk - 1; };
     for (int i = 0; i < clog2(m); i++) {
         const int st = 1 << i, lv = (int)s.levels.size();
-        for (int t = st; t < m; t++) {
-            const int e = (t + 1) * blk - 1, f = (t - st + 1) * blk - 1;
-            add(s, lv, OP_COMBINE, base + e, base + f, base + e);
+        if (sklansky_middle) {
+            // block end src = st - 1 + q 2 st feeds the following st block ends
+            for (int src = st - 1; src < m; src += 2 * st)
+                for (int t = src + 1; t <= src + st && t < m; t++) add(s, lv, OP_COMBINE, end(t), end(src), end(t));
+        } else {
+            for (int t = st; t < m; t++) add(s, lv, OP_COMBINE, end(t), end(t - st), end(t));
         }
     }
     for (int i = k - 1; i >= 0; i--) {
@@ -282,7 +290,8 @@ bool make_schedule(int kind, int n, int chunks, int global_kind, Schedule &out)
     case K_KOGGE_STONE: kogge_stone(out, n, 0); break;
     case K_BRENT_KUNG: brent_kung(out, n, 0); break;
     case K_BLELLOCH: blelloch(out, n, 0); break;
-    case K_HAN_CARLSON: han_carlson(out, n, chunks, 0); break;
+    case K_HAN_CARLSON: block_hybrid(out, n, chunks, 0, false); break;
+    case K_LADNER_FISCHER: block_hybrid(out, n, chunks, 0, true); break;
     case K_CHUNKED:
         if (global_kind < 0 || global_kind > K_BLELLOCH) return false;
         chunked(out, n, chunks, global_kind, 0);

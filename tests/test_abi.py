@@ -80,6 +80,14 @@ def test_han_carlson_schedule_matches_oracle(lib, k):
         assert aux == 0
 
 
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 9, 30])
+def test_ladner_fischer_schedule_matches_oracle(lib, k):
+    for n in list(range(1, 70)) + [127, 128, 399]:
+        got, aux = lib.schedule(S.LADNER_FISCHER, n, k)
+        assert _norm(got) == _norm(S.schedule(S.LADNER_FISCHER, n, k)), (k, n)
+        assert aux == 0
+
+
 def test_invalid_schedule_kind_is_rejected(lib):
     with pytest.raises(lib.RegError):
         lib.schedule(42, 8)

@@ -230,7 +230,7 @@ def test_config1_scan_operators_match_oracle(reg, orc, syn):
             acc = got.astype(np.float64) / 64
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 7])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 7, 8])
 def test_series_stable_input_matches_oracle(reg, orc, syn, kind):
     """Whole-series registration, every schedule, on the config-1 series
     without shot noise (expected counts), where the oracle's result is stable
@@ -240,7 +240,7 @@ def test_series_stable_input_matches_oracle(reg, orc, syn, kind):
     nl = cfg.pop("n_levels")
     fr = syn.series(noise=False, **cfg)
     p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    hc_k = 1  # Han-Carlson's parameter (unused by the other kinds here)
+    hc_k = 1  # k of Han-Carlson and Ladner-Fischer (unused by the other kinds here)
     with reg.Series(fr, p) as s:
         rep = s.prefix_scan(kind, chunks=hc_k)
         got = s.get_deformations()

@@ -139,3 +139,27 @@ def test_han_carlson_span_and_work_closed_forms():
         bk_ops, bk_steps = S.counts(S.brent_kung(n))
         hc_ops, hc_steps = S.counts(S.han_carlson(n, 1))
         assert bk_ops < hc_ops < ks_ops and ks_steps < hc_steps < bk_steps
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 5])
+def test_ladner_fischer_equals_serial_fold(k):
+    for n in range(1, 65):
+        lv = S.schedule(S.LADNER_FISCHER, n, k)
+        assert S.aux_slots(S.LADNER_FISCHER, n, k) == 0
+        assert S.run(lv, [_mat(i) for i in range(n)], _op) == _fold(n), (k, n)
+
+
+def test_ladner_fischer_span_and_work_closed_forms():
+    """For N = 2^L and 0 <= k <= L: span L + k (one less at k = L, whose top
+    down-sweep level is empty); work = up-sweep (N - M) + Sklansky over the
+    M = N / 2^k block ends ((M/2) log2 M) + down-sweep (N - M - k).  k = 0 is
+    Sklansky and k = L Brent-Kung, op list for op list."""
+    for L in range(1, 9):
+        n = 1 << L
+        for k in range(0, L + 1):
+            ops, steps = S.counts(S.ladner_fischer(n, k))
+            m = n >> k
+            assert steps == L + k - (1 if k == L else 0), (n, k, steps)
+            assert ops == 2 * n - 2 * m - k + (m // 2) * (L - k), (n, k, ops)
+        assert S.ladner_fischer(n, 0) == S.sklansky(n)
+        assert S.ladner_fischer(n, L) == S.brent_kung(n)
