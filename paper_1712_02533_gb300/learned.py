@@ -1,10 +1,19 @@
-"""Training the learned initialiser on displacements the plain method computes.
+"""Training the learned initialiser on displacements the plain method computes,
+and comparing the learned form with the plain one.
 
-The training pairs are neighbour pairs of seeded generator series of 256^2
-pixels; the plain GPU method (identity start) registers every pair, and the
-target is its displacement at the network's output positions (pixels (4i, 4j),
-i, j < 64).  The network trains on the GPU with the library's own forward,
-backward and Adam kernels; this module only moves data and loops.
+- training_set(): neighbour pairs of seeded generator series (256^2 frames by
+  default, or larger frames seen through their 257^2 pyramid level); the plain
+  GPU method (identity start) registers every pair, and the target is its
+  displacement at the network's output positions (every side/64-th frame
+  pixel), in pixels of the 256^2 input.
+- train(): Adam on minibatches with the library's own forward, backward and
+  update kernels; this module only moves data and loops.
+- compare(): series time and accuracy of the plain form against the learned
+  form (network start on the finest init_levels levels).
+- forward_rate(): forward throughput on the CUDA cores and the tensor cores.
+- main(): ``python -m paper_1712_02533_gb300.learned`` trains on pairs shaped
+  like the 400 x 1024^2 workload and compares on a fresh series (one JSON
+  object); ``--forward-rate B`` only times the forward pass.
 """
 from __future__ import annotations
 
