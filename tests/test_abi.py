@@ -48,6 +48,11 @@ def test_status_strings_and_defaults(lib):
     assert b"invalid" in so.reg_status_string(1)
     p = lib.default_params()
     assert p.n_levels == 3 and p.iter_max == 50 and p.armijo_sigma == 0.5 and p.trials_per_pass == 4
+    # every field after the first ones as well: the binding's struct layout is the header's
+    assert p.epsilon == 1e-7 and p.lambda_ == 10.0 and p.tau_init == 1.0 and p.tau_max == 1e4
+    assert p.tau_min == 1e-12 and p.storage == lib.STORAGE_F32 and p.max_steps == 0 and p.flags == 0
+    assert p.init_levels == 0 and p.learned_fallback_px == 2.0
+    assert not p.allocator.alloc and not p.allocator.free
 
 
 def _norm(levels):
