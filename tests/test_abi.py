@@ -96,3 +96,33 @@ def test_ladner_fischer_schedule_matches_oracle(lib, k):
 def test_invalid_schedule_kind_is_rejected(lib):
     with pytest.raises(lib.RegError):
         lib.schedule(42, 8)
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    that a C compiler gives the header's structures."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"reg_params": lib.Params, "reg_op_desc": lib.OpDesc, "reg_schedule_op": lib.ScheduleOp,
+               "reg_kernel_stats": lib.KernelStats, "reg_allocator": lib.Allocator}
+    cnames = {"lambda_": "lambda"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "reg.h"', 'int main(void) {']
+    want = []
+    for cname, py in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {cnames.get(fname, fname)}));')
+            want.append(getattr(py, fname).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
