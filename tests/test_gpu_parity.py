@@ -306,3 +306,27 @@ def test_invalid_arguments_are_rejected(reg, syn):
             s.apply_operator_batch([(0, -1, -1, 99, 0, 1)])
     with pytest.raises(reg.RegError):
         reg.Series(syn.series(9, 3, 48), reg.default_params(n_levels=2))  # not a power of two
+
+
+def test_full_size_sampled_operators_match_oracle(reg, orc, syn):
+    """The 400 x 1024^2 workload (5 levels) in the launch configuration the
+    benchmark times (all 399 neighbour pairs in one batch): sampled operators
+    against the oracle computed one by one, under the same criterion as the
+    smaller configurations."""
+    cfg = dict(syn.CONFIGS["c3_400x1024"])
+    nl = cfg.pop("n_levels")
+    fr = syn.series(**cfg)
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
+    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    side = 1024
+    n = len(fr) - 1
+    with reg.Series(fr, p) as s:
+        s.set_trace(1 << 23)
+        s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(n)])
+        gtr = _gpu_traces_by_op(s.get_trace(), n)
+        got = {e: s.get_slot(e)[0] for e in (0, 250)}
+    for e, u_gpu in got.items():
+        R, T = orc.embed(fr[e]), orc.embed(fr[e + 1])
+        with orc.trace() as t:
+            u, _, _ = orc.register(R, T, op)
+        _assert_op_parity(u_gpu, u * side, gtr[e], t.rows, f"A({e},{e + 1}) 1024^2", R, T)
