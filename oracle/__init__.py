@@ -208,9 +208,10 @@ def register(R, T, p: Params, u_init=None):
 
 
 class trace:
-    """Context manager recording every Armijo trial of the (single-threaded)
-    level solves run inside it: rows (n, iteration, tau, dE, sigma tau slope,
-    accepted)."""
+    """Context manager recording every Armijo trial of the level solves that
+    the calling thread runs inside it (the trace is per host thread, so several
+    threads may each trace their own operator): rows (n, iteration, tau, dE,
+    sigma tau slope, accepted)."""
 
     def __init__(self, cap=1 << 20):
         self.buf = np.zeros((cap, 6))

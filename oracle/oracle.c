@@ -36,9 +36,11 @@ static double *dalloc(size_t n) { return (double *)calloc(n, sizeof(double)); }
 
 /* Optional trace of every Armijo trial of orc_solve_level (for comparing
  * decision sequences in tests): records of 6 doubles
- * {n, iteration, tau, E(u + tau d) - E(u), sigma tau g^T d, accepted}. */
-static double *g_trace = NULL;
-static long g_trace_cap = 0, g_trace_len = 0;
+ * {n, iteration, tau, E(u + tau d) - E(u), sigma tau g^T d, accepted}.
+ * One trace per host thread, so that operators solved on several threads at
+ * once each record their own. */
+static _Thread_local double *g_trace = NULL;
+static _Thread_local long g_trace_cap = 0, g_trace_len = 0;
 
 void orc_set_trace(double *buf, long cap)
 {
