@@ -105,6 +105,11 @@ typedef struct reg_params {
 
 #define REG_FLAG_PROFILE 1    /* time kernel families with CUDA events */
 
+/* Replace the handle's reg_params.flags (REG_FLAG_*); takes effect at the next
+ * batch.  With REG_FLAG_PROFILE the step kernels are launched one by one
+ * between CUDA events instead of as the captured graph. */
+reg_status reg_set_flags(reg_series_t s, int32_t flags);
+
 /* Fills *p with the defaults: n_levels 3, iter_max 50, epsilon 1e-7,
  * lambda 10, sigma 0.5, tau_init 1, tau_max 1e4, tau_min 1e-12, F32 storage,
  * 4 trials per pass, init_levels 0, learned_fallback_px 2. */
@@ -311,9 +316,12 @@ reg_status reg_schedule(reg_scan_kind kind, int32_t n, int32_t chunks, reg_scan_
 
 /* Per-kernel-family statistics accumulated since creation (or the last reset):
  * launches, device time (ms, CUDA events, only with REG_FLAG_PROFILE) and
- * algorithmic bytes (counted on the device per processed node).  One more
- * record, "trial_exact_nodes", counts in `items` the trial-pass nodes whose
- * largest move left their cell (the exact path of the trial kernel). */
+ * algorithmic bytes (counted on the device per processed node).  Three more
+ * records count nodes in `items`: "trial_exact_nodes", the trial-pass nodes
+ * whose largest move left their cell (the exact path of the trial kernel);
+ * "trial_seq_nodes", the sum over Armijo trials decided of the level's node
+ * count (the trials of the one-at-a-time rule, however many step sizes a pass
+ * evaluated); "trial_start_nodes", the nodes of level-start energy passes. */
 typedef struct reg_kernel_stats {
     char name[24];
     int64_t launches;
@@ -332,6 +340,25 @@ reg_status reg_reset_kernel_stats(reg_series_t s);
  * recorded.  Records of one op appear in decision order. */
 reg_status reg_set_trace(reg_series_t s, int64_t capacity);
 reg_status reg_get_trace(reg_series_t s, double *out, int64_t cap, int64_t *n_out);
+
+/* Lockstep replay (diagnostic).  The iteration of the gradient flow (Section
+ * "Gradient flow": phi^{k+1} = phi^k - tau A^{-1} E'[phi^k], tau from the
+ * Armijo rule) is chaotic on noisy frames: a decision whose margin is at the
+ * rounding level sends two correct implementations down different paths.  In
+ * lockstep the device takes a given sequence of accepted step sizes instead of
+ * searching, so that its iterates can be compared step by step with another
+ * implementation's.  After this call every reg_apply_operator_batch of exactly
+ * n_ops operators (each with n_levels levels) runs in lockstep: operator o on
+ * level k (0 = coarsest) makes counts[o * n_levels + k] gradient steps with
+ * the step sizes taken in order from taus (operator-major, then level, then
+ * iteration), then ends the level; the trace (reg_set_trace) records each
+ * step's energy change and whether the Armijo test would have accepted it.
+ * The per-op status is MAXITER.  Host arrays, copied.  n_ops = 0 switches
+ * lockstep off.  Errors: REG_EINVAL for a negative count or a step size that
+ * is not positive and finite; a later batch of another size or level count
+ * fails with REG_EINVAL. */
+reg_status reg_set_lockstep(reg_series_t s, int32_t n_ops, int32_t n_levels, const int32_t *counts,
+                            const double *taus);
 
 /* Energy of one frame pair at one grid level, allocating no memory at all.
  * The paper has no counterpart: this is a service for callers that must not
@@ -354,7 +381,11 @@ reg_status reg_get_trace(reg_series_t s, double *out, int64_t cap, int64_t *n_ou
  * call on each device, so that first call should come before any stream
  * capture.  Every call shares the array and leaves its partial sums in it
  * (each call overwrites all it reads, so no clearing is needed); calls that
- * overlap on the GPU race and must be serialised by the caller.
+ * overlap on the GPU race and must be serialised by the caller.  The call
+ * waits for its stream (cudaStreamSynchronize) before it returns.  The sums
+ * are taken in two passes (FE means, then the moments of the centred images),
+ * so raw frames whose mean is large against their spread keep their
+ * precision.
  * Errors: REG_EINVAL for a null pointer, n < 3, n > REG_NOALLOC_MAX_NODES or
  * pitch < n; REG_ECUDA if a CUDA call fails.  Allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine. */

@@ -99,6 +99,8 @@ def _load():
         "reg_reset_kernel_stats": ([vp], ctypes.c_int),
         "reg_set_trace": ([vp, i64], ctypes.c_int),
         "reg_get_trace": ([vp, vp, i64, P(i64)], ctypes.c_int),
+        "reg_set_lockstep": ([vp, i32, i32, vp, vp], ctypes.c_int),
+        "reg_set_flags": ([vp, i32], ctypes.c_int),
         "reg_eval_energy_noalloc": ([vp, vp, i32, i32, vp, d, vp, i32, vp], ctypes.c_int),
         "reg_destroy_series": ([vp], ctypes.c_int),
         "reg_cnn_num_params": ([], i64),
@@ -334,6 +336,19 @@ def get_trace(h):
     return out[:n.value]
 
 
+def set_lockstep(h, counts, taus):
+    """Lockstep replay for the next batches: counts (n_ops, n_levels) accepted
+    steps per op and level (coarsest first), taus the step sizes in op, level,
+    iteration order.  counts=None switches it off."""
+    if counts is None:
+        _check(_load().reg_set_lockstep(h, 0, 0, None, None))
+        return
+    c = np.ascontiguousarray(counts, np.int32)
+    t = np.ascontiguousarray(taus, np.float64)
+    assert c.ndim == 2 and t.size == int(c.sum())
+    _check(_load().reg_set_lockstep(h, c.shape[0], c.shape[1], c.ctypes.data, t.ctypes.data if t.size else None))
+
+
 def eval_energy_noalloc(R, T, u_grid, lam, stream=None):
     """Energy of one pair at one level through the allocation-free entry point.
     R, T: CUDA float32 tensors (n, n) of the level's raw images; u_grid: CUDA
@@ -342,6 +357,10 @@ def eval_energy_noalloc(R, T, u_grid, lam, stream=None):
     torch = _torch()
     n = int(R.shape[-1])
     assert R.is_cuda and T.is_cuda and u_grid.is_cuda
+    # the kernels read n x n nodes of R and T and 2 x n x n of u: smaller buffers
+    # would be read past their end on the device
+    assert tuple(R.shape) == (n, n) and tuple(T.shape) == (n, n) and tuple(u_grid.shape) == (2, n, n)
+    assert R.dtype == T.dtype == u_grid.dtype == torch.float32
     R, T, u = R.contiguous(), T.contiguous(), u_grid.contiguous()
     parts = np.empty(5)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -504,8 +523,15 @@ class Series:
     def get_trace(self):
         return get_trace(self.h)
 
+    def set_lockstep(self, counts, taus=None):
+        set_lockstep(self.h, counts, taus)
+
     def kernel_stats(self):
         return get_kernel_stats(self.h)
+
+    def set_flags(self, flags):
+        """Replace the handle's flags (FLAG_PROFILE: per-kernel CUDA-event timing)."""
+        _check(_load().reg_set_flags(self.h, int(flags)))
 
     def reset_kernel_stats(self):
         reset_kernel_stats(self.h)

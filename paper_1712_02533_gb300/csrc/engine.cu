@@ -156,6 +156,12 @@ struct reg_series {
     double *d_trace = nullptr;
     unsigned long long *d_trace_len = nullptr;
     long long trace_cap = 0;
+    // lockstep replay (reg_set_lockstep): step sizes for batches of lock_ops ops
+    int lock_ops = 0, lock_levels = 0;
+    std::vector<int> lock_counts;  // lock_ops x lock_levels, coarsest level first
+    std::vector<double> lock_taus;
+    double *d_lock = nullptr;
+    size_t d_lock_cap = 0;
     // totals for reports
     int64_t tot_steps = 0, tot_ops = 0, tot_iters = 0, tot_trials = 0, tot_evals = 0;
 };
@@ -414,6 +420,32 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
             char *base = w + si.ws_off[k];
             L.V[0] = (NodeRec *)base;
             L.V[1] = (NodeRec *)(base + si.rec_bytes(k));
+        }
+    }
+    if (s->lock_ops > 0) {
+        // lockstep replay: every op of the batch takes the given step sizes
+        if (n != s->lock_ops) return fail(REG_EINVAL, "lockstep set for %d ops, batch has %d", s->lock_ops, n);
+        for (int i = 0; i < n; i++)
+            if (s->h_ops[i].nl != s->lock_levels)
+                return fail(REG_EINVAL, "lockstep set for %d levels, op %d has %d", s->lock_levels, i, s->h_ops[i].nl);
+        const size_t nt = std::max<size_t>(1, s->lock_taus.size());
+        if (nt > s->d_lock_cap) {
+            untrack(s, s->d_lock);
+            RET(track(s, (void **)&s->d_lock, nt * sizeof(double)));
+            s->d_lock_cap = nt;
+        }
+        if (!s->lock_taus.empty())
+            CK(cudaMemcpyAsync(s->d_lock, s->lock_taus.data(), s->lock_taus.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, s->stream));
+        int off = 0;
+        for (int i = 0; i < n; i++) {
+            OpDesc &d = s->h_ops[i];
+            d.lock_tau = s->d_lock;
+            for (int k = 0; k < d.nl; k++) {
+                d.lock_off[k] = off;
+                off += s->lock_counts[(size_t)i * s->lock_levels + k];
+            }
+            d.lock_off[d.nl] = off;
         }
     }
     CK(cudaMemcpyAsync(s->d_ops, s->h_ops, sizeof(OpDesc) * n, cudaMemcpyHostToDevice, s->stream));
@@ -1242,12 +1274,16 @@ reg_status reg_get_kernel_stats(reg_series_t s, reg_kernel_stats *buf, int32_t b
     unsigned long long w[16];
     CK(cudaMemcpyAsync(w, s->d_work, sizeof(w), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    *n_out = NFAM + 1;
-    if (buf_len > NFAM) {
-        // nodes of trial passes that took the exact path (largest move leaves the cell)
-        memset(&buf[NFAM], 0, sizeof(reg_kernel_stats));
-        snprintf(buf[NFAM].name, sizeof(buf[NFAM].name), "trial_exact_nodes");
-        buf[NFAM].items = (int64_t)w[KW_TEXACT];
+    // node counters beside the families: trial-pass nodes that took the exact
+    // path (largest move leaves the cell); nodes x sequential Armijo trials (the
+    // trials the one-at-a-time rule would evaluate); level-start energy nodes
+    const struct { const char *name; int k; } extra[3] = {
+        {"trial_exact_nodes", KW_TEXACT}, {"trial_seq_nodes", KW_TSEQ}, {"trial_start_nodes", KW_TSTART}};
+    *n_out = NFAM + 3;
+    for (int j = 0; j < 3 && NFAM + j < buf_len; j++) {
+        memset(&buf[NFAM + j], 0, sizeof(reg_kernel_stats));
+        snprintf(buf[NFAM + j].name, sizeof(buf[NFAM + j].name), "%s", extra[j].name);
+        buf[NFAM + j].items = (int64_t)w[extra[j].k];
     }
     for (int f = 0; f < NFAM && f < buf_len; f++) {
         reg_kernel_stats &k = buf[f];
@@ -1292,6 +1328,43 @@ reg_status reg_set_trace(reg_series_t s, int64_t capacity)
     }
     s->buf_gen++;  // the captured step graph holds the old pointers
     CK(cudaStreamSynchronize(s->stream));
+    return REG_OK;
+}
+
+reg_status reg_set_flags(reg_series_t s, int32_t flags)
+{
+    g_err.clear();
+    if (!s || (flags & ~REG_FLAG_PROFILE)) return fail(REG_EINVAL, "bad handle or unknown flag");
+    s->p.flags = flags;
+    return REG_OK;
+}
+
+reg_status reg_set_lockstep(reg_series_t s, int32_t n_ops, int32_t n_levels, const int32_t *counts,
+                            const double *taus)
+{
+    g_err.clear();
+    if (!s || n_ops < 0) return fail(REG_EINVAL, "bad argument");
+    if (n_ops == 0) {
+        s->lock_ops = 0;
+        s->lock_levels = 0;
+        s->lock_counts.clear();
+        s->lock_taus.clear();
+        return REG_OK;
+    }
+    if (n_levels < 1 || n_levels > REG_MAX_LEVELS || !counts) return fail(REG_EINVAL, "bad level count or counts");
+    int64_t total = 0;
+    for (int64_t i = 0; i < (int64_t)n_ops * n_levels; i++) {
+        if (counts[i] < 0 || counts[i] > 100000) return fail(REG_EINVAL, "step count %d out of range", counts[i]);
+        total += counts[i];
+    }
+    if (total > (1ll << 30)) return fail(REG_EINVAL, "too many step sizes");
+    if (total > 0 && !taus) return fail(REG_EINVAL, "null step sizes");
+    for (int64_t i = 0; i < total; i++)
+        if (!(taus[i] > 0.0) || !std::isfinite(taus[i])) return fail(REG_EINVAL, "step size %lld is not positive", (long long)i);
+    s->lock_ops = n_ops;
+    s->lock_levels = n_levels;
+    s->lock_counts.assign(counts, counts + (size_t)n_ops * n_levels);
+    s->lock_taus.assign(taus, taus + total);
     return REG_OK;
 }
 

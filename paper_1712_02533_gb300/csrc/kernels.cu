@@ -1333,8 +1333,26 @@ __device__ void level_end(OpState &s, const OpDesc &op, int status, double pendi
     }
 }
 
-__device__ void set_init_trials(OpState &s, const BatchDev &b)
+// Lockstep replay: the step size the given search of iteration s.iter takes.
+__device__ __forceinline__ double lock_step(const OpState &s, const OpDesc &op)
 {
+    return op.lock_tau[op.lock_off[s.lvl] + s.iter];
+}
+
+__device__ __forceinline__ int lock_count(const OpState &s, const OpDesc &op)
+{
+    return op.lock_off[s.lvl + 1] - op.lock_off[s.lvl];
+}
+
+__device__ void set_init_trials(OpState &s, const BatchDev &b, const OpDesc &op)
+{
+    if (op.lock_tau) {
+        // replay: the one step size the reference sequence accepted here
+        s.trial_tau[0] = lock_step(s, op);
+        s.ntr = 1;
+        s.search = SEARCH_INIT;
+        return;
+    }
     // sequential Armijo order: tau, then 2 tau (if accepted), else tau/2; the
     // pass covers the most likely continuations of both branches.
     int J = b.J;
@@ -1350,13 +1368,13 @@ __device__ void set_init_trials(OpState &s, const BatchDev &b)
     s.search = SEARCH_INIT;
 }
 
-__device__ void schedule_grad(OpState &s, const BatchDev &b, double pending)
+__device__ void schedule_grad(OpState &s, const BatchDev &b, const OpDesc &op, double pending)
 {
     s.phase = PH_GRAD;
     s.tau_acc = pending;
     s.src = s.cur;
     s.cur = 1 - s.cur;
-    set_init_trials(s, b);
+    set_init_trials(s, b, op);
 }
 
 }  // namespace
@@ -1464,7 +1482,8 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
         s.tau = b.tau_init;
         s.evals += 1;
         if (!isfinite(s.E)) level_end(s, op, OPST_NONFINITE, 0.0);
-        else schedule_grad(s, b, 0.0);
+        else if (op.lock_tau && lock_count(s, op) == 0) level_end(s, op, OPST_MAXITER, 0.0);
+        else schedule_grad(s, b, op, 0.0);
         return;
     }
     if (ph == PH_GRAD) {
@@ -1477,6 +1496,35 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
         }
     }
     s.evals += s.ntr;
+    if (op.lock_tau) {
+        // lockstep replay: take the given step whatever the test says (the
+        // trace records the test), end the level after the last given step
+        const double want = s.trial_tau[0];
+        double S1 = s.S1 + h2 * S[0], S2 = s.S2 + h2 * S[1], S3 = s.S3 + h2 * S[2];
+        double nc = ncc_of(S1, S2, S3);
+        double dE = -(nc - s.ncc) + 0.5 * b.lambda * h2 * (2.0 * want * Qud + want * want * Qdd);
+        s.trials_seq += 1;
+        atomicAdd(&b.work[KW_TSEQ], (unsigned long long)Lv.n * Lv.n);
+        bool acc = (dE <= b.sigma * want * s.slope);
+        if (b.trace) {
+            unsigned long long k = atomicAdd(b.trace_len, 1ull);
+            if ((long long)k < b.trace_cap) {
+                double *rec = b.trace + 7 * k;
+                rec[0] = o; rec[1] = Lv.n; rec[2] = s.iter - 1; rec[3] = want;
+                rec[4] = dE; rec[5] = b.sigma * want * s.slope; rec[6] = acc;
+            }
+        }
+        s.E += dE;
+        s.S1 = S1; s.S2 = S2; s.S3 = S3;
+        s.Tbar = S1;
+        double var = S2 - S1 * S1;
+        s.sigT = var > 0.0 ? sqrt(var) : 0.0;
+        s.ncc = nc;
+        s.tau = want;
+        if (s.iter >= lock_count(s, op)) level_end(s, op, OPST_MAXITER, want);
+        else schedule_grad(s, b, op, want);
+        return;
+    }
     // Walk the sequential Armijo search over the step sizes evaluated this pass.
     for (int guard = 0; guard < 4 * REG_MAX_TRIALS + 8; guard++) {
         double want;
@@ -1508,6 +1556,7 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
             double nc = ncc_of(S1, S2, S3);
             double dE = -(nc - s.ncc) + 0.5 * b.lambda * h2 * (2.0 * want * Qud + want * want * Qdd);
             s.trials_seq += 1;
+            atomicAdd(&b.work[KW_TSEQ], (unsigned long long)Lv.n * Lv.n);
             bool acc = (dE <= b.sigma * want * s.slope);
             if (b.trace) {
                 unsigned long long k = atomicAdd(b.trace_len, 1ull);
@@ -1547,7 +1596,7 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
             s.tau = s.btau;
             if (dec < b.eps * scale) level_end(s, op, OPST_CONVERGED, s.btau);
             else if (s.iter >= b.iter_max) level_end(s, op, OPST_MAXITER, s.btau);
-            else schedule_grad(s, b, s.btau);
+            else schedule_grad(s, b, op, s.btau);
             return;
         }
     }

@@ -48,7 +48,8 @@ enum { KW_G = 0,         // gradient pass nodes
        KW_PPROL = 4,     // prolongation: fine nodes written
        KW_PFIN = 5,      // final write: nodes
        KW_TEXACT = 6,    // trial nodes whose largest move leaves the cell (exact path)
-       KW_COUNT = 7 };
+       KW_TSEQ = 7,      // nodes x sequential Armijo trials decided (the one-at-a-time rule's trials)
+       KW_COUNT = 8 };
 
 // State of one operator at one node of a level, read and written as two
 // 16-byte words: the displacement in grid units of the level as a float pair
@@ -82,6 +83,12 @@ struct OpDesc {
     float2 *out;            // destination slot (finest level)
     int slot_pitch;
     int judge;              // the output slot holds a learned start: measure the correction
+    // Lockstep replay (diagnostic; null: free-running search).  Level k
+    // (0 = coarsest) takes exactly the accepted step sizes
+    // lock_tau[lock_off[k] .. lock_off[k+1]), one per gradient iteration, and
+    // ends after the last of them.
+    const double *lock_tau;
+    int lock_off[REG_MAX_LEVELS + 1];
     LevelDesc lv[REG_MAX_LEVELS];  // index 0 = coarsest level m0
 };
 

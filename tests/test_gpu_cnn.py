@@ -126,7 +126,8 @@ def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
     import synth
     from oracle import cnn as ocnn
     from paper_1712_02533_gb300 import learned
-    from test_gpu_parity import _assert_op_parity, _gpu_traces_by_op
+    import _parity as P
+    from test_gpu_parity import _gpu_traces_by_op
     fr = syn.series(31, 2, 256, **learned.TRAIN_SERIES)
     theta = synth.cnn_params(7)
     y = ocnn.forward(theta.astype(np.float64), _oracle_inputs(orc, fr),
@@ -147,10 +148,12 @@ def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
     if tensor_cores:
         return  # the start differs by the BF16 rounding flips; the FP32 case pins the operator
     g0, g1 = orc.embed(fr[0]), orc.embed(fr[1])
+    op = orc.params(n_levels=2, iter_max=50, lam=10.0)
     with orc.trace() as t:
-        u, _, stl = orc.register(g0, g1, orc.params(n_levels=2, iter_max=50, lam=10.0), u_init=u0 / 256)
+        u, _, stl = orc.register(g0, g1, op, u_init=u0 / 256)
     assert len(stl) == 2
-    _assert_op_parity(d, u * 256, gtr, t.rows, "A(0,1) from the learned start", g0, g1)
+    P.report("learned", P.free_running_parity(orc, d, u * 256, gtr, t.rows, "A(0,1) from the learned start", g0, g1,
+                                               op, 10.0, u_init_omega=u0 / 256))
 
 
 def test_plain_method_judges_the_learned_start_and_falls_back(reg, syn):

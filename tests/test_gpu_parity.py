@@ -7,10 +7,12 @@ registered displacements to 1e-3 px with final energies to 1e-5 relative.
 import numpy as np
 import pytest
 
+import _parity as P
+
 pytestmark = pytest.mark.gpu
 
-TOL_PX = 1e-3
-TOL_E = 1e-5
+TOL_PX = P.TOL_PX
+TOL_E = P.TOL_E
 
 
 def orc_energy(R, T, u, lam):
@@ -140,148 +142,185 @@ def test_function_a_matches_oracle(reg, orc, syn):
     assert abs(eg["E"] - stl[-1].E) <= TOL_E * abs(stl[-1].E)
 
 
-def _assert_op_parity(gpu_u_px, orc_u_px, gtr, otr, what, R, T, lam=10.0):
-    """Parity of one full operator application.  Either the displacement fields
-    agree to TOL_PX everywhere, or the two Armijo decision sequences agree up to
-    a decision that the oracle itself takes with a margin below 1e-3 (relative):
-    from such a decision on, rounding at the 1e-7 level legitimately sends the
-    iteration elsewhere (the same happens to the oracle under 1e-7 input
-    perturbations, see test_oracle_sensitivity.py).  When every decision
-    agrees, the fields may still differ at the few nodes that the iteration
-    drives onto a cell line of the bilinear interpolant: the template's
-    derivative jumps there, so which side such a node ends on is decided at the
-    rounding level (in FP32 on the GPU, FP64 in the oracle).  Those nodes must
-    stay rare (99.5% of the nodes within TOL_PX), and the GPU's field must be no
-    worse a minimiser: the oracle's FP64 energy at it may exceed the energy at
-    the oracle's own field by at most 1e-6 (relative)."""
-    err = float(np.abs(gpu_u_px - orc_u_px).max())
-    if err <= TOL_PX:
-        return err
-    m = min(len(gtr), len(otr))
-    for k in range(m):
-        a, b = gtr[k], otr[k]
-        assert a[0] == b[0] and a[1] == b[1] and a[2] == b[2], (what, "trial sequence differs before any decision", k)
-        if a[5] != b[5]:
-            # the oracle's own margin must lie within the disagreement of the two
-            # energy changes at that point (plus 1e-3): the flip is explained by
-            # the states having separated, not by a different decision rule
-            margin = abs(b[3] - b[4]) / abs(b[4])
-            spread = (abs(a[3] - b[3]) + abs(a[4] - b[4])) / abs(b[4])
-            assert margin < spread + 1e-3, (what, "decision differs at a non-marginal test", k, a, b, err)
-            return err
-    side = gpu_u_px.shape[-1] - 1
-    frac = float(np.mean(np.abs(gpu_u_px - orc_u_px) <= TOL_PX))
-    e_gpu, _ = orc_energy(R, T, gpu_u_px.astype(np.float64) / side, lam)
-    e_orc, _ = orc_energy(R, T, np.asarray(orc_u_px, np.float64) / side, lam)
-    assert frac >= 0.995 and e_gpu - e_orc <= 1e-6 * abs(e_orc), (
-        what, "fields differ although every decision agrees", err, frac, e_gpu, e_orc)
-    return err
-
-
 def _gpu_traces_by_op(tr, n_ops):
     return [tr[tr[:, 0] == o][:, 1:] for o in range(n_ops)]
 
 
+def _orc_traced(orc, R, T, p, u_init=None):
+    """One oracle operator with its Armijo trace (safe to run on several host
+    threads at once: each thread records its own trace)."""
+    with orc.trace() as t:
+        u, status, stl = orc.register(R, T, p, u_init=u_init)
+    return u, status, stl, t.rows
+
+
+def _orc_many(orc, jobs, p):
+    """Oracle operators (R, T, u_init) solved in parallel host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(16, max(1, len(jobs)))) as ex:
+        return list(ex.map(lambda j: _orc_traced(orc, j[0], j[1], p, j[2]), jobs))
+
+
+def _f32_px(u_omega, side):
+    """An oracle field (Omega units) rounded to the float32 pixels a slot holds."""
+    return (np.asarray(u_omega) * side).astype(np.float32)
+
+
 def test_config1_operators_match_oracle(reg, orc, syn):
     """Config-1 series (8 x 64^2, Poisson noise): every preprocessing operator
-    (function A) matches the oracle field by field or decision by decision."""
+    (function A) against the oracle, free running and in lockstep."""
     cfg = dict(syn.CONFIGS["c1_8x64"])
     nl = cfg.pop("n_levels")
     fr = syn.series(**cfg)
     g = [orc.embed(f) for f in fr]
-    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=lam)
+    op = orc.params(n_levels=nl, iter_max=50, lam=lam)
     n = len(fr) - 1
+    res = _orc_many(orc, [(g[e], g[e + 1], None) for e in range(n)], op)
     with reg.Series(fr, p) as s:
         s.set_trace(1 << 20)
         st, it = s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(n)])
         gtr = _gpu_traces_by_op(s.get_trace(), n)
         got = [s.get_slot(e)[0] for e in range(n)]
-    n_exact = 0
-    for e in range(n):
-        with orc.trace() as t:
-            u, status, stl = orc.register(g[e], g[e + 1], op)
-        err = _assert_op_parity(got[e], u * 64, gtr[e], t.rows, f"A({e},{e + 1})", g[e], g[e + 1])
-        n_exact += err <= TOL_PX
+        n_exact = 0
+        for e in range(n):
+            u, status, stl, rows = res[e]
+            rec = P.free_running_parity(orc, got[e], u * 64, gtr[e], rows, f"c1 A({e},{e + 1})", g[e], g[e + 1], op, lam)
+            P.report("c1", rec)
+            n_exact += rec["criterion"] == "fields"
+            P.report("c1", P.lockstep_parity(orc, s, (0, -1, -1, e, e, e + 1), e, nl, rows, u * 64,
+                                             f"c1 A({e},{e + 1})", g[e], g[e + 1], lam))
     assert n_exact >= n - 1
 
 
 def test_config1_scan_operators_match_oracle(reg, orc, syn):
-    """Function B along the serial scan of config 1, each given the operands the
-    GPU produced (so that both sides start from the same fields)."""
+    """Function B along the serial scan of config 1.  The operands are the
+    oracle's own results (rounded to the float32 pixels a slot holds) and are
+    given to both sides, so that both start from the same fields."""
     cfg = dict(syn.CONFIGS["c1_8x64"])
     nl = cfg.pop("n_levels")
     fr = syn.series(**cfg)
     g = [orc.embed(f) for f in fr]
-    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=lam)
+    op = orc.params(n_levels=nl, iter_max=50, lam=lam)
+    A = [_f32_px(r[0], 64) for r in _orc_many(orc, [(g[e], g[e + 1], None) for e in range(7)], op)]
+    acc = A[0]
     with reg.Series(fr, p) as s:
-        s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(7)])
-        A = [s.get_slot(e)[0].astype(np.float64) / 64 for e in range(7)]
-        acc = A[0]
         for k in range(1, 7):
+            left, right = acc.astype(np.float64) / 64, A[k].astype(np.float64) / 64
+            s.set_slot(0, acc, 0, k)
+            s.set_slot(1, A[k], k, k + 1)
             s.set_trace(1 << 20)
-            s.apply_operator_batch([(0, k - 1, k, k, 0, k + 1)])
-            got = s.get_slot(k)[0]
+            s.apply_operator_batch([(0, 0, 1, 2, 0, k + 1)])
+            got = s.get_slot(2)[0]
             gtr = s.get_trace()[:, 1:]
-            with orc.trace() as t:
-                out, _, _, _, _ = orc.apply_batch([dict(R=g[0], T=g[k + 1], left=acc, right=A[k])], op)
-            _assert_op_parity(got, out[0] * 64, gtr, t.rows, f"B(0,{k},{k + 1})", g[0], g[k + 1])
-            acc = got.astype(np.float64) / 64
+            u, _, _, rows = _orc_traced(orc, g[0], g[k + 1], op, orc.compose(left, right))
+            what = f"c1 B(0,{k},{k + 1})"
+            P.report("c1", P.free_running_parity(orc, got, u * 64, gtr, rows, what, g[0], g[k + 1], op, lam,
+                                                  u_init_omega=orc.compose(left, right)))
+            s.set_slot(0, acc, 0, k)
+            s.set_slot(1, A[k], k, k + 1)
+            P.report("c1", P.lockstep_parity(orc, s, (0, 0, 1, 2, 0, k + 1), 2, nl, rows, u * 64, what,
+                                             g[0], g[k + 1], lam))
+            acc = _f32_px(u, 64)
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 7, 8])
-def test_series_stable_input_matches_oracle(reg, orc, syn, kind):
-    """Whole-series registration, every schedule, on the config-1 series
-    without shot noise (expected counts), where the oracle's result is stable
-    under 1e-7 input perturbations (test_oracle_sensitivity.py): the GPU
-    deformations phi_{0,k} must match to TOL_PX at every node."""
+@pytest.mark.parametrize("kind,chunks,global_kind", [(0, 1, 2), (1, 1, 2), (2, 1, 2), (3, 1, 2), (4, 1, 2),
+                                                     (5, 3, 2), (5, 2, 4), (6, 3, 2), (6, 2, 4), (7, 1, 2),
+                                                     (8, 1, 2)])
+def test_series_stable_input_matches_oracle(reg, orc, syn, kind, chunks, global_kind):
+    """Whole-series registration, every schedule -- the chunked general
+    strategy and its alternative with Kogge-Stone and Blelloch global scans
+    included -- on the config-1 series without shot noise (expected counts),
+    where the oracle's result is stable under 1e-7 input perturbations
+    (test_oracle_sensitivity.py): the GPU deformations phi_{0,k} must match to
+    TOL_PX at every node."""
     cfg = dict(syn.CONFIGS["c1_8x64"])
     nl = cfg.pop("n_levels")
     fr = syn.series(noise=False, **cfg)
     p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    hc_k = 1  # k of Han-Carlson and Ladner-Fischer (unused by the other kinds here)
     with reg.Series(fr, p) as s:
-        rep = s.prefix_scan(kind, chunks=hc_k)
+        rep = s.prefix_scan(kind, chunks=chunks, global_kind=global_kind)
         got = s.get_deformations()
     op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
-    want, info = orc.register_series([fr], op, kind=kind, chunks=hc_k, return_info=True)
+    want, info = orc.register_series([fr], op, kind=kind, chunks=chunks, global_kind=global_kind, return_info=True)
     want = want[0][:, :, :64, :64]
     assert rep["ops"] == info["ops"]
     err = np.abs(got - want)
+    P.report("c1-series", dict(kind=kind, chunks=chunks, global_kind=global_kind, max_px=float(err.max()),
+                               mean_px=float(err.mean()), ops=rep["ops"]))
     assert err.max() <= TOL_PX, (err.max(), [float(err[k].max()) for k in range(len(err))])
 
 
+@pytest.mark.slow
+def test_config2_stable_series_matches_oracle(reg, orc, syn):
+    """A config-2-shaped series without shot noise (128 x 512^2, 4 levels),
+    registered as a whole by the Sklansky (= Ladner-Fischer) tree on both
+    sides: phi_{0,k} within TOL_PX at every node of every frame.  The oracle's
+    result for this input moves by less than 1e-5 px under 1e-7 relative
+    perturbations of the frames (measured), so any larger difference is the
+    GPU's."""
+    cfg = dict(syn.CONFIGS["c2_128x512"])
+    nl = cfg.pop("n_levels")
+    fr = syn.series(noise=False, **cfg)
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
+    with reg.Series(fr, p) as s:
+        rep = s.prefix_scan(reg.SKLANSKY)
+        got = s.get_deformations()
+    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    want, info = orc.register_series([fr], op, kind=reg.SKLANSKY, return_info=True)
+    want = want[0][:, :, :512, :512]
+    assert rep["ops"] == info["ops"]
+    err = np.abs(got - want)
+    P.report("c2-series", dict(max_px=float(err.max()), p99_px=float(np.quantile(err, 0.99)),
+                               mean_px=float(err.mean()), ops=rep["ops"]))
+    assert err.max() <= TOL_PX, (float(err.max()), [float(err[k].max()) for k in range(0, len(err), 8)])
+
+
 def test_config2_sampled_operators_match_oracle(reg, orc, syn):
-    """Config-2 sizes (512^2, 4 levels): sampled A and B operators of the
-    128-frame series, against the oracle computed one by one."""
+    """Config-2 sizes (512^2, 4 levels): sampled A operators of the 128-frame
+    series in the batch of all 127, and a B operator on the oracle's own
+    operands, free running and in lockstep; max |du| and the final-energy
+    difference of each are printed."""
     cfg = dict(syn.CONFIGS["c2_128x512"])
     nl = cfg.pop("n_levels")
     fr = syn.series(**cfg)
-    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=lam)
+    op = orc.params(n_levels=nl, iter_max=50, lam=lam)
     side = 512
+    g = {e: orc.embed(fr[e]) for e in (0, 1, 2, 77, 78)}
+    res = dict(zip((0, 77, 1), _orc_many(orc, [(g[0], g[1], None), (g[77], g[78], None), (g[1], g[2], None)], op)))
     with reg.Series(fr, p) as s:
         s.set_trace(1 << 22)
         n = len(fr) - 1
         s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(n)])
         gtr = _gpu_traces_by_op(s.get_trace(), n)
+        got = {e: s.get_slot(e)[0] for e in (0, 77)}
         for e in (0, 77):
-            got = s.get_slot(e)[0]
-            R, T = orc.embed(fr[e]), orc.embed(fr[e + 1])
-            with orc.trace() as t:
-                u, _, _ = orc.register(R, T, op)
-            _assert_op_parity(got, u * side, gtr[e], t.rows, f"A({e},{e + 1}) 512^2", R, T)
-        left = s.get_slot(0)[0].astype(np.float64) / side
-        right = s.get_slot(1)[0].astype(np.float64) / side
+            u, _, _, rows = res[e]
+            what = f"c2 A({e},{e + 1})"
+            P.report("c2", P.free_running_parity(orc, got[e], u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam))
+            P.report("c2", P.lockstep_parity(orc, s, (0, -1, -1, 5, e, e + 1), 5, nl, rows, u * side, what,
+                                             g[e], g[e + 1], lam))
+        # B(0,1,2) on the oracle's A(0,1) and A(1,2), rounded to float32 pixels
+        a01, a12 = _f32_px(res[0][0], side), _f32_px(res[1][0], side)
+        left, right = a01.astype(np.float64) / side, a12.astype(np.float64) / side
+        u, _, _, rows = _orc_traced(orc, g[0], g[2], op, orc.compose(left, right))
+        s.set_slot(0, a01, 0, 1)
+        s.set_slot(1, a12, 1, 2)
         s.set_trace(1 << 22)
-        s.apply_operator_batch([(0, 0, 1, 1, 0, 2)])
-        got = s.get_slot(1)[0]
+        s.apply_operator_batch([(0, 0, 1, 2, 0, 2)])
+        gotb = s.get_slot(2)[0]
         gtr2 = s.get_trace()[:, 1:]
-    # B given the GPU's operands on both sides
-    with orc.trace() as t:
-        out, _, _, _, _ = orc.apply_batch([dict(R=orc.embed(fr[0]), T=orc.embed(fr[2]), left=left, right=right)], op)
-    _assert_op_parity(got, out[0] * side, gtr2, t.rows, "B(0,1,2) 512^2", orc.embed(fr[0]), orc.embed(fr[2]))
+        P.report("c2", P.free_running_parity(orc, gotb, u * side, gtr2, rows, "c2 B(0,1,2)", g[0], g[2], op, lam,
+                                              u_init_omega=orc.compose(left, right)))
+        s.set_slot(0, a01, 0, 1)
+        s.set_slot(1, a12, 1, 2)
+        P.report("c2", P.lockstep_parity(orc, s, (0, 0, 1, 2, 0, 2), 2, nl, rows, u * side, "c2 B(0,1,2)",
+                                         g[0], g[2], lam))
 
 
 def test_identical_frames_give_zero_displacement(reg, syn):
@@ -310,23 +349,43 @@ def test_invalid_arguments_are_rejected(reg, syn):
 
 def test_full_size_sampled_operators_match_oracle(reg, orc, syn):
     """The 400 x 1024^2 workload (5 levels) in the launch configuration the
-    benchmark times (all 399 neighbour pairs in one batch): sampled operators
-    against the oracle computed one by one, under the same criterion as the
-    smaller configurations."""
+    benchmark times (all 399 neighbour pairs in one batch): sampled A operators
+    and one B operator on the oracle's own operands, against the oracle computed
+    one by one, free running and in lockstep, with max |du| and the
+    final-energy difference of each printed."""
     cfg = dict(syn.CONFIGS["c3_400x1024"])
     nl = cfg.pop("n_levels")
     fr = syn.series(**cfg)
-    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
-    op = orc.params(n_levels=nl, iter_max=50, lam=10.0)
+    lam = 10.0
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=lam)
+    op = orc.params(n_levels=nl, iter_max=50, lam=lam)
     side = 1024
     n = len(fr) - 1
+    g = {e: orc.embed(fr[e]) for e in (0, 1, 2, 250, 251)}
+    res = dict(zip((0, 250, 1), _orc_many(orc, [(g[0], g[1], None), (g[250], g[251], None), (g[1], g[2], None)], op)))
     with reg.Series(fr, p) as s:
         s.set_trace(1 << 23)
         s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(n)])
         gtr = _gpu_traces_by_op(s.get_trace(), n)
         got = {e: s.get_slot(e)[0] for e in (0, 250)}
-    for e, u_gpu in got.items():
-        R, T = orc.embed(fr[e]), orc.embed(fr[e + 1])
-        with orc.trace() as t:
-            u, _, _ = orc.register(R, T, op)
-        _assert_op_parity(u_gpu, u * side, gtr[e], t.rows, f"A({e},{e + 1}) 1024^2", R, T)
+        for e, u_gpu in got.items():
+            u, _, _, rows = res[e]
+            what = f"c3 A({e},{e + 1})"
+            P.report("c3", P.free_running_parity(orc, u_gpu, u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam))
+            P.report("c3", P.lockstep_parity(orc, s, (0, -1, -1, 5, e, e + 1), 5, nl, rows, u * side, what,
+                                             g[e], g[e + 1], lam))
+        a01, a12 = _f32_px(res[0][0], side), _f32_px(res[1][0], side)
+        left, right = a01.astype(np.float64) / side, a12.astype(np.float64) / side
+        u, _, _, rows = _orc_traced(orc, g[0], g[2], op, orc.compose(left, right))
+        s.set_slot(0, a01, 0, 1)
+        s.set_slot(1, a12, 1, 2)
+        s.set_trace(1 << 22)
+        s.apply_operator_batch([(0, 0, 1, 2, 0, 2)])
+        gotb = s.get_slot(2)[0]
+        gtr2 = s.get_trace()[:, 1:]
+        P.report("c3", P.free_running_parity(orc, gotb, u * side, gtr2, rows, "c3 B(0,1,2)", g[0], g[2], op, lam,
+                                              u_init_omega=orc.compose(left, right)))
+        s.set_slot(0, a01, 0, 1)
+        s.set_slot(1, a12, 1, 2)
+        P.report("c3", P.lockstep_parity(orc, s, (0, 0, 1, 2, 0, 2), 2, nl, rows, u * side, "c3 B(0,1,2)",
+                                         g[0], g[2], lam))
