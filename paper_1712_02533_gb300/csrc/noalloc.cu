@@ -14,14 +14,15 @@
 namespace {
 
 constexpr int NA_TX = 32, NA_TY = 32, NA_THREADS = 256;
-constexpr int NA_SUMS = 6;  // int R, int R^2, int That, int That^2, int R That, Dirichlet form
+constexpr int NA_SUMS = 6;  // per tile: int R, int That (pass 1); int Rc^2, int Tc^2, int Rc Tc, Dirichlet form (pass 2)
 constexpr int NA_MAX_NODES = REG_NOALLOC_MAX_NODES;
 constexpr int NA_MAX_TILES = ((NA_MAX_NODES - 1 + NA_TX - 1) / NA_TX) * ((NA_MAX_NODES - 1 + NA_TY - 1) / NA_TY);
+constexpr int NA_OUT = NA_MAX_TILES * NA_SUMS;  // results: {E, NCC, reg, T_bar, sigma_T}, then R_bar
 
-// Per-tile partial sums of the last call, then the five results.  Every call
+// Per-tile partial sums of the last call, then the results.  Every call
 // overwrites the partials of all its tiles before reading them, so nothing has
 // to start at zero; calls that overlap on the GPU race on this array.
-static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_TILES * NA_SUMS + 8];
+static __device__ __align__(256) double g_noalloc_scratch[NA_OUT + 8];
 
 __device__ __forceinline__ float bilinear_clamped(const float *T, int n, int pitch, int c, int r, float vx, float vy)
 {
@@ -40,17 +41,22 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// One block per 32 x 32 tile of cells: the FE integrals (Q1 element mass form)
-// of R, R^2, That, That^2, R That and the Dirichlet form of u, per tile, in
-// double.  The same cell formulas as the batched energy pass, on raw images.
+// One block per 32 x 32 tile of cells: FE integrals (Q1 element mass form) per
+// tile, in double.  Pass 1 (centre == nullptr): int R and int That, for the
+// means.  Pass 2: the second moments of the centred images R - R_bar and
+// That - T_bar (centring first keeps the FP32 cell sums relative to the
+// images' spread, not to their mean) and the Dirichlet form of u.
 __global__ void __launch_bounds__(NA_THREADS) k_energy_tiles_noalloc(const float *R, const float *T, int n, int pitch,
-                                                                     const float *u, double *scratch)
+                                                                     const float *u, const double *centre,
+                                                                     double *scratch)
 {
     const int tx = (n - 1 + NA_TX - 1) / NA_TX;
     const int c = (blockIdx.x % tx) * NA_TX + threadIdx.x % NA_TX;
     const int r0 = (blockIdx.x / tx) * NA_TY, ly = threadIdx.x / NA_TX;
     const size_t N = (size_t)n * n;
-    float acc[NA_SUMS] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool second = centre != nullptr;
+    const float Rb = second ? (float)centre[5] : 0.f, Tb = second ? (float)centre[3] : 0.f;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int lr = ly; lr < NA_TY; lr += NA_THREADS / NA_TX) {
         const int r = r0 + lr;
         if (r >= n - 1 || c >= n - 1) continue;
@@ -61,8 +67,13 @@ __global__ void __launch_bounds__(NA_THREADS) k_energy_tiles_noalloc(const float
             size_t i = (size_t)cr[k] * n + cc[k];
             ux[k] = u[i];
             uy[k] = u[N + i];
-            Rv[k] = R[(size_t)cr[k] * pitch + cc[k]];
-            Tv[k] = bilinear_clamped(T, n, pitch, cc[k], cr[k], ux[k], uy[k]);
+            Rv[k] = R[(size_t)cr[k] * pitch + cc[k]] - Rb;
+            Tv[k] = bilinear_clamped(T, n, pitch, cc[k], cr[k], ux[k], uy[k]) - Tb;
+        }
+        if (!second) {
+            acc[0] += 0.25f * (Rv[0] + Rv[1] + Rv[2] + Rv[3]);
+            acc[1] += 0.25f * (Tv[0] + Tv[1] + Tv[2] + Tv[3]);
+            continue;
         }
         // element mass matrix (1/36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4]
         auto mform = [](const float *v, const float *w) {
@@ -72,61 +83,68 @@ __global__ void __launch_bounds__(NA_THREADS) k_energy_tiles_noalloc(const float
             float Mw3 = 2.f * w[0] + w[1] + 2.f * w[2] + 4.f * w[3];
             return (v[0] * Mw0 + v[1] * Mw1 + v[2] * Mw2 + v[3] * Mw3) * (1.f / 36.f);
         };
-        acc[0] += 0.25f * (Rv[0] + Rv[1] + Rv[2] + Rv[3]);
-        acc[1] += mform(Rv, Rv);
-        acc[2] += 0.25f * (Tv[0] + Tv[1] + Tv[2] + Tv[3]);
-        acc[3] += mform(Tv, Tv);
-        acc[4] += mform(Rv, Tv);
+        acc[0] += mform(Rv, Rv);
+        acc[1] += mform(Tv, Tv);
+        acc[2] += mform(Rv, Tv);
         // Dirichlet form (p^2 + pq + q^2 + r^2 + rs + s^2) / 3 per component
         for (int ch = 0; ch < 2; ch++) {
             const float *v = ch ? uy : ux;
             float p = v[1] - v[0], q = v[2] - v[3], rr = v[3] - v[0], s = v[2] - v[1];
-            acc[5] += (p * p + p * q + q * q + rr * rr + rr * s + s * s) * (1.f / 3.f);
+            acc[3] += (p * p + p * q + q * q + rr * rr + rr * s + s * s) * (1.f / 3.f);
         }
     }
-    __shared__ float red[NA_THREADS / 32][NA_SUMS];
-    for (int k = 0; k < NA_SUMS; k++) {
+    __shared__ float red[NA_THREADS / 32][4];
+    for (int k = 0; k < 4; k++) {
         float v = warp_sum(acc[k]);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < NA_SUMS) {
+    if (threadIdx.x < 4) {
         double t = 0.0;
         for (int w = 0; w < NA_THREADS / 32; w++) t += red[w][threadIdx.x];
-        scratch[(size_t)blockIdx.x * NA_SUMS + threadIdx.x] = t;
+        scratch[(size_t)blockIdx.x * NA_SUMS + (second ? 2 : 0) + threadIdx.x] = t;
     }
 }
 
-// One block: sums the tiles' partials in a fixed order and forms
-// E = -NCC + lambda/2 h^2 sum |grad u|^2 with NCC from the FE means and
-// standard deviations of R and That (Section "Spatial discretization").
-__global__ void k_energy_finish_noalloc(int n_tiles, int n, double lambda, double *scratch)
+// One block: sums the tiles' partials in a fixed order.  Pass 1 forms the FE
+// means R_bar = h^2 int R, T_bar = h^2 int That; pass 2 forms
+// sigma^2 = h^2 int (F - F_bar)^2 (FE form), NCC = h^2 int Rc Tc / (sigma_R
+// sigma_T) and E = -NCC + lambda/2 h^2 sum |grad u|^2 (Section "Spatial
+// discretization").
+__global__ void k_energy_finish_noalloc(int n_tiles, int n, double lambda, int second, double *scratch)
 {
-    __shared__ double red[32][NA_SUMS];
-    double s[NA_SUMS] = {0, 0, 0, 0, 0, 0};
+    __shared__ double red[32][4];
+    const int base = second ? 2 : 0, cnt = second ? 4 : 2;
+    double s[4] = {0, 0, 0, 0};
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
-        for (int k = 0; k < NA_SUMS; k++) s[k] += scratch[(size_t)t * NA_SUMS + k];
-    for (int k = 0; k < NA_SUMS; k++) {
+        for (int k = 0; k < cnt; k++) s[k] += scratch[(size_t)t * NA_SUMS + base + k];
+    for (int k = 0; k < cnt; k++) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double S[NA_SUMS] = {0, 0, 0, 0, 0, 0};
+        double S[4] = {0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x / 32); w++)
-            for (int k = 0; k < NA_SUMS; k++) S[k] += red[w][k];
+            for (int k = 0; k < cnt; k++) S[k] += red[w][k];
         double h2 = 1.0 / ((double)(n - 1) * (n - 1));
-        double Rb = h2 * S[0], Tb = h2 * S[2];
-        double vR = h2 * S[1] - Rb * Rb, vT = h2 * S[3] - Tb * Tb;
+        double *out = scratch + NA_OUT;
+        if (!second) {
+            out[5] = h2 * S[0];  // R_bar
+            out[3] = h2 * S[1];  // T_bar
+            return;
+        }
+        // the images were centred on the means rounded to float, c = F_bar + dF:
+        // (F - c)^T M (G - c') = (F - F_bar)^T M (G - G_bar) + dF dG  (w^T 1 = 1)
+        const double dR = (double)(float)out[5] - out[5], dT = (double)(float)out[3] - out[3];
+        double vR = h2 * S[0] - dR * dR, vT = h2 * S[1] - dT * dT;
         double sR = vR > 0.0 ? sqrt(vR) : 0.0, sT = vT > 0.0 ? sqrt(vT) : 0.0;
-        double ncc = (h2 * S[4] - Rb * Tb) / (sR * sT);
-        double reg = 0.5 * lambda * h2 * S[5];
-        double *out = scratch + (size_t)NA_MAX_TILES * NA_SUMS;
+        double ncc = (h2 * S[2] - dR * dT) / (sR * sT);
+        double reg = 0.5 * lambda * h2 * S[3];
         out[0] = -ncc + reg;
         out[1] = ncc;
         out[2] = reg;
-        out[3] = Tb;
         out[4] = sT;
     }
 }
@@ -160,11 +178,14 @@ extern "C" reg_status reg_eval_energy_noalloc(const float *R, const float *T, in
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int tiles = ((n - 1 + NA_TX - 1) / NA_TX) * ((n - 1 + NA_TY - 1) / NA_TY);
-    k_energy_tiles_noalloc<<<tiles, NA_THREADS, 0, st>>>(R, T, n, pitch, u_grid, scratch);
-    k_energy_finish_noalloc<<<1, 1024, 0, st>>>(tiles, n, lambda, scratch);
+    // pass 1: means; pass 2: centred second moments and the regulariser
+    k_energy_tiles_noalloc<<<tiles, NA_THREADS, 0, st>>>(R, T, n, pitch, u_grid, nullptr, scratch);
+    k_energy_finish_noalloc<<<1, 1024, 0, st>>>(tiles, n, lambda, 0, scratch);
+    k_energy_tiles_noalloc<<<tiles, NA_THREADS, 0, st>>>(R, T, n, pitch, u_grid, scratch + NA_OUT, scratch);
+    k_energy_finish_noalloc<<<1, 1024, 0, st>>>(tiles, n, lambda, 1, scratch);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(parts_out, scratch + (size_t)NA_MAX_TILES * NA_SUMS, 5 * sizeof(double),
+        e = cudaMemcpyAsync(parts_out, scratch + NA_OUT, 5 * sizeof(double),
                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? REG_OK : REG_ECUDA;

@@ -64,3 +64,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(reg):
     assert rc == reg.EINVAL
     rc = lib.reg_eval_energy_noalloc(None, t.data_ptr(), 17, 17, t.data_ptr(), 1.0, parts.ctypes.data, 0, None)
     assert rc == reg.EINVAL
+
+
+@pytest.mark.parametrize("side,offset", [(256, 0.0), (256, 1000.0), (2048, 0.0)])
+def test_noalloc_energy_matches_oracle(reg, orc, syn, side, offset):
+    """Against the FP64 oracle directly: raw embedded frames (a constant
+    offset of 1000 counts makes the mean large against the spread, where a
+    one-pass variance would cancel), and the largest size the scratch array
+    holds (frames of 2048^2, REG_NOALLOC_MAX_NODES nodes per side)."""
+    import torch
+    lam = 10.0
+    n = side + 1
+    fr = syn.series(5, 2, side, peak=10.0, spacing=12.0, sigma=2.0) + np.float32(offset)
+    R, T = orc.embed(fr[0]), orc.embed(fr[1])
+    Rt = torch.from_numpy(R.astype(np.float32)).cuda()
+    Tt = torch.from_numpy(T.astype(np.float32)).cuda()
+    for seed, amp in [(2, 0.7), (3, 2.5)]:
+        u = _field(n, seed, amp)
+        got = reg.eval_energy_noalloc(Rt, Tt, torch.from_numpy(u).cuda(), lam)
+        E, parts = orc.energy(R, T, u.astype(np.float64) / side, lam)
+        scale = abs(parts["ncc"]) + abs(parts["reg"])
+        assert abs(got["E"] - E) <= 1e-5 * scale, (side, offset, seed, got, E)
+        assert abs(got["ncc"] - parts["ncc"]) <= 1e-5 * abs(parts["ncc"])
+        assert abs(got["reg"] - parts["reg"]) <= 1e-5 * abs(parts["reg"])
+        assert abs(got["Tbar"] - parts["Tbar"]) <= 1e-5 * abs(parts["Tbar"])
+        assert abs(got["sigT"] - parts["sigT"]) <= 1e-5 * parts["sigT"]
