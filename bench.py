@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--autotune", type=int, default=64,
                     help="pairs in the tile autotuner's sample batch before timing (0: default tiles)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cnn", action="store_true", help="skip the CNN tensor-core roofline entry")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -82,6 +83,97 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+FAMILIES = ("prolong", "grad", "trial", "control", "plan", "setup")
+
+# Algorithmic bytes per node of the step kernels in the survey's model of one
+# gradient iteration (FP32 storage): the gradient pass reads u and d (16 B), the
+# template (4) and M~R~ (4) and writes u and d (16): 40 B; every sequential
+# Armijo trial reads u and d, the template and M~R~: 24 B; every per-level
+# setup pass 16 B.  With BF16 images the template read is 2 B.
+MODEL_BYTES = {"grad": 40.0, "trial_seq": 24.0, "trial_start": 16.0}
+
+
+def roofline_of(stats, cfg, bf16=False):
+    """Roofline of the dominant step kernel from one profiled step: achieved =
+    model bytes per launch / mean launch time (CUDA events), against the
+    measured HBM peak; the library's own byte count (what the kernels read and
+    write per node: the 32-byte node records) is given beside it."""
+    peak, peak_kind = _peaks()
+    img_save = 2.0 if bf16 else 0.0
+    model = {"grad": stats["grad"]["items"] * (MODEL_BYTES["grad"] - img_save),
+             "trial": stats["trial_seq_nodes"]["items"] * (MODEL_BYTES["trial_seq"] - img_save)
+             + stats["trial_start_nodes"]["items"] * MODEL_BYTES["trial_start"],
+             "prolong": None}
+    fams = {k: v for k, v in stats.items() if k in ("grad", "trial", "prolong")}
+    dom = max(fams, key=lambda k: fams[k]["ms"])
+    dk = fams[dom]
+    launches = max(1, dk["launches"])
+    sec = dk["ms"] * 1e-3
+    mb = model[dom] if model[dom] is not None else dk["bytes"]
+    achieved = mb / sec / 1e9 if sec > 0 else 0.0
+    lib_achieved = dk["bytes"] / sec / 1e9 if sec > 0 else 0.0
+    total_ms = sum(v["ms"] for k, v in stats.items() if k in FAMILIES)
+    kern = {}
+    for k, v in stats.items():
+        if k not in FAMILIES:
+            continue
+        e = {"ms": round(v["ms"], 2), "launches": v["launches"], "share": round(v["ms"] / total_ms, 4) if total_ms else None,
+             "GBps_library_bytes": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None}
+        if model.get(k):
+            e["GBps_model_bytes"] = round(model[k] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None
+        kern[k] = e
+    seq_per_pass = (stats["trial_seq_nodes"]["items"] / max(1, stats["trial"]["items"] - stats["trial_start_nodes"]["items"]))
+    return {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "bytes_model": "40 B/node per gradient pass + 24 B/node per sequential Armijo trial + 16 B/node per "
+                           "level-start pass (FP32 storage)",
+            "traffic": _traffic(dom, dk["bytes"] / launches), "traffic_note": "estimated: committed DRAM/library-byte "
+                       "ratio of an ncu capture times this launch's library bytes (null if the kernel source changed)",
+            "bytes_per_launch": mb / launches, "library_bytes_per_launch": dk["bytes"] / launches,
+            "achieved_library_bytes": round(lib_achieved, 1), "frac_library_bytes": round(lib_achieved / peak, 4),
+            "ms_per_launch": dk["ms"] / launches, "sequential_trials_per_trial_pass": round(seq_per_pass, 3),
+            "kernels": kern}
+
+
+def cnn_roofline(reg, s, torch, batch=64, reps=20):
+    """Tensor-core roofline of the learned initialiser's forward pass: the 64
+    network inputs of the series' first neighbour pairs through the 6-layer
+    CNN (the four 32->32 layers on the BF16 tensor cores), timed with CUDA
+    events; FLOPs = 2 x multiply-adds of all six layers (0.326 GFLOP per pair)."""
+    import synth
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    x = torch.empty((batch, 2, 256, 256), dtype=torch.float32, device="cuda")
+    s.cnn_pairs(0, batch, x)
+    flop_pair = 0.0
+    side = 256
+    for (c, o), stride in zip(synth.CNN_SHAPES, (2, 2, 1, 1, 1, 1)):
+        side //= stride
+        flop_pair += 2.0 * side * side * o * c * 9
+    with reg.Cnn(synth.cnn_params(1), side=256, max_batch=batch) as net:
+        y = net.forward(x, tensor_cores=True)
+        for _ in range(3):
+            net.forward(x, y, tensor_cores=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.forward(x, y, tensor_cores=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    tflops = flop_pair * batch / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "CNN forward (k_conv32_tc on the four 32->32 layers, BF16 operands, FP32 "
+                                        "accumulation; the 2->32 and 32->2 layers on the CUDA cores)",
+            "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tflops / peak, 5),
+            "peak_source": src, "batch": batch, "ms_per_forward": round(ms, 4),
+            "gflop_per_pair": round(flop_pair / 1e9, 4), "traffic": None}
 
 
 class ClockSampler:
@@ -243,8 +335,8 @@ def main():
     frames = synth.series(rank_seed(cfg["seed"], rank), cfg["n_frames"], cfg["side"], spacing=cfg["spacing"],
                           sigma=cfg["sigma"], peak=cfg["peak"], drift_sd=cfg["drift_sd"], dist_amp=cfg["dist_amp"])
     gen_s = time.time() - t0
-    params = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"],
-                                flags=reg.FLAG_PROFILE)
+    # the product path: the step kernels replayed as captured CUDA graphs (flags 0)
+    params = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"], flags=0)
     fd = torch.from_numpy(frames).to(dev)
     torch.cuda.synchronize()
     t0 = time.time()
@@ -282,27 +374,25 @@ def main():
     barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    stats = s.kernel_stats()
+    timed = s.kernel_stats()  # launches, algorithmic bytes and node counters of the timed steps
     ops_per_step = reports[-1]["ops"]
     ms = max_over_ranks(ms, world, dev)
     ms_step = ms / a.steps
     value = job_rate(world, ops_per_step, ms_step / 1e3)
 
-    # dominant kernel and its roofline
-    peak, peak_kind = _peaks()
-    fams = {k: v for k, v in stats.items() if k in ("grad", "trial", "prolong")}
-    dom = max(fams, key=lambda k: fams[k]["ms"])
-    dk = fams[dom]
-    launches = max(1, dk["launches"])
-    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": _traffic(dom, dk["bytes"] / launches), "bytes_per_launch": dk["bytes"] / launches,
-                "ms_per_launch": dk["ms"] / launches,
-                "kernels": {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
-                                "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
-                            for k, v in stats.items()}}
-    gpu_launches = int(sum(v["launches"] for v in stats.values()))
+    # Per-kernel device times: one more step, untimed, with every step kernel
+    # launched directly between CUDA events on the library's stream
+    # (REG_FLAG_PROFILE); the same work as a timed step.
+    s.set_flags(reg.FLAG_PROFILE)
+    s.reset_kernel_stats()
+    prof_rep = step()
+    torch.cuda.synchronize()
+    stats = s.kernel_stats()
+    s.set_flags(0)
+    roofline = roofline_of(stats, cfg, bf16=False)
+    roofline["profiled_step_ms"] = round(prof_rep["ms"], 2) if prof_rep.get("ms") else None
+    gpu_launches = int(sum(v["launches"] for k, v in timed.items() if k in FAMILIES))
+    roofline_cnn = None if a.preprocess_only or a.no_cnn else cnn_roofline(reg, s, torch)
 
     # end to end through the C-ABI with host buffers (upload, pyramid, scan, download)
     e2e = None
@@ -312,7 +402,7 @@ def main():
         p2 = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"])
         if tiles:
             p2.trials_per_pass = tiles["trials_per_pass"]
-        e2e_steps = max(1, min(a.steps, 2))
+        e2e_steps = max(1, a.steps)
         barrier()
         t = time.time()
         for _ in range(e2e_steps):
@@ -345,10 +435,14 @@ def main():
                        if a.kind in ("han_carlson", "ladner_fischer") else None,
                        "ops_per_step": ops_per_step, "preprocessing_ops": rep["preprocessing_ops"],
                        "scan_ops": rep["scan_ops"], "scan_batches": rep["scan_batches"],
-                       "iters_per_step": rep["iters"], "l2": "working set (GBs) larger than L2; no flush",
+                       "iters_per_step": rep["iters"], "trials_per_step": rep.get("trials"),
+                       "timed_path": "captured CUDA graphs (8 steps per replay); per-kernel times from one "
+                                     "more untimed step with per-kernel CUDA events",
+                       "l2": "working set (GBs) larger than L2; no flush",
                        "tiles": tiles,
                        "generator_s": round(gen_s, 1), "create_ms": round(create_s * 1e3, 1)},
-            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
+            "roofline": roofline, "roofline_cnn": roofline_cnn, "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
