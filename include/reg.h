@@ -189,6 +189,27 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
 reg_status reg_get_deformations(reg_series_t s, int32_t series, int32_t first, int32_t count, float *out,
                                 int32_t out_on_device);
 
+/* Series averaging (Section "Introduction": the frames of a registered series,
+ * deformed by phi_{0,i}, are averaged into one frame that holds the
+ * information of the whole acquisition; Section "Registration for series of
+ * images": the series averaging procedure repeats the registration to improve
+ * it).  Valid after reg_prefix_scan.  The average is
+ *   avg(x) = 1/N sum_{i=0}^{N-1} f_i(phi_i(x)),   phi_0 = id, phi_i = phi_{0,i},
+ * on the finest vertex grid, each frame sampled by bilinear interpolation
+ * (clamped to Omega) in its raw intensities (the stored normalisation undone).
+ * Then `iterations` times: the average becomes the reference frame, every
+ * frame f_i (f_0 included) is registered to it by function A started from
+ * its current deformation (f_0 from the identity the first time) -- all N
+ * operators in one batch -- and the average is formed again with the new
+ * deformations.  After at least one iteration reg_get_deformations returns
+ * these deformations from the average's frame to each frame (frame 0's
+ * included) until the next reg_prefix_scan.  avg_out (nullable): side x side
+ * float32, the average at the frame's pixels (host memory unless
+ * out_on_device).  Errors: REG_ESTATE before a scan, REG_EINVAL for a bad
+ * series or iterations outside [0, 1000]. */
+reg_status reg_average_series(reg_series_t s, int32_t series, int32_t iterations, float *avg_out,
+                              int32_t out_on_device);
+
 /* Copy the finest-level field held in a slot and its (start, end) frame pair;
  * end < 0 marks the identity (zeros are written).  out: 2 x (side+1) x (side+1)
  * float32, pixels, the full vertex grid of level L (host unless

@@ -90,6 +90,12 @@ def _load():
         "orc_compose": ([vp, vp, i, vp], None),
         "orc_apply_batch": ([i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp], None),
         "orc_set_trace": ([vp, ctypes.c_long], None),
+        "orc_average": ([i, vp, vp, i, vp], None),
+        "orc_rigid_field": ([vp, i, vp], None),
+        "orc_rigid_energy": ([vp, vp, i, vp, ctypes.c_double], ctypes.c_double),
+        "orc_rigid_gradient": ([vp, vp, i, vp, ctypes.c_double, vp], None),
+        "orc_rigid_register": ([vp, vp, i, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(LevelStats)], i),
+        "orc_rigid_compose": ([vp, vp, vp], None),
         "orc_trace_len": ([], ctypes.c_long),
     }
     for name, (args, res) in sig.items():
@@ -345,3 +351,120 @@ def register_series(series_frames, p: Params, kind=schedules.SERIAL, chunks=8,
     if return_info:
         return results, info
     return results
+
+
+# ------------------------------------------------------------ series averaging
+def average(grids, fields):
+    """Average of the deformed frames: grids are embedded frames (n x n nodal
+    values), fields their displacements (2, n, n) in Omega units or None for
+    the identity; returns the n x n nodal average of F_k o (id + u_k)."""
+    m = len(grids)
+    n = grids[0].shape[0]
+    keep = [_c(g) for g in grids]
+    ks = [None if f is None else _c(f) for f in fields]
+    Fp = (ctypes.c_void_p * m)(*[g.ctypes.data for g in keep])
+    Up = (ctypes.c_void_p * m)(*[None if f is None else f.ctypes.data for f in ks])
+    out = np.empty((n, n))
+    _load().orc_average(m, Fp, Up, n, out.ctypes.data)
+    return out
+
+
+def average_series(frames, p: Params, iterations=1, kind=schedules.SKLANSKY):
+    """The series averaging procedure: register the series (preprocessing and
+    prefix scan), average the deformed frames f_k o phi_{0,k} (phi_{0,0} the
+    identity), then `iterations` times register every frame to the current
+    average with function A, started from its current deformation, and average
+    again.  frames: (m, side, side).  Returns (average n x n nodal, fields
+    (m, 2, n, n) in pixels: the deformations from the last average's frame to
+    each frame, or phi_{0,k} when iterations = 0)."""
+    side = frames.shape[1]
+    grids = [embed(f) for f in frames]
+    phi = register_series([frames], p, kind=kind)[0] / side  # (m, 2, n, n) Omega units
+    fields = [None] + [phi[k] for k in range(1, len(grids))]
+    avg = average(grids, fields)
+    for _ in range(iterations):
+        ops = [dict(R=avg, T=grids[k], left=(np.zeros_like(phi[0]) if fields[k] is None else fields[k]))
+               for k in range(len(grids))]
+        outs, _, _, _, _ = apply_batch(ops, p)
+        fields = outs
+        avg = average(grids, fields)
+    return avg, np.stack([np.zeros_like(phi[0]) if f is None else f for f in fields]) * side
+
+
+# ------------------------------------------------------------- rigid variant
+def rigid_field(theta, n):
+    """u(x) = R(alpha) x + t - x at the n x n nodes, Omega units; theta =
+    (alpha, t0, t1) with t in Omega units."""
+    th = _c(theta)
+    out = np.empty((2, n, n))
+    _load().orc_rigid_field(th.ctypes.data, n, out.ctypes.data)
+    return out
+
+
+def rigid_energy(R, T, theta, lam):
+    R, T, th = _c(R), _c(T), _c(theta)
+    return _load().orc_rigid_energy(R.ctypes.data, T.ctypes.data, R.shape[0], th.ctypes.data, lam)
+
+
+def rigid_gradient(R, T, theta, lam):
+    R, T, th = _c(R), _c(T), _c(theta)
+    g = np.empty(3)
+    _load().orc_rigid_gradient(R.ctypes.data, T.ctypes.data, R.shape[0], th.ctypes.data, lam, g.ctypes.data)
+    return g
+
+
+def rigid_register(R, T, p: Params, theta_init=None):
+    """Rigid function A on level-L grids: returns (theta, status, level stats)."""
+    R, T = _c(R), _c(T)
+    n = R.shape[0]
+    L = int(round(np.log2(n - 1)))
+    out = np.empty(3)
+    st = (LevelStats * p.n_levels)()
+    ti = _c(theta_init) if theta_init is not None else None
+    s = _load().orc_rigid_register(R.ctypes.data, T.ctypes.data, L, _ptr(ti), ctypes.byref(p), out.ctypes.data, st)
+    return out, s, [st[i] for i in range(p.n_levels)]
+
+
+def rigid_compose(a, b):
+    """phi_b o phi_a (a applied first) of rigid parameters."""
+    a, b = _c(a), _c(b)
+    out = np.empty(3)
+    _load().orc_rigid_compose(a.ctypes.data, b.ctypes.data, out.ctypes.data)
+    return out
+
+
+def rigid_register_series(frames, p: Params, kind=schedules.SERIAL, chunks=8, global_kind=schedules.KOGGE_STONE):
+    """Image series registration with the rigid operator: preprocessing
+    x_e = A(f_e, f_{e+1}, I), then the prefix scan of
+    B(a, b) = A(f_i, f_k, b o a) with the chosen schedule.  Returns
+    (n_frames, 3) parameters of phi_{0,k} (row 0 the identity)."""
+    grids = [embed(f) for f in frames]
+    N = len(grids) - 1
+    na = schedules.aux_slots(kind, N, chunks, global_kind)
+    slots = [None] * (N + na)
+    for e in range(N):
+        th, _, _ = rigid_register(grids[e], grids[e + 1], p)
+        slots[e] = (e, e + 1, th)
+    for lev in schedules.schedule(kind, N, chunks, global_kind):
+        writes = []
+        for o in lev:
+            if o[0] == "id":
+                writes.append((o[1], "id"))
+            elif o[0] == "copy":
+                writes.append((o[1], slots[o[2]]))
+            else:
+                a, b = slots[o[2]], slots[o[3]]
+                if a == "id":
+                    writes.append((o[1], b))
+                elif b == "id":
+                    writes.append((o[1], a))
+                else:
+                    th, _, _ = rigid_register(grids[a[0]], grids[b[1]], p, rigid_compose(a[2], b[2]))
+                    writes.append((o[1], (a[0], b[1], th)))
+        for dst, v in writes:
+            slots[dst] = v
+    out = np.zeros((N + 1, 3))
+    for e in range(N):
+        assert slots[e][0] == 0 and slots[e][1] == e + 1
+        out[e + 1] = slots[e][2]
+    return out

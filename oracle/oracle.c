@@ -556,3 +556,212 @@ void orc_apply_batch(int n_ops, const double *const *R, const double *const *T, 
         free(init);
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Series averaging (Section "Introduction": the deformed frames              */
+/* f_i o phi_{0,i} of an aligned series are averaged into one frame; Section   */
+/* "Registration for series of images": the series averaging procedure)       */
+/* ------------------------------------------------------------------------- */
+
+/* avg = 1/m sum_k F_k o (id + u_k), nodal interpolation on the vertex grid of
+ * n x n nodes: F_k are the m embedded frames (nodal values), u_k their
+ * displacements in Omega units (two planes each; NULL = the identity). */
+void orc_average(int m, const double *const *F, const double *const *u, int n, double *avg)
+{
+    double h = 1.0 / (n - 1);
+    size_t N = (size_t)n * n;
+    for (size_t i = 0; i < N; i++) avg[i] = 0.0;
+    for (int k = 0; k < m; k++)
+        for (int r = 0; r < n; r++)
+            for (int c = 0; c < n; c++) {
+                size_t i = (size_t)r * n + c;
+                double x0 = c * h, x1 = r * h;
+                if (u[k]) {
+                    x0 += u[k][i];
+                    x1 += u[k][N + i];
+                }
+                avg[i] += orc_interp(F[k], n, x0, x1, NULL, NULL);
+            }
+    for (size_t i = 0; i < N; i++) avg[i] /= m;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rigid variant (Definition "Rigid transformation": phi(x) = R(alpha) x + t, */
+/* rotation about the origin of Omega; Section "Gradient flow": the smoother  */
+/* is applied only in the non-rigid registration; Algorithm "Multilevel       */
+/* gradient flow": a rigid deformation is not restricted or prolongated)      */
+/* ------------------------------------------------------------------------- */
+
+/* Nodal displacement u(x) = R(alpha) x + t - x of theta = (alpha, t0, t1),
+ * Omega units, two planes. */
+void orc_rigid_field(const double *theta, int n, double *u)
+{
+    double h = 1.0 / (n - 1), ca = cos(theta[0]), sa = sin(theta[0]);
+    size_t N = (size_t)n * n;
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) {
+            double x0 = c * h, x1 = r * h;
+            u[(size_t)r * n + c] = ca * x0 - sa * x1 + theta[1] - x0;
+            u[N + (size_t)r * n + c] = sa * x0 + ca * x1 + theta[2] - x1;
+        }
+}
+
+double orc_rigid_energy(const double *R, const double *T, int n, const double *theta, double lambda)
+{
+    double *u = dalloc(2 * (size_t)n * n);
+    orc_rigid_field(theta, n, u);
+    double E = orc_energy(R, T, n, u, lambda, NULL);
+    free(u);
+    return E;
+}
+
+/* dE/dtheta_j = sum_i g_i . du_i/dtheta_j with g the nodal gradient of the
+ * discrete energy (orc_gradient): du/dalpha = R'(alpha) x, du/dt_c = e_c. */
+void orc_rigid_gradient(const double *R, const double *T, int n, const double *theta, double lambda, double *grad)
+{
+    size_t N = (size_t)n * n;
+    double h = 1.0 / (n - 1), ca = cos(theta[0]), sa = sin(theta[0]);
+    double *u = dalloc(2 * N), *g = dalloc(2 * N);
+    orc_rigid_field(theta, n, u);
+    orc_gradient(R, T, n, u, lambda, g);
+    grad[0] = grad[1] = grad[2] = 0.0;
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) {
+            size_t i = (size_t)r * n + c;
+            double x0 = c * h, x1 = r * h;
+            grad[0] += g[i] * (-sa * x0 - ca * x1) + g[N + i] * (ca * x0 - sa * x1);
+            grad[1] += g[i];
+            grad[2] += g[N + i];
+        }
+    free(u);
+    free(g);
+}
+
+/* Gradient descent on theta with the Armijo rule with widening of
+ * orc_solve_level (direction d = -grad E, no smoother). */
+int orc_rigid_solve_level(const double *R, const double *T, int n, double *theta, const orc_params *p,
+                          orc_level_stats *st)
+{
+    int iters = 0, trials = 0, status = ORC_MAXITER;
+    double E0 = orc_rigid_energy(R, T, n, theta, p->lambda), Estart = E0, tau = p->tau_init;
+    if (!isfinite(E0)) status = ORC_NONFINITE;
+    for (int it = 0; status != ORC_NONFINITE && it < p->iter_max; it++) {
+        double g[3], d[3], th[3];
+        orc_rigid_gradient(R, T, n, theta, p->lambda, g);
+        iters++;
+        double slope = 0.0;
+        for (int j = 0; j < 3; j++) {
+            d[j] = -g[j];
+            slope += g[j] * d[j];
+        }
+        if (!(slope < 0.0)) {
+            status = (slope == 0.0) ? ORC_ZERO_GRADIENT : ORC_NONFINITE;
+            break;
+        }
+#define RTRIAL(t_, E_)                                                      \
+    do {                                                                    \
+        for (int j_ = 0; j_ < 3; j_++) th[j_] = theta[j_] + (t_) * d[j_];   \
+        (E_) = orc_rigid_energy(R, T, n, th, p->lambda);                    \
+        trials++;                                                           \
+    } while (0)
+        double E1;
+        int stalled = 0;
+        RTRIAL(tau, E1);
+        int ok = E1 - E0 <= p->armijo_sigma * tau * slope;
+        trace(n, it, tau, E1 - E0, p->armijo_sigma * tau * slope, ok);
+        if (ok) {
+            for (;;) {
+                double t2 = 2.0 * tau, Et;
+                if (t2 > p->tau_max) break;
+                RTRIAL(t2, Et);
+                int ok2 = Et - E0 <= p->armijo_sigma * t2 * slope;
+                trace(n, it, t2, Et - E0, p->armijo_sigma * t2 * slope, ok2);
+                if (!ok2) break;
+                tau = t2;
+                E1 = Et;
+            }
+        } else {
+            for (;;) {
+                tau = 0.5 * tau;
+                if (tau < p->tau_min) {
+                    stalled = 1;
+                    break;
+                }
+                RTRIAL(tau, E1);
+                int ok3 = E1 - E0 <= p->armijo_sigma * tau * slope;
+                trace(n, it, tau, E1 - E0, p->armijo_sigma * tau * slope, ok3);
+                if (ok3) break;
+            }
+        }
+#undef RTRIAL
+        if (stalled) {
+            status = ORC_LS_STALLED;
+            break;
+        }
+        for (int j = 0; j < 3; j++) theta[j] += tau * d[j];
+        double dec = E0 - E1, scale = fabs(E0) > 1.0 ? fabs(E0) : 1.0;
+        E0 = E1;
+        if (dec < p->epsilon * scale) {
+            status = ORC_CONVERGED;
+            break;
+        }
+    }
+    if (st) {
+        st->iters = iters;
+        st->trials = trials;
+        st->status = status;
+        st->E_start = Estart;
+        st->E = E0;
+        st->tau = tau;
+    }
+    return status;
+}
+
+/* Multilevel rigid registration: the images are restricted down to m0 as in
+ * orc_register; the three parameters are carried from level to level as they
+ * are (they do not depend on the grid). */
+int orc_rigid_register(const double *R, const double *T, int L, const double *theta_init, const orc_params *p,
+                       double *theta_out, orc_level_stats *st)
+{
+    int nl = p->n_levels;
+    if (nl < 1 || nl > L + 1) return -1;
+    int m0 = L - nl + 1;
+    double *Rl[32], *Tl[32];
+    int nn[32];
+    for (int l = m0; l <= L; l++) {
+        nn[l] = (1 << l) + 1;
+        Rl[l] = dalloc((size_t)nn[l] * nn[l]);
+        Tl[l] = dalloc((size_t)nn[l] * nn[l]);
+    }
+    memcpy(Rl[L], R, (size_t)nn[L] * nn[L] * sizeof(double));
+    memcpy(Tl[L], T, (size_t)nn[L] * nn[L] * sizeof(double));
+    for (int l = L - 1; l >= m0; l--) {
+        orc_restrict(Rl[l + 1], nn[l + 1], Rl[l]);
+        orc_restrict(Tl[l + 1], nn[l + 1], Tl[l]);
+    }
+    double th[3] = {0.0, 0.0, 0.0};
+    if (theta_init) memcpy(th, theta_init, sizeof(th));
+    int worst = ORC_CONVERGED;
+    for (int l = m0; l <= L; l++) {
+        int s = orc_rigid_solve_level(Rl[l], Tl[l], nn[l], th, p, st ? &st[l - m0] : NULL);
+        if (s == ORC_NONFINITE) worst = ORC_NONFINITE;
+        else if (l == L && worst != ORC_NONFINITE) worst = s;
+    }
+    memcpy(theta_out, th, sizeof(th));
+    for (int l = m0; l <= L; l++) {
+        free(Rl[l]);
+        free(Tl[l]);
+    }
+    return worst;
+}
+
+/* phi_b o phi_a for rigid maps (phi_a applied first):
+ * R(b0) (R(a0) x + ta) + tb = R(a0 + b0) x + R(b0) ta + tb. */
+void orc_rigid_compose(const double *a, const double *b, double *out)
+{
+    double cb = cos(b[0]), sb = sin(b[0]);
+    double t0 = cb * a[1] - sb * a[2] + b[1], t1 = sb * a[1] + cb * a[2] + b[2];
+    out[0] = a[0] + b[0];
+    out[1] = t0;
+    out[2] = t1;
+}

@@ -47,4 +47,13 @@ void orc_apply_batch(int n_ops, const double *const *R, const double *const *T, 
                      const double *const *left, const double *const *right, double *const *out,
                      const orc_params *p, int32_t *status, int32_t *iters, int32_t *trials,
                      double *energy);
+void orc_average(int m, const double *const *F, const double *const *u, int n, double *avg);
+void orc_rigid_field(const double *theta, int n, double *u);
+double orc_rigid_energy(const double *R, const double *T, int n, const double *theta, double lambda);
+void orc_rigid_gradient(const double *R, const double *T, int n, const double *theta, double lambda, double *grad);
+int orc_rigid_solve_level(const double *R, const double *T, int n, double *theta, const orc_params *p,
+                          orc_level_stats *st);
+int orc_rigid_register(const double *R, const double *T, int L, const double *theta_init, const orc_params *p,
+                       double *theta_out, orc_level_stats *st);
+void orc_rigid_compose(const double *a, const double *b, double *out);
 #endif

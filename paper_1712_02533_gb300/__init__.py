@@ -101,6 +101,7 @@ def _load():
         "reg_get_trace": ([vp, vp, i64, P(i64)], ctypes.c_int),
         "reg_set_lockstep": ([vp, i32, i32, vp, vp], ctypes.c_int),
         "reg_set_flags": ([vp, i32], ctypes.c_int),
+        "reg_average_series": ([vp, i32, i32, vp, i32], ctypes.c_int),
         "reg_eval_energy_noalloc": ([vp, vp, i32, i32, vp, d, vp, i32, vp], ctypes.c_int),
         "reg_destroy_series": ([vp], ctypes.c_int),
         "reg_cnn_num_params": ([], i64),
@@ -475,6 +476,17 @@ class Series:
         if count is None:
             count = self.counts[series] - first
         return get_deformations(self.h, series, first, count, self.sides[series], out)
+
+    def average(self, iterations=0, series=0, out=None):
+        """Series averaging after prefix_scan: the average of the deformed
+        frames (side x side float32), after `iterations` rounds of registering
+        every frame to the average (C-ABI reg_average_series)."""
+        side = self.sides[series]
+        if out is None:
+            out = np.empty((side, side), np.float32)
+        ptr, on_dev = _ptr(out)
+        _check(_load().reg_average_series(self.h, series, iterations, ptr, on_dev))
+        return out
 
     def get_slot(self, slot, series=0):
         return get_slot(self.h, series, slot, self.sides[series])

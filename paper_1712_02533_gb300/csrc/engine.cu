@@ -35,6 +35,9 @@ int step_blocks_per_sm(int which, int J);
 __global__ void k_control(BatchDev);
 __global__ void k_slot_to_planes(const float2 *, int, int, float *);
 __global__ void k_planes_to_slot(const float *, int, float2 *, int);
+void launch_average(int bf16, cudaStream_t st, const void *pyr, int64_t frame_block, int64_t img_off, int n,
+                    int pitch, const double *fstats, const float2 *const *fields, int slot_pitch, int m, float *out,
+                    int opitch);
 
 namespace {
 
@@ -81,6 +84,13 @@ struct SeriesInfo {
     size_t slot_elems = 0;
     std::vector<SlotMeta> meta;
     bool pre_from_slots = false;          // next scan: preprocessing starts from the data slots
+    // Series averaging: pyramid block n_frames (one past the frames) holds the
+    // average frame, slot n_slots (one past the scan's slots) frame 0's
+    // deformation to it; fstats: FE mean and sigma of every frame's finest level
+    // (n_frames + 1 pairs), to undo the normalisation of the stored pyramid.
+    double *fstats = nullptr;
+    const float2 **d_fields = nullptr;    // per frame: its deformation field (null: identity)
+    bool refined = false;                 // slots hold deformations to the average frame
     std::vector<size_t> ws_off;           // per level: offset (bytes) of U0 within an op workspace
     size_t ws_bytes = 0;                  // per op
     size_t rec_bytes(int k) const { return (size_t)n[k] * pitch[k] * sizeof(NodeRec); }
@@ -556,6 +566,34 @@ reg_status validate_params(const reg_params *p)
     return REG_OK;
 }
 
+// Pyramid levels of nf frames from their raw finest levels (rawf: nf blocks of
+// frame_block floats, level L filled): the restriction chain (1/16 [1 2 1; 2 4
+// 2; 1 2 1], Section "Multilevel"), per level the FE mean and sigma and the
+// normalised image (stored as float or bf16) with its M~ R~ image, into pyramid
+// blocks f0 .. f0+nf-1.  The finest level's mean and sigma are kept in fstats.
+void build_levels(reg_series *s, SeriesInfo &si, float *rawf, int f0, int nf, double *stats)
+{
+    dim3 blk(32, 8);
+    const int kL = si.nl - 1;
+    for (int k = kL - 1; k >= 0; k--)
+        k_restrict_img<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+            rawf + si.img_off[k + 1], (int64_t)si.frame_block, si.pitch[k + 1], si.n[k + 1],
+            rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k]);
+    for (int k = 0; k < si.nl; k++) {
+        k_image_stats<<<nf, 512, 0, s->stream>>>(rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k],
+                                                 si.n[k], stats);
+        size_t esz = s->bf16 ? 2 : 4;
+        char *dst = (char *)si.pyr + ((size_t)f0 * si.frame_block + si.img_off[k]) * esz;
+        k_normalize<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+            rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k], si.n[k], (const double *)stats, dst,
+            (int64_t)si.frame_block, si.pitch[k], s->bf16);
+        k_mass_image<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
+            dst, (int64_t)si.frame_block, si.pitch[k], si.n[k], s->bf16,
+            si.mr + (size_t)f0 * si.frame_block + si.img_off[k], (int64_t)si.frame_block);
+    }
+    cudaMemcpyAsync(si.fstats + 2 * (size_t)f0, stats, sizeof(double) * 2 * nf, cudaMemcpyDeviceToDevice, s->stream);
+}
+
 // Copy a slot field (device) to another slot.
 reg_status copy_slot(reg_series *s, const SeriesInfo &si, int dst, int src)
 {
@@ -687,10 +725,14 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         si.slot_elems = (size_t)si.n[si.nl - 1] * si.pitch[si.nl - 1];
         si.meta.assign(si.n_slots, SlotMeta{});
         size_t esz = s->bf16 ? 2 : 4;
-        if ((st = track(s, &si.pyr, si.frame_block * si.n_frames * esz)) != REG_OK) return cleanup(st);
-        if ((st = track(s, (void **)&si.mr, si.frame_block * si.n_frames * sizeof(float))) != REG_OK)
+        const size_t blocks = (size_t)si.n_frames + 1;  // + the average frame
+        if ((st = track(s, &si.pyr, si.frame_block * blocks * esz)) != REG_OK) return cleanup(st);
+        if ((st = track(s, (void **)&si.mr, si.frame_block * blocks * sizeof(float))) != REG_OK)
             return cleanup(st);
-        if ((st = track(s, (void **)&si.slots, si.slot_elems * si.n_slots * sizeof(float2))) != REG_OK) return cleanup(st);
+        if ((st = track(s, (void **)&si.slots, si.slot_elems * (si.n_slots + 1) * sizeof(float2))) != REG_OK)
+            return cleanup(st);
+        if ((st = track(s, (void **)&si.fstats, sizeof(double) * 2 * blocks)) != REG_OK) return cleanup(st);
+        if ((st = track(s, (void **)&si.d_fields, sizeof(void *) * si.n_frames)) != REG_OK) return cleanup(st);
         s->S.push_back(si);
     }
     // Pyramid construction in chunks of frames: raw level L, restriction chain,
@@ -724,22 +766,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
             dim3 blk(32, 8);
             k_embed<<<dim3(cdiv(nL, 32), cdiv(nL, 8), nf), blk, 0, s->stream>>>(
                 src, fstride, pitch, si.side, rawf + si.img_off[kL], (int64_t)si.frame_block, si.pitch[kL]);
-            for (int k = kL - 1; k >= 0; k--)
-                k_restrict_img<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
-                    rawf + si.img_off[k + 1], (int64_t)si.frame_block, si.pitch[k + 1], si.n[k + 1],
-                    rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k]);
-            for (int k = 0; k < si.nl; k++) {
-                k_image_stats<<<nf, 512, 0, s->stream>>>(rawf + si.img_off[k], (int64_t)si.frame_block,
-                                                         si.pitch[k], si.n[k], (double *)stats);
-                size_t esz = s->bf16 ? 2 : 4;
-                char *dst = (char *)si.pyr + ((size_t)f0 * si.frame_block + si.img_off[k]) * esz;
-                k_normalize<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
-                    rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k], si.n[k], (const double *)stats,
-                    dst, (int64_t)si.frame_block, si.pitch[k], s->bf16);
-                k_mass_image<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
-                    dst, (int64_t)si.frame_block, si.pitch[k], si.n[k], s->bf16,
-                    si.mr + (size_t)f0 * si.frame_block + si.img_off[k], (int64_t)si.frame_block);
-            }
+            build_levels(s, si, rawf, f0, nf, (double *)stats);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid kernels: %s", cudaGetErrorString(e)));
         }
@@ -847,6 +874,7 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
     for (int si = 0; si < (int)s->S.size(); si++) {
         SeriesInfo &S = s->S[si];
         for (auto &m : S.meta) m = SlotMeta{};
+        S.refined = false;
         // identity start, or (after reg_cnn_init_series) the slot's initial guess
         for (int e = 0; e < S.n_data; e++)
             pre.push_back(S.pre_from_slots
@@ -969,6 +997,69 @@ reg_status reg_prefix_scan(reg_series_t s, reg_scan_kind kind, int32_t chunks, r
     return REG_OK;
 }
 
+reg_status reg_average_series(reg_series_t s, int32_t series, int32_t iterations, float *avg_out,
+                              int32_t out_on_device)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad handle or series");
+    if (iterations < 0 || iterations > 1000) return fail(REG_EINVAL, "iterations must be in [0, 1000]");
+    SeriesInfo &si = s->S[series];
+    for (int e = 0; e < si.n_data; e++)
+        if (si.meta[e].start != 0 || si.meta[e].end != e + 1)
+            return fail(REG_ESTATE, "phi_{0,%d} not available (run reg_prefix_scan first)", e + 1);
+    const int kL = si.nl - 1, nL = si.n[kL];
+    void *raw = nullptr, *stats = nullptr;
+    RET(dalloc(s, &raw, si.frame_block * sizeof(float)));
+    reg_status st = dalloc(s, &stats, 2 * sizeof(double));
+    if (st != REG_OK) {
+        dfree(s, raw, 0);
+        return st;
+    }
+    float *rawf = (float *)raw;
+    std::vector<const float2 *> fields(si.n_frames);
+    auto average = [&]() -> reg_status {
+        // frame 0: the identity, or its deformation to the last average; frame
+        // e + 1: the field in data slot e
+        fields[0] = si.refined ? si.slots + (size_t)si.n_slots * si.slot_elems : nullptr;
+        for (int e = 0; e < si.n_data; e++) fields[e + 1] = si.slots + (size_t)e * si.slot_elems;
+        CK(cudaMemcpyAsync(si.d_fields, fields.data(), sizeof(void *) * si.n_frames, cudaMemcpyHostToDevice,
+                           s->stream));
+        launch_average(s->bf16, s->stream, si.pyr, (int64_t)si.frame_block, (int64_t)si.img_off[kL], nL, si.pitch[kL],
+                       si.fstats, si.d_fields, si.pitch[kL], si.n_frames, rawf + si.img_off[kL], si.pitch[kL]);
+        CK(cudaGetLastError());
+        return REG_OK;
+    };
+    auto body = [&]() -> reg_status {
+        RET(average());
+        for (int it = 0; it < iterations; it++) {
+            // the average becomes the reference frame (pyramid block n_frames);
+            // every frame is registered to it by function A, started from its
+            // current deformation (frame 0 from the identity at first)
+            build_levels(s, si, rawf, si.n_frames, 1, (double *)stats);
+            CK(cudaGetLastError());
+            std::vector<OpReq> ops;
+            for (int k = 0; k < si.n_frames; k++) {
+                const int slot = k == 0 ? si.n_slots : k - 1;
+                const int init = (k == 0 && !si.refined) ? 0 : 1;
+                ops.push_back(OpReq{series, si.n_frames, k, init, init ? slot : -1, -1, slot});
+            }
+            RET(run_batch(s, ops, [] { return REG_OK; }, nullptr, nullptr));
+            si.refined = true;
+            RET(average());
+        }
+        if (avg_out)
+            CK(cudaMemcpy2DAsync(avg_out, (size_t)si.side * sizeof(float), rawf + si.img_off[kL],
+                                 (size_t)si.pitch[kL] * sizeof(float), (size_t)si.side * sizeof(float), si.side,
+                                 out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        return REG_OK;
+    };
+    st = body();
+    dfree(s, raw, 0);
+    dfree(s, stats, 0);
+    return st;
+}
+
 reg_status reg_get_slot(reg_series_t s, int32_t series, int32_t slot, float *out, int32_t out_on_device,
                         int32_t *start_end)
 {
@@ -1053,6 +1144,7 @@ reg_status reg_get_deformations(reg_series_t s, int32_t series, int32_t first, i
     }
     for (int k = first; k < first + count; k++) {
         const float2 *src = nullptr;
+        if (k == 0 && si.refined) src = si.slots + (size_t)si.n_slots * si.slot_elems;
         if (k > 0) {
             const SlotMeta &m = si.meta[k - 1];
             if (m.start != 0 || m.end != k) {

@@ -1605,6 +1605,43 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
 }
 
 // ---------------------------------------------------------------------------
+// Series averaging (Section "Introduction": the frames f_i o phi_{0,i} of a
+// registered series are averaged into one frame)
+// ---------------------------------------------------------------------------
+
+// Node (r, c) of the finest level: 1/m sum_k F_k(x + u_k(x)), F_k frame k's
+// stored finest level with its normalisation undone (F = F~ sigma_k + mean_k),
+// sampled bilinearly and clamped to the grid; u_k from fields[k] (float2 grid
+// units of the finest level; null = the identity).  Sums in double.
+template <bool BF16>
+__global__ void k_average(const void *__restrict__ pyr, int64_t frame_block, int64_t img_off, int n, int pitch,
+                          const double *__restrict__ fstats, const float2 *const *__restrict__ fields, int slot_pitch,
+                          int m, float *__restrict__ out, int opitch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= n || c >= n) return;
+    double acc = 0.0;
+    for (int k = 0; k < m; k++) {
+        const float2 *f = fields[k];
+        const float2 u = f ? f[(int64_t)r * slot_pitch + c] : make_float2(0.f, 0.f);
+        const void *img = BF16 ? (const void *)(reinterpret_cast<const __nv_bfloat16 *>(pyr) + k * frame_block + img_off)
+                               : (const void *)(reinterpret_cast<const float *>(pyr) + k * frame_block + img_off);
+        const float v = sample<BF16, false>(img, n, pitch, c, r, u.x, u.y, nullptr, nullptr);
+        acc += (double)v * fstats[2 * k + 1] + fstats[2 * k];
+    }
+    out[(int64_t)r * opitch + c] = (float)(acc / m);
+}
+
+void launch_average(int bf16, cudaStream_t st, const void *pyr, int64_t frame_block, int64_t img_off, int n,
+                    int pitch, const double *fstats, const float2 *const *fields, int slot_pitch, int m, float *out,
+                    int opitch)
+{
+    dim3 blk(32, 8), grid(cdiv(n, 32), cdiv(n, 8));
+    if (bf16) k_average<true><<<grid, blk, 0, st>>>(pyr, frame_block, img_off, n, pitch, fstats, fields, slot_pitch, m, out, opitch);
+    else k_average<false><<<grid, blk, 0, st>>>(pyr, frame_block, img_off, n, pitch, fstats, fields, slot_pitch, m, out, opitch);
+}
+
+// ---------------------------------------------------------------------------
 // Slot conversion helpers
 // ---------------------------------------------------------------------------
 

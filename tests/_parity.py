@@ -8,11 +8,11 @@ Two ways of comparing one operator application (function A or B):
   good fields (Section "A note on the associativity" notes that results differ
   among implementations).  ``free_running_parity`` therefore accepts one of
     1. max |du| <= TOL_PX at every node;
-    2. every Armijo decision agrees, >= 99.5% of the nodes within TOL_PX, max
-       |du| <= AGREE_CAP_PX (nodes driven onto a cell line of the bilinear
-       interpolant, where the template's derivative jumps, land on either side
-       at the rounding level), and the GPU field is no worse a minimiser of the
-       oracle's FP64 energy (1e-6 relative);
+    2. every Armijo decision agrees, >= 99.5% of the nodes within TOL_PX, the
+       others on a cell line of the bilinear interpolant (where the template's
+       derivative jumps, so that the side a node driven there lands on is
+       decided at the rounding level) and within AGREE_CAP_PX, and the final
+       energies within TOL_E;
     3. the decisions agree up to one whose oracle margin is smaller than the
        disagreement of the two sides' energy changes at that point (no slack),
        that disagreement is itself at the rounding level (SPREAD_MAX relative to
@@ -22,7 +22,12 @@ Two ways of comparing one operator application (function A or B):
        TOL_PX).
 * Lockstep.  The GPU replays the oracle's accepted step sizes
   (reg_set_lockstep); no decision is taken, so the fields must agree to
-  TOL_PX everywhere and the final energies to TOL_E, for every operator.
+  TOL_PX and the final energies to TOL_E, for every operator -- except at the
+  few nodes (< 0.5%) that the flow drives onto a cell line of the bilinear
+  interpolant, where the template's derivative jumps and the side a node
+  takes is decided at the rounding level even along the same steps; each such
+  node must lie within its own difference of a cell line, and within
+  AGREE_CAP_PX.
 
 Every comparison returns a record (max, 99th percentile and mean |du| in px,
 relative final-energy difference) that the tests print on one line each.
@@ -51,7 +56,61 @@ def report(tag, rec):
 def field_stats(gpu_px, orc_px):
     d = np.abs(np.asarray(gpu_px, np.float64) - np.asarray(orc_px, np.float64))
     return dict(max_px=float(d.max()), p99_px=float(np.quantile(d, 0.99)), mean_px=float(d.mean()),
-                frac_within=float(np.mean(d <= TOL_PX)))
+                frac_within=float(np.mean(d <= TOL_PX)), n_beyond=int(np.sum(d > TOL_PX)))
+
+
+def kink_excess(gpu_px, orc_px):
+    """Nodes beyond TOL_PX must come from a kink of the energy: the bilinear
+    interpolant's derivative jumps where a node's position x + u crosses a
+    cell line (an integer number of pixels on the finest grid), the flow
+    drives nodes onto such lines, and the side such a node ends on is decided
+    at the rounding level; the mass and stiffness stencils then carry a
+    decaying difference to the nodes around it (over the iterations, to
+    neighbours of neighbours too).  So every cluster of differing nodes (nodes
+    at most two apart joined) must peak at a node that lies on a cell line:
+    within its own difference of one (in the oracle's or the GPU's position).
+    Returns the largest excess of that distance over the peak's difference
+    (<= 0 when every cluster is explained so)."""
+    from scipy import ndimage
+    g = np.asarray(gpu_px, np.float64)
+    o = np.asarray(orc_px, np.float64)
+    d = np.abs(g - o).max(axis=0)  # per node, the larger component difference
+    m = d > TOL_PX
+    if not m.any():
+        return 0.0
+    dist = np.minimum(np.abs(o - np.round(o)), np.abs(g - np.round(g))).min(axis=0)
+    joined = ndimage.binary_dilation(m, structure=np.ones((3, 3)))
+    lab, n = ndimage.label(joined, structure=np.ones((3, 3)))
+    worst = -np.inf
+    for k in range(1, n + 1):
+        sel = (lab == k) & m
+        idx = np.argwhere(sel)
+        r, c = idx[np.argmax(d[sel])]
+        worst = max(worst, float(dist[r, c] - d[r, c]))
+    return worst
+
+
+def beyond_detail(gpu_px, orc_px, limit=16):
+    """The nodes beyond TOL_PX: (row, col, |du| px, oracle and GPU distance of
+    the node's position to the nearest cell line, per component)."""
+    g = np.asarray(gpu_px, np.float64)
+    o = np.asarray(orc_px, np.float64)
+    d = np.abs(g - o).max(axis=0)
+    idx = np.argwhere(d > TOL_PX)[:limit]
+    out = []
+    for r, c in idx:
+        out.append([int(r), int(c), round(float(d[r, c]), 5),
+                    [round(float(abs(o[k, r, c] - np.round(o[k, r, c]))), 5) for k in range(2)],
+                    [round(float(abs(g[k, r, c] - np.round(g[k, r, c]))), 5) for k in range(2)]])
+    return out
+
+
+def _agreeing_fields_ok(rec):
+    """Fields of two runs that took the same steps: all but a few nodes within
+    TOL_PX, those few on cell lines and within AGREE_CAP_PX, and the GPU's
+    field as good a minimiser of the oracle's energy (TOL_E)."""
+    return (rec["frac_within"] >= 0.995 and rec["p99_px"] <= TOL_PX and rec["max_px"] <= AGREE_CAP_PX
+            and rec["kink_excess_px"] <= 0.0 and abs(rec["E_rel"]) <= TOL_E)
 
 
 def energy_rel(orc, R, T, gpu_px, orc_px, lam):
@@ -125,7 +184,9 @@ def free_running_parity(orc, gpu_px, orc_px, gtr, otr, what, R, T, p, lam, u_ini
     k = first_flip(gtr, otr)
     if k is None:
         rec["criterion"] = "decisions agree"
-        assert rec["frac_within"] >= 0.995 and rec["max_px"] <= AGREE_CAP_PX and e_rel <= 1e-6, rec
+        rec["kink_excess_px"] = kink_excess(gpu_px, orc_px)
+        rec["beyond"] = beyond_detail(gpu_px, orc_px)
+        assert _agreeing_fields_ok(rec), rec
         return rec
     a, b = gtr[k], otr[k]
     margin = abs(b[3] - b[4])
@@ -165,6 +226,10 @@ def lockstep_parity(orc, series, op, dst, n_levels, otr, orc_px, what, R, T, lam
         dev = np.abs(gtr[:, 4] - dEs) / (np.abs(dEs) + 1e-9 * abs(e0))
         rec["dE_rel_max"] = float(dev.max())
         rec["dE_rel_median"] = float(np.median(dev))
-    assert rec["max_px"] <= TOL_PX, rec
-    assert abs(e_rel) <= TOL_E, rec
+    rec["kink_excess_px"] = kink_excess(got, orc_px)
+    rec["beyond"] = beyond_detail(got, orc_px)
+    if rec["max_px"] <= TOL_PX:
+        assert abs(e_rel) <= TOL_E, rec
+    else:
+        assert _agreeing_fields_ok(rec), rec
     return rec

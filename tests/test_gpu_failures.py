@@ -29,7 +29,9 @@ def test_step_budget_times_out_and_handle_recovers(reg, syn):
             s.apply_operator_batch([(0, -1, -1, 0, 0, 1)])  # needs far more than 8 device steps
         assert e.value.code == reg.ETIMEOUT
         st, it = s.apply_operator_batch([(0, -1, -1, 2, 2, 3)])
-        assert int(st[0]) in (reg.OP_ZERO_GRADIENT, reg.OP_CONVERGED), st
+        # identical frames: NCC rounds a few ulp below 1, so the search either
+        # finds no decrease (stalled) or sees a zero slope
+        assert int(st[0]) in (reg.OP_ZERO_GRADIENT, reg.OP_CONVERGED, reg.OP_LS_STALLED), st
         u, se = s.get_slot(2)
         assert se == (2, 3) and np.abs(u).max() < 1e-6
     # the same operator with the default budget finishes normally
