@@ -101,18 +101,42 @@ typedef struct reg_params {
     int32_t init_levels;      /* 0 or 1..n_levels, see above */
     double learned_fallback_px; /* see above; 0: never fall back */
     reg_allocator allocator;
+    double smooth;            /* H1-type smoother width s in grid spacings of each level; 0: lumped L2 flow */
 } reg_params;
 
 #define REG_FLAG_PROFILE 1    /* time kernel families with CUDA events */
+/* Rigid variant (Definition "Rigid transformation": phi(x) = R(alpha) x + t,
+ * rotation about the origin of Omega, t in Omega units).  A handle created
+ * with this flag registers with the three-parameter operator: function A runs
+ * gradient descent on theta = (alpha, t0, t1) (no smoother, Section "Gradient
+ * flow") with the same Armijo rule on every pyramid level, carrying theta from
+ * level to level unchanged (a rigid deformation is not restricted or
+ * prolongated, Algorithm "Multilevel gradient flow"); the energy is E at
+ * phi, whose regulariser is 2 lambda (1 - cos alpha) for a rigid map; function
+ * B starts from the composition of the two rigid maps.  Slots hold the
+ * parameters (reg_get_rigid / reg_set_rigid) and the field they define, so
+ * reg_get_slot, reg_get_deformations and reg_average_series work unchanged.
+ * The operator's iterations are driven from the host: each round launches one
+ * evaluation over all active operators of the batch. */
+#define REG_FLAG_RIGID 2
 
 /* Replace the handle's reg_params.flags (REG_FLAG_*); takes effect at the next
  * batch.  With REG_FLAG_PROFILE the step kernels are launched one by one
  * between CUDA events instead of as the captured graph. */
 reg_status reg_set_flags(reg_series_t s, int32_t flags);
 
+/* The smoother A of the gradient flow d = -A^{-1} E'[phi] (Section "Gradient
+ * flow": A is selected to smooth in the non-rigid registration).  smooth = 0:
+ * A = diag(w), the lumped mass (an L2 flow; the default).  smooth = s > 0: A is
+ * the tensor-product H1 Gram matrix M_s (x) M_s with M_s = M1 + (s h)^2 / 2 K1
+ * (M1, K1 the 1D P1 mass and stiffness, h the level's grid spacing), whose
+ * inverse is a tridiagonal solve along every row and then every column; two
+ * more kernels per gradient step.  The diagnostic calls reg_eval_direction and
+ * reg_eval_trials keep the lumped direction. */
+
 /* Fills *p with the defaults: n_levels 3, iter_max 50, epsilon 1e-7,
  * lambda 10, sigma 0.5, tau_init 1, tau_max 1e4, tau_min 1e-12, F32 storage,
- * 4 trials per pass, init_levels 0, learned_fallback_px 2. */
+ * 4 trials per pass, init_levels 0, learned_fallback_px 2, smooth 0. */
 void reg_default_params(reg_params *p);
 
 /* One operator application (Section "Registration for series of images").
@@ -224,6 +248,14 @@ reg_status reg_get_slot(reg_series_t s, int32_t series, int32_t slot, float *out
  * the identity (field ignored). */
 reg_status reg_set_slot(reg_series_t s, int32_t series, int32_t slot, const float *field, int32_t on_device,
                         int32_t start, int32_t end);
+
+/* Rigid handles (REG_FLAG_RIGID): the parameters (alpha in radians, t0, t1 in
+ * Omega units) of the rigid map held in a slot, and its (start, end) pair;
+ * reg_set_rigid sets a slot to phi_{start,end} given by its parameters (the
+ * slot's field follows).  REG_ESTATE on a non-rigid handle. */
+reg_status reg_get_rigid(reg_series_t s, int32_t series, int32_t slot, double *theta, int32_t *start_end);
+reg_status reg_set_rigid(reg_series_t s, int32_t series, int32_t slot, const double *theta, int32_t start,
+                         int32_t end);
 
 /* Number of slots of a series (N-1 data slots for N frames plus the
  * auxiliary slots the largest schedule needs). */

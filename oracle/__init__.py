@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int32), ("iter_max", ctypes.c_int32),
                 ("epsilon", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("armijo_sigma", ctypes.c_double), ("tau_init", ctypes.c_double),
-                ("tau_max", ctypes.c_double), ("tau_min", ctypes.c_double)]
+                ("tau_max", ctypes.c_double), ("tau_min", ctypes.c_double), ("smooth", ctypes.c_double)]
 
 
 class LevelStats(ctypes.Structure):
@@ -44,11 +44,12 @@ class LevelStats(ctypes.Structure):
 
 
 def params(n_levels=3, iter_max=50, epsilon=1e-7, lam=0.01, armijo_sigma=0.5,
-           tau_init=1.0, tau_max=1e4, tau_min=1e-12) -> Params:
+           tau_init=1.0, tau_max=1e4, tau_min=1e-12, smooth=0.0) -> Params:
     """Method parameters: pyramid depth, iteration cap and epsilon (Algorithm
     "Multilevel gradient flow" stopping criteria), regulariser weight lambda,
-    Armijo sigma = 0.5 and the step-size bounds (Section "Gradient flow")."""
-    return Params(n_levels, iter_max, epsilon, lam, armijo_sigma, tau_init, tau_max, tau_min)
+    Armijo sigma = 0.5 and the step-size bounds (Section "Gradient flow");
+    smooth > 0 selects the H1-type smoother of that width (grid spacings)."""
+    return Params(n_levels, iter_max, epsilon, lam, armijo_sigma, tau_init, tau_max, tau_min, smooth)
 
 
 def build(force: bool = False) -> str:
@@ -91,6 +92,8 @@ def _load():
         "orc_apply_batch": ([i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp], None),
         "orc_set_trace": ([vp, ctypes.c_long], None),
         "orc_average": ([i, vp, vp, i, vp], None),
+        "orc_smooth_apply": ([i, ctypes.c_double, vp, vp], None),
+        "orc_smooth_matvec": ([i, ctypes.c_double, vp, vp], None),
         "orc_rigid_field": ([vp, i, vp], None),
         "orc_rigid_energy": ([vp, vp, i, vp, ctypes.c_double], ctypes.c_double),
         "orc_rigid_gradient": ([vp, vp, i, vp, ctypes.c_double, vp], None),
@@ -189,6 +192,22 @@ def gradient(R, T, u, lam):
     g = np.empty_like(u)
     _load().orc_gradient(R.ctypes.data, T.ctypes.data, R.shape[0], u.ctypes.data, lam, g.ctypes.data)
     return g
+
+
+def smooth_apply(g, smooth):
+    """d = -(M_s (x) M_s)^{-1} g for a nodal gradient g (2, n, n)."""
+    g = _c(g)
+    d = np.empty_like(g)
+    _load().orc_smooth_apply(g.shape[1], smooth, g.ctypes.data, d.ctypes.data)
+    return d
+
+
+def smooth_matvec(v, smooth):
+    """(M_s (x) M_s) v for one plane v (n, n)."""
+    v = _c(v)
+    out = np.empty_like(v)
+    _load().orc_smooth_matvec(v.shape[0], smooth, v.ctypes.data, out.ctypes.data)
+    return out
 
 
 def solve_level(R, T, u, p: Params):

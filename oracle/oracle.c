@@ -345,9 +345,70 @@ void orc_gradient(const double *R, const double *T, int n, const double *u, doub
 /* Gradient flow with the Armijo rule with widening (Section "Gradient flow")*/
 /* ------------------------------------------------------------------------- */
 
+/* ------------------------------------------------------------------------- */
+/* H1-type smoother (Section "Gradient flow": A^{-1} smooths the first        */
+/* variation in the non-rigid registration)                                   */
+/* ------------------------------------------------------------------------- */
+
+/* 1D H1 Gram matrix M_s = M1 + (s^2/2) K1 with s = smooth * h (the smoother's
+ * width in grid spacings of the level): int psi_i psi_j + s^2/2 int psi_i' psi_j'. */
+static _Thread_local double m1s_smooth;
+static double m1s(int i, int j, int n, double h)
+{
+    double s = m1s_smooth * h;
+    return m1(i, j, n, h) + 0.5 * s * s * k1(i, j, n, h);
+}
+
+/* out = (M_s (x) M_s) v: the tensor-product H1 Gram matrix applied to one
+ * plane of nodal values. */
+void orc_smooth_matvec(int n, double smooth, const double *v, double *out)
+{
+    m1s_smooth = smooth;
+    kron_apply(m1s, m1s, v, n, out);
+}
+
+/* Solve the tridiagonal 1D system M_s x = b along one line (stride st): the
+ * plain Thomas elimination. */
+static void smooth_line(int n, double h, double smooth, const double *b, double *x, size_t st)
+{
+    double s = smooth * h, c = 0.5 * s * s;
+    double *cp = dalloc((size_t)n), *dp = dalloc((size_t)n);
+    for (int i = 0; i < n; i++) {
+        double diag = m1(i, i, n, h) + c * k1(i, i, n, h);
+        double lo = i > 0 ? m1(i, i - 1, n, h) + c * k1(i, i - 1, n, h) : 0.0;
+        double up = i < n - 1 ? m1(i, i + 1, n, h) + c * k1(i, i + 1, n, h) : 0.0;
+        double den = diag - (i > 0 ? lo * cp[i - 1] : 0.0);
+        cp[i] = up / den;
+        dp[i] = (b[(size_t)i * st] - (i > 0 ? lo * dp[i - 1] : 0.0)) / den;
+    }
+    x[(size_t)(n - 1) * st] = dp[n - 1];
+    for (int i = n - 2; i >= 0; i--) x[(size_t)i * st] = dp[i] - cp[i] * x[(size_t)(i + 1) * st];
+    free(cp);
+    free(dp);
+}
+
+/* d = -(M_s (x) M_s)^{-1} g for both planes of g: since the matrix is a
+ * Kronecker product, its inverse is M_s^{-1} (x) M_s^{-1}, i.e. one 1D solve
+ * along every row, then one along every column. */
+void orc_smooth_apply(int n, double smooth, const double *g, double *d)
+{
+    double h = 1.0 / (n - 1);
+    size_t N = (size_t)n * n;
+    double *t = dalloc(N);
+    for (int ch = 0; ch < 2; ch++) {
+        const double *gc = g + ch * N;
+        double *dc = d + ch * N;
+        for (int r = 0; r < n; r++) smooth_line(n, h, smooth, gc + (size_t)r * n, t + (size_t)r * n, 1);
+        for (int c = 0; c < n; c++) smooth_line(n, h, smooth, t + c, dc + c, (size_t)n);
+        for (size_t i = 0; i < N; i++) dc[i] = -dc[i];
+    }
+    free(t);
+}
+
 /* Forward Euler step phi^{k+1} = phi^k - tau A^{-1} E'[phi^k] with the
  * smoother A = diag(w) (lumped mass, an L2 gradient flow), i.e. direction
- * d = -g / w.  Step size: start from the previous accepted tau (tau_init at the
+ * d = -g / w, or with p->smooth > 0 the tensor-product H1 Gram matrix
+ * A = M_s (x) M_s (orc_smooth_apply).  Step size: start from the previous accepted tau (tau_init at the
  * start of the level); if the Armijo condition
  *     E(u + tau d) - E(u) <= sigma tau g^T d
  * holds, keep doubling while it still holds and 2 tau <= tau_max; otherwise
@@ -369,10 +430,10 @@ int orc_solve_level(const double *R, const double *T, int n, double *u, const or
         orc_gradient(R, T, n, u, p->lambda, g);
         iters++;
         double slope = 0.0;
-        for (size_t i = 0; i < 2 * N; i++) {
-            d[i] = -g[i] / w[i % N];
-            slope += g[i] * d[i];
-        }
+        if (p->smooth > 0.0) orc_smooth_apply(n, p->smooth, g, d);
+        else
+            for (size_t i = 0; i < 2 * N; i++) d[i] = -g[i] / w[i % N];
+        for (size_t i = 0; i < 2 * N; i++) slope += g[i] * d[i];
         if (!(slope < 0.0)) {
             status = (slope == 0.0) ? ORC_ZERO_GRADIENT : ORC_NONFINITE;
             break;

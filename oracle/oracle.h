@@ -14,6 +14,7 @@ typedef struct orc_params {
     double tau_init;
     double tau_max;
     double tau_min;
+    double smooth;  /* H1-type smoother width in grid spacings (0: lumped-mass L2 flow) */
 } orc_params;
 
 typedef struct orc_level_stats {
@@ -56,4 +57,6 @@ int orc_rigid_solve_level(const double *R, const double *T, int n, double *theta
 int orc_rigid_register(const double *R, const double *T, int L, const double *theta_init, const orc_params *p,
                        double *theta_out, orc_level_stats *st);
 void orc_rigid_compose(const double *a, const double *b, double *out);
+void orc_smooth_apply(int n, double smooth, const double *g, double *d);
+void orc_smooth_matvec(int n, double smooth, const double *v, double *out);
 #endif

@@ -34,6 +34,7 @@ SCAN_NAMES = {SERIAL: "serial", SKLANSKY: "sklansky", KOGGE_STONE: "kogge_stone"
               LADNER_FISCHER: "ladner_fischer"}
 STORAGE_F32, STORAGE_BF16 = 0, 1
 FLAG_PROFILE = 1
+FLAG_RIGID = 2
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -49,7 +50,7 @@ class Params(ctypes.Structure):
                 ("tau_max", ctypes.c_double), ("tau_min", ctypes.c_double), ("storage", ctypes.c_int32),
                 ("trials_per_pass", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("init_levels", ctypes.c_int32), ("learned_fallback_px", ctypes.c_double),
-                ("allocator", Allocator)]
+                ("allocator", Allocator), ("smooth", ctypes.c_double)]
 
 
 class OpDesc(ctypes.Structure):
@@ -102,6 +103,8 @@ def _load():
         "reg_set_lockstep": ([vp, i32, i32, vp, vp], ctypes.c_int),
         "reg_set_flags": ([vp, i32], ctypes.c_int),
         "reg_average_series": ([vp, i32, i32, vp, i32], ctypes.c_int),
+        "reg_get_rigid": ([vp, i32, i32, vp, vp], ctypes.c_int),
+        "reg_set_rigid": ([vp, i32, i32, vp, i32, i32], ctypes.c_int),
         "reg_eval_energy_noalloc": ([vp, vp, i32, i32, vp, d, vp, i32, vp], ctypes.c_int),
         "reg_destroy_series": ([vp], ctypes.c_int),
         "reg_cnn_num_params": ([], i64),
@@ -486,6 +489,50 @@ class Series:
             out = np.empty((side, side), np.float32)
         ptr, on_dev = _ptr(out)
         _check(_load().reg_average_series(self.h, series, iterations, ptr, on_dev))
+        return out
+
+    def n_slots(self, series=0):
+        return num_slots(self.h, series)
+
+    def get_slot_device(self, slot, series=0):
+        """A slot's field as a CUDA tensor (2, side+1, side+1), pixels."""
+        torch = _torch()
+        side = self.sides[series]
+        out = torch.empty((2, side + 1, side + 1), dtype=torch.float32, device="cuda")
+        se = np.empty(2, np.int32)
+        _check(_load().reg_get_slot(self.h, series, slot, out.data_ptr(), 1, se.ctypes.data))
+        return out
+
+    def set_slot_device(self, slot, field, start, end, series=0):
+        """Set a slot from a CUDA tensor (2, side+1, side+1), pixels."""
+        f = field.contiguous()
+        _check(_load().reg_set_slot(self.h, series, slot, f.data_ptr(), 1, start, end))
+
+    def copy_slot(self, src, dst, start, end, series=0):
+        self.set_slot_device(dst, self.get_slot_device(src, series), start, end, series)
+
+    def schedule_ops(self, kind, n, chunks=1, global_kind=KOGGE_STONE):
+        return schedule(kind, n, chunks, global_kind)
+
+    def get_rigid(self, slot, series=0):
+        """Rigid handles: (theta (alpha, t0, t1 in Omega units), (start, end)) of a slot."""
+        th = np.empty(3)
+        se = np.empty(2, np.int32)
+        _check(_load().reg_get_rigid(self.h, series, slot, th.ctypes.data, se.ctypes.data))
+        return th, (int(se[0]), int(se[1]))
+
+    def set_rigid(self, slot, theta, start, end, series=0):
+        th = np.ascontiguousarray(theta, np.float64)
+        _check(_load().reg_set_rigid(self.h, series, slot, th.ctypes.data, start, end))
+
+    def rigid_params(self, series=0):
+        """Rigid handles after prefix_scan: (n_frames, 3) parameters of phi_{0,k}
+        (row 0 the identity)."""
+        out = np.zeros((self.counts[series], 3))
+        for k in range(1, self.counts[series]):
+            th, se = self.get_rigid(k - 1, series)
+            assert se == (0, k), se
+            out[k] = th
         return out
 
     def get_slot(self, slot, series=0):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -31,10 +32,14 @@ __global__ void k_plan(BatchDev);
 __global__ void k_prolong(BatchDev);
 void launch_grad(int bf16, int grid, cudaStream_t st, const BatchDev &b);
 void launch_trial(int bf16, int J, int grid, cudaStream_t st, const BatchDev &b);
+void launch_smooth(int grid, cudaStream_t st, const BatchDev &b);
 int step_blocks_per_sm(int which, int J);
 __global__ void k_control(BatchDev);
 __global__ void k_slot_to_planes(const float2 *, int, int, float *);
 __global__ void k_planes_to_slot(const float *, int, float2 *, int);
+void launch_rigid(int bf16, int tiles, int n_ops, cudaStream_t st, const RigidLevel *lv, const RigidReq *req,
+                  double *part, double *sums);
+void launch_rigid_fill(const RigidReq &q, int n, float2 *slot, int pitch, cudaStream_t st);
 void launch_average(int bf16, cudaStream_t st, const void *pyr, int64_t frame_block, int64_t img_off, int n,
                     int pitch, const double *fstats, const float2 *const *fields, int slot_pitch, int m, float *out,
                     int opitch);
@@ -89,6 +94,7 @@ struct SeriesInfo {
     // deformation to it; fstats: FE mean and sigma of every frame's finest level
     // (n_frames + 1 pairs), to undo the normalisation of the stored pyramid.
     double *fstats = nullptr;
+    std::vector<std::array<double, 3>> rigid;  // rigid handles: the slots' parameters (alpha, t0, t1 in Omega units)
     const float2 **d_fields = nullptr;    // per frame: its deformation field (null: identity)
     bool refined = false;                 // slots hold deformations to the average frame
     std::vector<size_t> ws_off;           // per level: offset (bytes) of U0 within an op workspace
@@ -172,6 +178,16 @@ struct reg_series {
     std::vector<double> lock_taus;
     double *d_lock = nullptr;
     size_t d_lock_cap = 0;
+    // H1-type smoother: Thomas pivots per level l (2^l + 1 nodes), partial sums
+    float2 *d_smtab[REG_TILE_LEVELS] = {nullptr};
+    double *d_partS = nullptr;
+    int sm_rch = 0, sm_cch = 0, grid_S = 0;
+    // rigid variant buffers
+    RigidLevel *d_rlv = nullptr, *h_rlv = nullptr;
+    RigidReq *d_rreq = nullptr, *h_rreq = nullptr;
+    double *d_rpart = nullptr, *d_rsums = nullptr, *h_rsums = nullptr;
+    int rcap_ops = 0;
+    int64_t rcap_part = 0;
     // totals for reports
     int64_t tot_steps = 0, tot_ops = 0, tot_iters = 0, tot_trials = 0, tot_evals = 0;
 };
@@ -256,6 +272,14 @@ BatchDev make_batch(reg_series *s)
     b.iter_max = s->p.iter_max;
     b.J = s->p.trials_per_pass;
     b.bf16 = s->bf16;
+    if (s->p.smooth > 0.0) {
+        b.smooth = 1;
+        b.partS = s->d_partS;
+        b.rch = s->sm_rch;
+        b.cch = s->sm_cch;
+        const double sg = s->p.smooth;
+        b.sm_a = (float)(1.0 / 6.0 - 0.5 * sg * sg);
+    }
     return b;
 }
 
@@ -287,6 +311,7 @@ void fill_level(const reg_series *s, LevelDesc &L, int n, int pitch)
     const double h = 1.0 / (n - 1);
     L.h2d = h * h;
     L.h2 = (float)L.h2d;
+    L.sm_tab = s->d_smtab[level_of(n)];
 }
 
 // Batch buffers for n_ops operators with ws_total bytes of workspace and up to
@@ -303,6 +328,10 @@ reg_status ensure_capacity(reg_series *s, int n_ops, size_t ws_total, int64_t it
         RET(track(s, (void **)&s->d_ops, sizeof(OpDesc) * c));
         RET(track(s, (void **)&s->d_st, sizeof(OpState) * c));
         RET(track(s, (void **)&s->d_lists, sizeof(int) * (6 * c + 3)));
+        if (s->p.smooth > 0.0) {
+            untrack(s, s->d_partS);
+            RET(track(s, (void **)&s->d_partS, sizeof(double) * 2 * (size_t)s->sm_cch * c));
+        }
         CK(cudaMallocHost((void **)&s->h_ops, sizeof(OpDesc) * c));
         s->cap_ops = c;
         changed = true;
@@ -345,6 +374,7 @@ reg_status build_graph(reg_series *s)
     for (int k = 0; k < GRAPH_STEPS; k++) {
         k_prolong<<<s->grid_P, REG_THREADS, 0, cs>>>(b);
         launch_grad(s->bf16, s->grid_G, cs, b);
+        if (b.smooth) launch_smooth(s->grid_S, cs, b);
         launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, cs, b);
         k_control<<<std::min(s->cap_ops, 2048), 256, 0, cs>>>(b);
         k_plan<<<1, 1024, 0, cs>>>(b);
@@ -385,9 +415,14 @@ const void *img_ptr(reg_series *s, const SeriesInfo &si, int frame, int k)
 // Run one batch of operator applications.  pre_iter runs on the stream after
 // all operands have been read (composition) and before any result is written.
 template <class F>
+reg_status run_batch_rigid(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, int32_t *status_out,
+                           int32_t *iters_out);
+
+template <class F>
 reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, int32_t *status_out,
                      int32_t *iters_out)
 {
+    if (s->p.flags & REG_FLAG_RIGID) return run_batch_rigid(s, ops, pre_iter, status_out, iters_out);
     int n = (int)ops.size();
     if (n == 0) return pre_iter();
     // each op's workspace at its own offset (series of different sides share a
@@ -496,6 +531,7 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
                 k_prolong<<<s->grid_P, REG_THREADS, 0, s->stream>>>(b);
                 cudaEventRecord(s->ev[k][F_G], s->stream);
                 launch_grad(s->bf16, s->grid_G, s->stream, b);
+                if (b.smooth) launch_smooth(s->grid_S, s->stream, b);  // timed with the gradient family
                 cudaEventRecord(s->ev[k][F_T], s->stream);
                 launch_trial(s->bf16, s->p.trials_per_pass, s->grid_T, s->stream, b);
                 cudaEventRecord(s->ev[k][F_C], s->stream);
@@ -537,6 +573,321 @@ reg_status run_batch(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, i
     return REG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Rigid variant (Definition "Rigid transformation"): function A on the three
+// parameters theta = (alpha, t0, t1) of phi(x) = R(alpha) x + t, by gradient
+// descent (no smoother, Section "Gradient flow") with the Armijo rule with
+// widening on every level of the pyramid; theta is carried from level to
+// level unchanged (Algorithm "Multilevel gradient flow": a rigid deformation
+// is not restricted or prolongated).  The energy is E of the non-rigid
+// method at phi; for a rigid map the regulariser is 2 lambda (1 - cos alpha)
+// exactly.  All operators of a batch advance level by level together; each
+// round evaluates, for every active operator, up to trials_per_pass parameter
+// sets (energy sums) or the gradient, in one launch over all their tiles, and
+// the FP64 state machine of each operator runs on the host.
+// ---------------------------------------------------------------------------
+struct RigidState {
+    std::array<double, 3> th{}, d{}, btheta{};
+    double E = 0, S1 = 0, S2 = 0, S3 = 0, ncc = 0, sig = 0, slope = 0, tau = 1, btau = 0, bE = 0, sh_tau = 0;
+    double bS[3] = {0, 0, 0};
+    int phase = 0;  // 0 start energy, 1 gradient, 2 trials, 3 level done
+    int iter = 0, iters_total = 0, search = 0, ntr = 0, status = OPST_MAXITER, nonfinite = 0;
+    double trial_tau[REG_MAX_TRIALS];
+};
+
+inline std::array<double, 3> rigid_compose_h(const std::array<double, 3> &a, const std::array<double, 3> &b)
+{
+    // phi_b o phi_a = R(a0 + b0) x + R(b0) ta + tb (phi_a applied first)
+    const double cb = cos(b[0]), sb = sin(b[0]);
+    return {a[0] + b[0], cb * a[1] - sb * a[2] + b[1], sb * a[1] + cb * a[2] + b[2]};
+}
+
+inline RigidReq rigid_req(const std::array<double, 3> &th, int n)
+{
+    RigidReq q;
+    memset(&q, 0, sizeof(q));
+    const double nm1 = n - 1;
+    const double sh = sin(0.5 * th[0]);
+    q.a = (float)(-2.0 * sh * sh);  // cos(alpha) - 1 without cancellation
+    q.b = (float)sin(th[0]);
+    q.tx = (float)(th[1] * nm1);
+    q.ty = (float)(th[2] * nm1);
+    q.ca = (float)cos(th[0]);
+    q.sa = q.b;
+    q.h = (float)(1.0 / nm1);
+    q.nm1 = (float)nm1;
+    return q;
+}
+
+reg_status rigid_capacity(reg_series *s, int n_ops, int64_t tiles)
+{
+    if (n_ops > s->rcap_ops) {
+        const int c = std::max(n_ops, 2 * s->rcap_ops);
+        untrack(s, s->d_rlv);
+        untrack(s, s->d_rreq);
+        untrack(s, s->d_rsums);
+        if (s->h_rlv) cudaFreeHost(s->h_rlv);
+        if (s->h_rreq) cudaFreeHost(s->h_rreq);
+        if (s->h_rsums) cudaFreeHost(s->h_rsums);
+        RET(track(s, (void **)&s->d_rlv, sizeof(RigidLevel) * c));
+        RET(track(s, (void **)&s->d_rreq, sizeof(RigidReq) * REG_MAX_TRIALS * c));
+        RET(track(s, (void **)&s->d_rsums, sizeof(double) * RIGID_SUMS * c));
+        CK(cudaMallocHost((void **)&s->h_rlv, sizeof(RigidLevel) * c));
+        CK(cudaMallocHost((void **)&s->h_rreq, sizeof(RigidReq) * REG_MAX_TRIALS * c));
+        CK(cudaMallocHost((void **)&s->h_rsums, sizeof(double) * RIGID_SUMS * c));
+        s->rcap_ops = c;
+    }
+    if ((int64_t)n_ops * tiles > s->rcap_part) {
+        const int64_t c = std::max<int64_t>((int64_t)n_ops * tiles, 2 * s->rcap_part);
+        untrack(s, s->d_rpart);
+        RET(track(s, (void **)&s->d_rpart, sizeof(double) * RIGID_SUMS * c));
+        s->rcap_part = c;
+    }
+    return REG_OK;
+}
+
+// Trial step sizes of one Armijo search pass, in the order the sequential rule
+// would try them (the same order as the non-rigid device state machine).
+void rigid_init_trials(RigidState &r, const reg_params &p)
+{
+    int k = 0;
+    r.trial_tau[k++] = r.tau;
+    double up = r.tau, dn = r.tau;
+    while (k < p.trials_per_pass) {
+        if (2.0 * up <= p.tau_max) { up *= 2.0; r.trial_tau[k++] = up; }
+        if (k < p.trials_per_pass && 0.5 * dn >= p.tau_min) { dn *= 0.5; r.trial_tau[k++] = dn; }
+        if (2.0 * up > p.tau_max && 0.5 * dn < p.tau_min) break;
+    }
+    r.ntr = k;
+    r.search = SEARCH_INIT;
+}
+
+double rigid_energy(const reg_params &p, double h2, const double *S, double alpha, double &S1, double &S2, double &S3,
+                    double &ncc, double &sig)
+{
+    S1 = h2 * S[0];
+    S2 = h2 * S[1];
+    S3 = h2 * S[2];
+    const double var = S2 - S1 * S1;
+    // A warped template without variance (every sample clamped to one border
+    // value: the map moved the frame off the image) has no NCC; the FP32 sums
+    // leave a spurious variance at their resolution, which would give a huge
+    // NCC.  Such a parameter set has no energy (NaN: a trial is rejected), as
+    // the exact 0/0 in FP64.
+    if (!(var > 1e-6 * S2)) {
+        sig = 0.0;
+        ncc = NAN;
+        return NAN;
+    }
+    sig = sqrt(var);
+    ncc = S3 / sig;
+    return -ncc + 2.0 * p.lambda * (1.0 - cos(alpha));
+}
+
+template <class F>
+reg_status run_batch_rigid(reg_series *s, const std::vector<OpReq> &ops, F pre_iter, int32_t *status_out,
+                           int32_t *iters_out)
+{
+    const int n = (int)ops.size();
+    if (n == 0) return pre_iter();
+    const reg_params &p = s->p;
+    std::vector<RigidState> st(n);
+    int nl = 0;
+    int64_t max_tiles = 1;
+    for (int i = 0; i < n; i++) {
+        const OpReq &o = ops[i];
+        const SeriesInfo &si = s->S[o.series];
+        nl = std::max(nl, si.nl);
+        const int tx = cdiv(si.n[si.nl - 1], 32);
+        max_tiles = std::max<int64_t>(max_tiles, (int64_t)tx * tx);
+        std::array<double, 3> th{0.0, 0.0, 0.0};
+        if (o.init >= 1) th = si.rigid[o.left];
+        if (o.init == 2) th = rigid_compose_h(si.rigid[o.left], si.rigid[o.right]);
+        st[i].th = th;
+    }
+    RET(pre_iter());  // operands read: copies may overwrite them now
+    RET(rigid_capacity(s, n, max_tiles));
+    const int J = std::max(1, std::min(p.trials_per_pass, REG_MAX_TRIALS));
+    int64_t rounds = 0;
+    for (int lvl = 0; lvl < nl; lvl++) {
+        // level descriptors (level index counted from the finest one, so that
+        // series of different depths end on their finest levels together)
+        std::vector<int> act;
+        for (int i = 0; i < n; i++) {
+            const SeriesInfo &si = s->S[ops[i].series];
+            const int k = si.nl - nl + lvl;
+            RigidLevel &L = s->h_rlv[i];
+            if (k < 0) { L.n = 0; continue; }
+            L.n = si.n[k];
+            L.pitch = si.pitch[k];
+            L.T = img_ptr(s, si, ops[i].frame_k, k);
+            L.MR = si.mr + (size_t)ops[i].frame_i * si.frame_block + si.img_off[k];
+            RigidState &r = st[i];
+            r.phase = 0;
+            r.iter = 0;
+            r.tau = p.tau_init;
+            act.push_back(i);
+        }
+        CK(cudaMemcpyAsync(s->d_rlv, s->h_rlv, sizeof(RigidLevel) * n, cudaMemcpyHostToDevice, s->stream));
+        int guard = 0;
+        while (!act.empty()) {
+            if (++guard > 4 * (p.iter_max + 2) * (2 + 48 / J) + 64)
+                return fail(REG_ETIMEOUT, "rigid batch did not finish its level");
+            // requests of this round
+            for (int i = 0; i < n; i++) s->h_rreq[(size_t)i * REG_MAX_TRIALS].n_e = 0;
+            for (int i : act) {
+                RigidState &r = st[i];
+                const int nn = s->h_rlv[i].n;
+                RigidReq *q = s->h_rreq + (size_t)i * REG_MAX_TRIALS;
+                if (r.phase == 0) {
+                    q[0] = rigid_req(r.th, nn);
+                    q[0].n_e = 1;
+                } else if (r.phase == 1) {
+                    q[0] = rigid_req(r.th, nn);
+                    q[0].n_e = 1;
+                    q[0].grad = 1;
+                    q[0].inv_sig = (float)(1.0 / r.sig);
+                    q[0].ncc_over_var = (float)(r.ncc / (r.sig * r.sig));
+                    q[0].tbar = (float)r.S1;
+                } else {
+                    for (int j = 0; j < r.ntr; j++) {
+                        std::array<double, 3> t;
+                        for (int c = 0; c < 3; c++) t[c] = r.th[c] + r.trial_tau[j] * r.d[c];
+                        q[j] = rigid_req(t, nn);
+                    }
+                    q[0].n_e = r.ntr;
+                }
+            }
+            CK(cudaMemcpyAsync(s->d_rreq, s->h_rreq, sizeof(RigidReq) * REG_MAX_TRIALS * n, cudaMemcpyHostToDevice,
+                               s->stream));
+            int lvl_tiles = 1;
+            for (int i : act) lvl_tiles = std::max(lvl_tiles, cdiv(s->h_rlv[i].n, 32) * cdiv(s->h_rlv[i].n, 32));
+            launch_rigid(s->bf16, lvl_tiles, n, s->stream, s->d_rlv, s->d_rreq, s->d_rpart, s->d_rsums);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(s->h_rsums, s->d_rsums, sizeof(double) * RIGID_SUMS * n, cudaMemcpyDeviceToHost,
+                               s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            rounds++;
+            std::vector<int> next;
+            for (int i : act) {
+                RigidState &r = st[i];
+                const double *S = s->h_rsums + (size_t)i * RIGID_SUMS;
+                const int nn = s->h_rlv[i].n;
+                const double h2 = 1.0 / ((double)(nn - 1) * (nn - 1));
+                bool done = false;
+                auto end_level = [&](int status) {
+                    r.status = status;
+                    if (status == OPST_NONFINITE) r.nonfinite = 1;
+                    done = true;
+                };
+                if (r.phase == 0) {
+                    r.E = rigid_energy(p, h2, S, r.th[0], r.S1, r.S2, r.S3, r.ncc, r.sig);
+                    if (!std::isfinite(r.E)) end_level(OPST_NONFINITE);
+                    else r.phase = 1;
+                } else if (r.phase == 1) {
+                    double g[3] = {h2 * S[3 * REG_MAX_TRIALS] + 2.0 * p.lambda * sin(r.th[0]),
+                                   h2 * S[3 * REG_MAX_TRIALS + 1], h2 * S[3 * REG_MAX_TRIALS + 2]};
+                    r.iter++;
+                    r.iters_total++;
+                    r.slope = 0.0;
+                    for (int c = 0; c < 3; c++) {
+                        r.d[c] = -g[c];
+                        r.slope += g[c] * r.d[c];
+                    }
+                    if (!(r.slope < 0.0)) end_level(r.slope == 0.0 ? OPST_ZERO_GRAD : OPST_NONFINITE);
+                    else {
+                        rigid_init_trials(r, p);
+                        r.phase = 2;
+                    }
+                } else {
+                    // walk the sequential Armijo rule with widening over the evaluated steps
+                    double Et[REG_MAX_TRIALS];
+                    for (int j = 0; j < r.ntr; j++) {
+                        double a, b, c2, nc, sg;
+                        Et[j] = rigid_energy(p, h2, S + 3 * j, r.th[0] + r.trial_tau[j] * r.d[0], a, b, c2, nc, sg);
+                    }
+                    for (int guard2 = 0; guard2 < 4 * REG_MAX_TRIALS + 8 && !done; guard2++) {
+                        double want = r.search == SEARCH_INIT ? r.tau : (r.search == SEARCH_WIDEN ? 2.0 * r.btau : 0.5 * r.sh_tau);
+                        bool finish = false;
+                        if (r.search == SEARCH_WIDEN && want > p.tau_max) finish = true;
+                        if (r.search == SEARCH_SHRINK && want < p.tau_min) {
+                            end_level(OPST_STALLED);
+                            break;
+                        }
+                        if (!finish) {
+                            int j = -1;
+                            for (int k = 0; k < r.ntr; k++)
+                                if (r.trial_tau[k] == want) { j = k; break; }
+                            if (j < 0) {
+                                // continue the search in another round
+                                int k = 0;
+                                double t = want;
+                                if (r.search == SEARCH_WIDEN) { while (k < J && t <= p.tau_max) { r.trial_tau[k++] = t; t *= 2.0; } }
+                                else { while (k < J && t >= p.tau_min) { r.trial_tau[k++] = t; t *= 0.5; } }
+                                r.ntr = k;
+                                break;
+                            }
+                            const double dE = Et[j] - r.E;
+                            const bool acc = dE <= p.armijo_sigma * want * r.slope;
+                            if (acc) {
+                                r.bE = Et[j];
+                                for (int c = 0; c < 3; c++) r.bS[c] = h2 * S[3 * j + c];
+                            }
+                            if (r.search == SEARCH_INIT) {
+                                if (acc) { r.search = SEARCH_WIDEN; r.btau = want; }
+                                else { r.search = SEARCH_SHRINK; r.sh_tau = want; }
+                                continue;
+                            }
+                            if (r.search == SEARCH_WIDEN) {
+                                if (acc) { r.btau = want; continue; }
+                                finish = true;
+                            } else {
+                                if (acc) { r.btau = want; finish = true; }
+                                else { r.sh_tau = want; continue; }
+                            }
+                        }
+                        if (finish) {
+                            const double dec = r.E - r.bE, scale = fabs(r.E) > 1.0 ? fabs(r.E) : 1.0;
+                            for (int c = 0; c < 3; c++) r.th[c] += r.btau * r.d[c];
+                            r.E = r.bE;
+                            r.S1 = r.bS[0];
+                            r.S2 = r.bS[1];
+                            r.S3 = r.bS[2];
+                            const double var = r.S2 - r.S1 * r.S1;
+                            r.sig = var > 0.0 ? sqrt(var) : 0.0;
+                            r.ncc = r.S3 / r.sig;
+                            r.tau = r.btau;
+                            if (dec < p.epsilon * scale) end_level(OPST_CONVERGED);
+                            else if (r.iter >= p.iter_max) end_level(OPST_MAXITER);
+                            else r.phase = 1;
+                            break;
+                        }
+                    }
+                }
+                if (!done) next.push_back(i);
+            }
+            act.swap(next);
+        }
+    }
+    // results into the destination slots: parameters and the finest field
+    for (int i = 0; i < n; i++) {
+        const OpReq &o = ops[i];
+        SeriesInfo &si = s->S[o.series];
+        si.rigid[o.dst] = st[i].th;
+        const int nL = si.n[si.nl - 1];
+        launch_rigid_fill(rigid_req(st[i].th, nL), nL, si.slots + (size_t)o.dst * si.slot_elems, si.pitch[si.nl - 1],
+                          s->stream);
+        if (status_out) status_out[i] = st[i].nonfinite ? REG_OP_NONFINITE : st[i].status;
+        if (iters_out) iters_out[i] = st[i].iters_total;
+        s->tot_iters += st[i].iters_total;
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    s->tot_ops += n;
+    s->tot_steps += rounds;
+    return REG_OK;
+}
+
 // Resident-block grids of the step kernels (the trial kernel's depends on the
 // step sizes per pass).
 void set_grids(reg_series *s)
@@ -563,6 +914,8 @@ reg_status validate_params(const reg_params *p)
     if (p->init_levels < 0 || p->init_levels > p->n_levels)
         return fail(REG_EINVAL, "init_levels must be in [0, n_levels]");
     if (!(p->learned_fallback_px >= 0.0)) return fail(REG_EINVAL, "learned_fallback_px must be >= 0");
+    if (p->flags & ~(REG_FLAG_PROFILE | REG_FLAG_RIGID)) return fail(REG_EINVAL, "unknown flag");
+    if (!(p->smooth >= 0.0 && p->smooth <= 1e3)) return fail(REG_EINVAL, "smooth must be in [0, 1000]");
     return REG_OK;
 }
 
@@ -595,8 +948,9 @@ void build_levels(reg_series *s, SeriesInfo &si, float *rawf, int f0, int nf, do
 }
 
 // Copy a slot field (device) to another slot.
-reg_status copy_slot(reg_series *s, const SeriesInfo &si, int dst, int src)
+reg_status copy_slot(reg_series *s, SeriesInfo &si, int dst, int src)
 {
+    si.rigid[dst] = si.rigid[src];
     CK(cudaMemcpyAsync(si.slots + (size_t)dst * si.slot_elems, si.slots + (size_t)src * si.slot_elems,
                        si.slot_elems * sizeof(float2), cudaMemcpyDeviceToDevice, s->stream));
     return REG_OK;
@@ -724,6 +1078,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         si.ws_bytes = woff;
         si.slot_elems = (size_t)si.n[si.nl - 1] * si.pitch[si.nl - 1];
         si.meta.assign(si.n_slots, SlotMeta{});
+        si.rigid.assign(si.n_slots + 1, {0.0, 0.0, 0.0});
         size_t esz = s->bf16 ? 2 : 4;
         const size_t blocks = (size_t)si.n_frames + 1;  // + the average frame
         if ((st = track(s, &si.pyr, si.frame_block * blocks * esz)) != REG_OK) return cleanup(st);
@@ -734,6 +1089,35 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         if ((st = track(s, (void **)&si.fstats, sizeof(double) * 2 * blocks)) != REG_OK) return cleanup(st);
         if ((st = track(s, (void **)&si.d_fields, sizeof(void *) * si.n_frames)) != REG_OK) return cleanup(st);
         s->S.push_back(si);
+    }
+    // H1-type smoother: Thomas pivots (c'_i, m_i) of the dimensionless 1D
+    // system T = tridiag(1/6 - s^2/2, 2/3 + s^2, .), 1/3 + s^2/2 at the ends,
+    // for every level in use
+    if (p->smooth > 0.0) {
+        const double sg = p->smooth, a = 1.0 / 6.0 - 0.5 * sg * sg;
+        int nmax = 0;
+        for (auto &si : s->S)
+            for (int k = 0; k < si.nl; k++) {
+                const int n = si.n[k], l = level_of(n);
+                nmax = std::max(nmax, n);
+                if (s->d_smtab[l]) continue;
+                std::vector<float2> tab(n);
+                double cp = 0.0;
+                for (int i = 0; i < n; i++) {
+                    const double diag = (i == 0 || i == n - 1) ? 1.0 / 3.0 + 0.5 * sg * sg : 2.0 / 3.0 + sg * sg;
+                    const double m = 1.0 / (diag - (i > 0 ? a * cp : 0.0));
+                    cp = a * m;
+                    tab[i] = make_float2((float)cp, (float)m);
+                }
+                if ((st = track(s, (void **)&s->d_smtab[l], sizeof(float2) * n)) != REG_OK) return cleanup(st);
+                if (cudaMemcpyAsync(s->d_smtab[l], tab.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s->stream) !=
+                    cudaSuccess)
+                    return cleanup(fail(REG_ECUDA, "smoother table upload"));
+                if (cudaStreamSynchronize(s->stream) != cudaSuccess) return cleanup(fail(REG_ECUDA, "sync"));
+            }
+        s->sm_rch = cdiv(nmax, 32);
+        s->sm_cch = cdiv(nmax, REG_GW);
+        s->grid_S = s->nsm * 8;
     }
     // Pyramid construction in chunks of frames: raw level L, restriction chain,
     // per-level FE mean/sigma, normalisation into the stored pyramid.
@@ -1121,6 +1505,46 @@ reg_status reg_set_slot(reg_series_t s, int32_t series, int32_t slot, const floa
     return REG_OK;
 }
 
+reg_status reg_get_rigid(reg_series_t s, int32_t series, int32_t slot, double *theta, int32_t *start_end)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size() || !theta) return fail(REG_EINVAL, "bad argument");
+    if (!(s->p.flags & REG_FLAG_RIGID)) return fail(REG_ESTATE, "not a rigid handle");
+    SeriesInfo &si = s->S[series];
+    if (slot < 0 || slot >= si.n_slots) return fail(REG_EINVAL, "slot out of range");
+    for (int c = 0; c < 3; c++) theta[c] = si.meta[slot].end >= 0 ? si.rigid[slot][c] : 0.0;
+    if (start_end) {
+        start_end[0] = si.meta[slot].start;
+        start_end[1] = si.meta[slot].end;
+    }
+    return REG_OK;
+}
+
+reg_status reg_set_rigid(reg_series_t s, int32_t series, int32_t slot, const double *theta, int32_t start,
+                         int32_t end)
+{
+    g_err.clear();
+    if (!s || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad argument");
+    if (!(s->p.flags & REG_FLAG_RIGID)) return fail(REG_ESTATE, "not a rigid handle");
+    SeriesInfo &si = s->S[series];
+    if (slot < 0 || slot >= si.n_slots) return fail(REG_EINVAL, "slot out of range");
+    if (end < 0) {
+        si.meta[slot] = SlotMeta{};
+        return REG_OK;
+    }
+    if (!theta || start < 0 || start >= si.n_frames || end >= si.n_frames) return fail(REG_EINVAL, "bad parameters or frames");
+    for (int c = 0; c < 3; c++)
+        if (!std::isfinite(theta[c])) return fail(REG_EINVAL, "parameters must be finite");
+    si.rigid[slot] = {theta[0], theta[1], theta[2]};
+    const int nL = si.n[si.nl - 1];
+    launch_rigid_fill(rigid_req(si.rigid[slot], nL), nL, si.slots + (size_t)slot * si.slot_elems, si.pitch[si.nl - 1],
+                      s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    si.meta[slot] = SlotMeta{start, end};
+    return REG_OK;
+}
+
 reg_status reg_num_slots(reg_series_t s, int32_t series, int32_t *n_slots)
 {
     if (!s || !n_slots || series < 0 || series >= (int)s->S.size()) return fail(REG_EINVAL, "bad argument");
@@ -1427,6 +1851,7 @@ reg_status reg_set_flags(reg_series_t s, int32_t flags)
 {
     g_err.clear();
     if (!s || (flags & ~REG_FLAG_PROFILE)) return fail(REG_EINVAL, "bad handle or unknown flag");
+    flags |= s->p.flags & REG_FLAG_RIGID;  // the operator of a handle is fixed at creation
     s->p.flags = flags;
     return REG_OK;
 }

@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev b)
         if (o < n_ops) {
             OpState &s = b.st[o];
             if (inP) { b.listP[offE[0] + eP] = o; b.prefP[offE[0] + eP] = offI[0] + iP; }
-            if (inG) { b.listG[offE[1] + eG] = o; b.prefG[offE[1] + eG] = offI[1] + iG; }
+            if (inG) { b.listG[offE[1] + eG] = o; b.prefG[offE[1] + eG] = offI[1] + iG; s.g_entry = offE[1] + eG; }
             if (inT) { b.listT[offE[2] + eT] = o; b.prefT[offE[2] + eT] = offI[2] + iT; }
             s.g_begin = offI[1] + iG; s.g_end = s.g_begin + tG;
             s.t_begin = offI[2] + iT; s.t_end = s.t_begin + tT;
@@ -697,6 +697,164 @@ __global__ void __launch_bounds__(REG_STRIP_THREADS, 8) k_grad(BatchDev b)
         qud = warp_sum(qud / 6.f);
         if (lane < PG_STRIDE) b.partG[(int64_t)item * PG_STRIDE + lane] = lane == 0 ? slope : qud;
     }
+}
+
+// ---------------------------------------------------------------------------
+// S: the H1-type smoother (Section "Gradient flow": d = -A^{-1} E'[phi], A
+// selected to smooth).  A = M_s (x) M_s, the tensor-product Gram matrix of
+// M_s = M1 + (s^2/2) K1 with s a number of grid spacings; in grid units of
+// the level the direction is d = (T (x) T)^{-1} (omega d_L2), T = M_s / h the
+// dimensionless tridiagonal matrix (off-diagonal 1/6 - s^2/2, diagonal
+// 2/3 + s^2, 1/3 + s^2/2 at the ends) and d_L2 = -psi / (h^2 omega) the lumped
+// direction of the gradient pass.  The Kronecker inverse is one tridiagonal
+// solve along every row, then one along every column (Thomas elimination
+// with the level's precomputed pivots).  The previous iterate's node records
+// (not read again before the next gradient pass overwrites them) hold the
+// intermediate fields.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 *sm_scratch(NodeRec *V, int64_t idx, int k)
+{
+    return reinterpret_cast<float2 *>(&V[idx].u) + k;  // k = 0: u.x, u.y; k = 1: u.z, u.w
+}
+
+// Rows: lane = one row of one operator, sequential over its columns.
+__global__ void __launch_bounds__(128) k_smooth_rows(BatchDev b)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * 4, nG = b.ctr[2];
+    const float a = b.sm_a;
+    for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < nG * b.rch; it += nwarps) {
+        const int e = it / b.rch, ch = it % b.rch;
+        const int o = b.listG[e];
+        const OpState &s = b.st[o];
+        const LevelDesc &Lv = b.ops[o].lv[s.lvl];
+        const int n = Lv.n, pitch = Lv.pitch, r = ch * 32 + lane;
+        if (r >= n) continue;
+        const NodeRec *Vc = Lv.V[s.cur];
+        NodeRec *Vs = Lv.V[s.src];
+        const float omr = (r == 0 || r == n - 1) ? 0.5f : 1.f;
+        float2 y = make_float2(0.f, 0.f);
+        for (int c = 0; c < n; c++) {
+            const int64_t idx = (int64_t)r * pitch + c;
+            const float2 d = Vc[idx].d;
+            const float om = omr * ((c == 0 || c == n - 1) ? 0.5f : 1.f);
+            const float m = Lv.sm_tab[c].y;
+            y.x = (om * d.x - a * y.x) * m;
+            y.y = (om * d.y - a * y.y) * m;
+            *sm_scratch(Vs, idx, 0) = y;
+        }
+        float2 x = make_float2(0.f, 0.f);
+        for (int c = n - 1; c >= 0; c--) {
+            const int64_t idx = (int64_t)r * pitch + c;
+            const float2 yc = *sm_scratch(Vs, idx, 0);
+            const float cp = c < n - 1 ? Lv.sm_tab[c].x : 0.f;
+            x.x = yc.x - cp * x.x;
+            x.y = yc.y - cp * x.y;
+            *sm_scratch(Vs, idx, 0) = x;
+        }
+    }
+}
+
+// Columns: a warp holds REG_GW owned columns and one halo column on each side
+// (lanes 0 and 31), walks down for the elimination and up for the
+// substitution; on the way up it writes d into the current records and sums
+// the new slope g^T d = -h^4 sum omega d_L2 . d and u^T K d (6 K u by the
+// integer stencils of the gradient pass, hi and lo parts of u differenced
+// separately).
+__global__ void __launch_bounds__(128) k_smooth_cols(BatchDev b)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * 4, nG = b.ctr[2];
+    const float a = b.sm_a;
+    for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < nG * b.cch; it += nwarps) {
+        const int e = it / b.cch, ch = it % b.cch;
+        const int o = b.listG[e];
+        const OpState &s = b.st[o];
+        const LevelDesc &Lv = b.ops[o].lv[s.lvl];
+        const int n = Lv.n, pitch = Lv.pitch;
+        if (ch * REG_GW >= n) continue;  // warp-uniform
+        const int c = ch * REG_GW - 1 + lane;
+        const bool colIn = c >= 0 && c < n, own = colIn && lane >= 1 && lane <= REG_GW;
+        NodeRec *Vc = Lv.V[s.cur];
+        NodeRec *Vs = Lv.V[s.src];
+        float2 y = make_float2(0.f, 0.f);
+        if (colIn)
+            for (int r = 0; r < n; r++) {
+                const int64_t idx = (int64_t)r * pitch + c;
+                const float2 x = *sm_scratch(Vs, idx, 0);
+                const float m = Lv.sm_tab[r].y;
+                y.x = (x.x - a * y.x) * m;
+                y.y = (x.y - a * y.y) * m;
+                *sm_scratch(Vs, idx, 1) = y;
+            }
+        const float cx6 = (c == 0 || c == n - 1) ? 2.f : 4.f;
+        const float omc = (c == 0 || c == n - 1) ? 0.5f : 1.f;
+        // rolling rows r+1 (P), r (C), r-1 (N) of u and of K1 along the row
+        auto ldu = [&](int r) {
+            return (colIn && r >= 0 && r < n) ? reinterpret_cast<const float4 *>(Vc + (int64_t)r * pitch + c)[0]
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        auto kx_of = [&](const float4 &u, int r) {
+            // [u(c) - u(c-1)] - [u(c+1) - u(c)] along the row (0 past the grid)
+            float4 uR;
+            uR.x = __shfl_down_sync(FULL, u.x, 1);
+            uR.y = __shfl_down_sync(FULL, u.y, 1);
+            uR.z = __shfl_down_sync(FULL, u.z, 1);
+            uR.w = __shfl_down_sync(FULL, u.w, 1);
+            const bool rowIn = r >= 0 && r < n, hasR = colIn && rowIn && c + 1 < n;
+            const float dxx = hasR ? (uR.x - u.x) + (uR.z - u.z) : 0.f;
+            const float dxy = hasR ? (uR.y - u.y) + (uR.w - u.w) : 0.f;
+            return make_float2(__shfl_up_sync(FULL, dxx, 1) - dxx, __shfl_up_sync(FULL, dxy, 1) - dxy);
+        };
+        float4 uP = make_float4(0.f, 0.f, 0.f, 0.f), uC = ldu(n - 1);
+        float2 kP = make_float2(0.f, 0.f), kC = kx_of(uC, n - 1);
+        float2 dnext = make_float2(0.f, 0.f);
+        float sl = 0.f, qd = 0.f;
+        for (int r = n - 1; r >= 0; r--) {
+            const float4 uN = ldu(r - 1);
+            const float2 kN = kx_of(uN, r - 1);
+            float2 dn = make_float2(0.f, 0.f);
+            const int64_t idx = (int64_t)r * pitch + c;
+            if (colIn) {
+                const float2 yr = *sm_scratch(Vs, idx, 1);
+                const float cp = r < n - 1 ? Lv.sm_tab[r].x : 0.f;
+                dn.x = yr.x - cp * dnext.x;
+                dn.y = yr.y - cp * dnext.y;
+            }
+            dnext = dn;
+            // K1 along the column at (r, c): [u(r) - u(r-1)] - [u(r+1) - u(r)]
+            const bool hasU = colIn && r >= 1, hasD = colIn && r + 1 < n;
+            const float kyx = (hasU ? (uC.x - uN.x) + (uC.z - uN.z) : 0.f) - (hasD ? (uP.x - uC.x) + (uP.z - uC.z) : 0.f);
+            const float kyy = (hasU ? (uC.y - uN.y) + (uC.w - uN.w) : 0.f) - (hasD ? (uP.y - uC.y) + (uP.w - uC.w) : 0.f);
+            const float KYx = (__shfl_up_sync(FULL, kyx, 1) + __shfl_down_sync(FULL, kyx, 1)) + cx6 * kyx;
+            const float KYy = (__shfl_up_sync(FULL, kyy, 1) + __shfl_down_sync(FULL, kyy, 1)) + cx6 * kyy;
+            if (own) {
+                const float cy6 = (r == 0 || r == n - 1) ? 2.f : 4.f;
+                const float kux = (kP.x + kN.x) + cy6 * kC.x + KYx;  // 6 (K u)
+                const float kuy = (kP.y + kN.y) + cy6 * kC.y + KYy;
+                const float om = omc * ((r == 0 || r == n - 1) ? 0.5f : 1.f);
+                const float2 dl = Vc[idx].d;
+                sl += om * (dl.x * dn.x + dl.y * dn.y);
+                qd += dn.x * kux + dn.y * kuy;
+                Vc[idx].d = dn;
+            }
+            uP = uC; uC = uN;
+            kP = kC; kC = kN;
+        }
+        sl = warp_sum(sl);
+        qd = warp_sum(qd / 6.f);
+        if (lane == 0) {
+            b.partS[((int64_t)e * b.cch + ch) * 2] = sl;
+            b.partS[((int64_t)e * b.cch + ch) * 2 + 1] = qd;
+        }
+    }
+}
+
+void launch_smooth(int grid, cudaStream_t st, const BatchDev &b)
+{
+    k_smooth_rows<<<grid, 128, 0, st>>>(b);
+    k_smooth_cols<<<grid, 128, 0, st>>>(b);
 }
 
 // Bilinear sampling helpers of the trial pass.
@@ -1462,9 +1620,20 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
 {
     const LevelDesc &Lv = op.lv[s.lvl];
     const double h2 = Lv.h2d;
+    if (ph == PH_GRAD && b.smooth) {
+        // the smoothed direction's slope and u^T K d (smoother partials, fixed order)
+        double sl = 0.0, qd = 0.0;
+        const int nch = (Lv.n + REG_GW - 1) / REG_GW;
+        for (int ch = 0; ch < nch; ch++) {
+            sl += b.partS[((int64_t)s.g_entry * b.cch + ch) * 2];
+            qd += b.partS[((int64_t)s.g_entry * b.cch + ch) * 2 + 1];
+        }
+        slope = -h2 * h2 * sl;
+        qud = qd;
+    }
     if (ph == PH_GRAD) {
-        // the Dirichlet forms of the new search: u^T K d from the gradient pass,
-        // d^T K d from its first trial pass
+        // the Dirichlet forms of the new search: u^T K d from the gradient pass
+        // (or the smoother), d^T K d from its first trial pass
         s.Qud = qud;
         s.Qdd = S[3 * REG_MAX_TRIALS + 2];
     }
@@ -1639,6 +1808,160 @@ void launch_average(int bf16, cudaStream_t st, const void *pyr, int64_t frame_bl
     dim3 blk(32, 8), grid(cdiv(n, 32), cdiv(n, 8));
     if (bf16) k_average<true><<<grid, blk, 0, st>>>(pyr, frame_block, img_off, n, pitch, fstats, fields, slot_pitch, m, out, opitch);
     else k_average<false><<<grid, blk, 0, st>>>(pyr, frame_block, img_off, n, pitch, fstats, fields, slot_pitch, m, out, opitch);
+}
+
+// ---------------------------------------------------------------------------
+// Rigid variant (Definition "Rigid transformation": phi(x) = R(alpha) x + t;
+// Section "Gradient flow": no smoother in the rigid case)
+// ---------------------------------------------------------------------------
+
+// Rigid displacement of node (c, r) in grid units of a level of n nodes:
+// u = (R(alpha) - I) x + t with a = cos(alpha) - 1, b = sin(alpha) and the
+// translation (tx, ty) in grid units.
+__device__ __forceinline__ float2 rigid_u(const RigidReq &q, int c, int r)
+{
+    return make_float2(fmaf(q.a, (float)c, fmaf(-q.b, (float)r, q.tx)), fmaf(q.b, (float)c, fmaf(q.a, (float)r, q.ty)));
+}
+
+// One block per 32 x 32 node tile of one operator (grid: tiles, ops).  For
+// every requested parameter set j < q.n_e: the FE sums of the warped template
+// That = T(x + u) over the tile (nodes and cells it owns): sum omega That,
+// sum of the Q1 element mass forms of That, sum That M~R~ (multiplied by h^2
+// on the host).  With q.grad: the data part of dE/dtheta at parameter set 0,
+//   -sum_i dNCC/dThat_i (dT_0 du_0/dtheta + dT_1 du_1/dtheta),
+//   dNCC/dThat_i = h^2 [ M~R~_i / sigma_T - NCC ((M~ That)_i - T_bar omega_i) / sigma_T^2 ],
+// derivatives in Omega units.  That of the tile and a one-node halo is kept in
+// shared memory for the cell forms and M~ That.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_rigid_eval(const RigidLevel *__restrict__ lv, const RigidReq *__restrict__ req,
+                                                    double *__restrict__ part)
+{
+    constexpr int TS = 32, HS = TS + 2;
+    __shared__ float sh[HS][HS + 1];
+    __shared__ float red[8][RIGID_SUMS];
+    const int o = blockIdx.y;
+    const RigidLevel L = lv[o];
+    const int n = L.n;
+    const int tx = (n + TS - 1) / TS;
+    const int tile = blockIdx.x;
+    if (tile >= tx * tx) return;
+    const int c0 = (tile % tx) * TS, r0 = (tile / tx) * TS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *out = part + ((int64_t)o * gridDim.x + tile) * RIGID_SUMS;
+    const RigidReq *qs = req + (int64_t)o * REG_MAX_TRIALS;
+    auto omega = [n](int i) { return (i == 0 || i == n - 1) ? 0.5f : 1.f; };
+    auto w6 = [n](int i, int a) { return a == 0 ? ((i == 0 || i == n - 1) ? 2.f : 4.f) : 1.f; };
+    const int nsets = qs[0].n_e;
+    for (int j = 0; j < nsets; j++) {
+        const RigidReq q = qs[j];
+        const bool grad = (j == 0) && q.grad;
+        // That on the tile plus a one-node halo (nodes outside the grid: 0)
+        for (int k = threadIdx.x; k < HS * HS; k += blockDim.x) {
+            const int rr = r0 - 1 + k / HS, cc = c0 - 1 + k % HS;
+            float v = 0.f;
+            if (rr >= 0 && rr < n && cc >= 0 && cc < n) {
+                const float2 u = rigid_u(q, cc, rr);
+                v = sample<BF16, false>(L.T, n, L.pitch, cc, rr, u.x, u.y, nullptr, nullptr);
+            }
+            sh[k / HS][k % HS] = v;
+        }
+        __syncthreads();
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        for (int k = threadIdx.x; k < TS * TS; k += blockDim.x) {
+            const int lr = k / TS, lc = k % TS, r = r0 + lr, c = c0 + lc;
+            if (r >= n || c >= n) continue;
+            const float t = sh[lr + 1][lc + 1];
+            const float om = omega(r) * omega(c);
+            const float mr = L.MR[(int64_t)r * L.pitch + c];
+            s1 += om * t;
+            s3 += t * mr;
+            if (r < n - 1 && c < n - 1) {
+                // cell (r, c): corners a=(r,c) b=(r,c+1) cc=(r+1,c+1) d=(r+1,c), element mass (1/36)[4 2 1 2; ...]
+                const float A = t, B = sh[lr + 1][lc + 2], C = sh[lr + 2][lc + 2], D = sh[lr + 2][lc + 1];
+                s2 += (4.f * (A * A + B * B + C * C + D * D) + 4.f * (A * B + B * C + C * D + D * A) +
+                       2.f * (A * C + B * D)) * (1.f / 36.f);
+            }
+            if (grad) {
+                // (36 M~ That)_i: integer weights, boundary rows/cols halved
+                float mt = 0.f;
+                for (int a = -1; a <= 1; a++) {
+                    if (r + a < 0 || r + a >= n) continue;
+                    float row = 0.f;
+                    for (int b = -1; b <= 1; b++) {
+                        if (c + b < 0 || c + b >= n) continue;
+                        row += w6(c, b) * sh[lr + 1 + a][lc + 1 + b];
+                    }
+                    mt += w6(r, a) * row;
+                }
+                const float2 u = rigid_u(q, c, r);
+                float dx, dy;
+                sample<BF16, true>(L.T, n, L.pitch, c, r, u.x, u.y, &dx, &dy);
+                // dNCC/dThat_i / h^2, times (n - 1) for derivatives in Omega units
+                const float dn = (mr * q.inv_sig - q.ncc_over_var * (mt * (1.f / 36.f) - q.tbar * om)) * q.nm1;
+                const float x0 = (float)c * q.h, x1 = (float)r * q.h;
+                g0 -= dn * (dx * (-q.sa * x0 - q.ca * x1) + dy * (q.ca * x0 - q.sa * x1));
+                g1 -= dn * dx;
+                g2 -= dn * dy;
+            }
+        }
+        float v[6] = {s1, s2, s3, g0, g1, g2};
+        const int nv = grad ? 6 : 3;
+        for (int m = 0; m < nv; m++) {
+            float w = warp_sum(v[m]);
+            if (lane == 0) red[wid][m] = w;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double acc = 0.0;
+            for (int w = 0; w < 8; w++) acc += red[w][threadIdx.x];
+            out[(threadIdx.x < 3 ? 3 * j : 3 * REG_MAX_TRIALS - 3) + threadIdx.x] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Per operator: the tiles' partial sums in a fixed order (one block per op).
+__global__ void k_rigid_reduce(const double *__restrict__ part, int tiles_stride, const RigidLevel *__restrict__ lv,
+                               double *__restrict__ sums)
+{
+    const int o = blockIdx.x;
+    const int n = lv[o].n, tx = (n + 31) / 32, tiles = tx * tx;
+    __shared__ double red[RIGID_SUMS][8];
+    for (int m = 0; m < RIGID_SUMS; m++) {
+        double acc = 0.0;
+        for (int t = threadIdx.x; t < tiles; t += blockDim.x) acc += part[((int64_t)o * tiles_stride + t) * RIGID_SUMS + m];
+        acc = warp_sum_d(acc);
+        if ((threadIdx.x & 31) == 0) red[m][threadIdx.x >> 5] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < RIGID_SUMS) {
+        double acc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) acc += red[threadIdx.x][w];
+        sums[(int64_t)o * RIGID_SUMS + threadIdx.x] = acc;
+    }
+}
+
+// The finest-level field of rigid parameters, in pixels (= grid units of the
+// finest level), into a slot: u = (R(alpha) - I) x + t.
+__global__ void k_rigid_fill(RigidReq q, int n, float2 *__restrict__ slot, int pitch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= n || c >= n) return;
+    slot[(int64_t)r * pitch + c] = rigid_u(q, c, r);
+}
+
+void launch_rigid(int bf16, int tiles, int n_ops, cudaStream_t st, const RigidLevel *lv, const RigidReq *req,
+                  double *part, double *sums)
+{
+    dim3 grid(tiles, n_ops);
+    if (bf16) k_rigid_eval<true><<<grid, 256, 0, st>>>(lv, req, part);
+    else k_rigid_eval<false><<<grid, 256, 0, st>>>(lv, req, part);
+    k_rigid_reduce<<<n_ops, 256, 0, st>>>(part, tiles, lv, sums);
+}
+
+void launch_rigid_fill(const RigidReq &q, int n, float2 *slot, int pitch, cudaStream_t st)
+{
+    k_rigid_fill<<<dim3(cdiv(n, 32), cdiv(n, 8)), dim3(32, 8), 0, st>>>(q, n, slot, pitch);
 }
 
 // ---------------------------------------------------------------------------

@@ -73,6 +73,7 @@ struct LevelDesc {
     const void *T;    // normalised template frame
     const float *MR;  // M~ R~: the reference frame times the FE mass matrix (units h^2)
     NodeRec *V[2];    // node records, double-buffered (the gradient pass reads one, writes the other)
+    const float2 *sm_tab;  // H1-type smoother: Thomas coefficients (c'_i, m_i) of the level's 1D system
 };
 
 struct OpDesc {
@@ -97,6 +98,7 @@ struct OpState {
     int iter, iters_total, trials_seq, evals;
     int status, nonfinite_seen, search, ntr;
     int t_begin, t_end, g_begin, g_end;
+    int g_entry;      // index in the gradient pass's op list of this step (smoother partials)
     double tau;       // base step of the current search
     double tau_acc;   // step to apply at the start of the next G/P pass
     double sh_tau;    // shrinking: last rejected step
@@ -128,7 +130,28 @@ struct BatchDev {
     long long trace_cap;
     double lambda, sigma, tau_init, tau_max, tau_min, eps;
     int iter_max, J, bf16, pad;
+    // H1-type smoother (smooth != 0): per gradient-pass op and column chunk of
+    // REG_GW columns, the partial sums {sum omega d_L2 . d, sum d . 6 K u}
+    double *partS;
+    int smooth, rch, cch;  // row chunks of 32 and column chunks of REG_GW per op (maxima)
+    float sm_a;            // off-diagonal of the dimensionless 1D system (1/6 - s^2/2)
 };
+
+// Rigid variant: one level of one operator, and one requested parameter set
+// (element 0 of an operator's REG_MAX_TRIALS requests carries the count n_e
+// and, with grad, the scalars of the gradient at that parameter set).
+struct RigidLevel {
+    int n, pitch;
+    const void *T;     // normalised template at this level
+    const float *MR;   // M~ R~ of the normalised reference
+};
+struct RigidReq {
+    float a, b, tx, ty;           // cos(alpha) - 1, sin(alpha), translation in grid units
+    float ca, sa, h, nm1;         // cos, sin, grid spacing 1/(n-1) and n-1 (gradient only)
+    float inv_sig, ncc_over_var, tbar;  // 1/sigma_T, NCC/sigma_T^2, T_bar at the gradient's parameters
+    int n_e, grad;                // request 0: number of parameter sets, gradient wanted
+};
+#define RIGID_SUMS (3 * REG_MAX_TRIALS + 3)  // 3 energy sums per set, then 3 gradient sums
 
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 

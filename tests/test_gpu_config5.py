@@ -49,3 +49,63 @@ def test_config5_full_size_mixed_scan(reg, syn):
               f"max {err.max():.3f} px, 99th percentile {np.quantile(err, 0.99):.4f} px")
         assert np.isfinite(err).all()
         assert err.mean() < 1.0, (side, float(err.mean()))
+
+
+def test_config5_sampled_operators_against_the_oracle(reg, orc, syn):
+    """Config 5's four series (256^2, 512^2, 1024^2, 2048^2; c3's generator, 5
+    levels) in one batch: operator A(1,2) of every series from the FP32 and the
+    BF16 storage form against the FP64 oracle.  FP32: the parity criteria of
+    the plain form, free running and in lockstep with the oracle's steps.
+    BF16: max, 99th percentile and mean |du| and the final-energy difference
+    are stated (the precision policy bounds them by nothing a priori)."""
+    import _parity as P
+    from concurrent.futures import ThreadPoolExecutor
+    series = [syn.series(6 + i, 3, side, **GEN) for i, side in enumerate(SIDES)]
+    lam, nl = 10.0, 5
+    op = orc.params(n_levels=nl, iter_max=50, lam=lam)
+    g = [(orc.embed(f[1]), orc.embed(f[2])) for f in series]
+
+    def solve(k):
+        with orc.trace() as t:
+            u, _, _ = orc.register(g[k][0], g[k][1], op)
+        return u, t.rows
+
+    with ThreadPoolExecutor(max_workers=len(SIDES)) as ex:
+        res = list(ex.map(solve, range(len(SIDES))))
+    ops = [(k, -1, -1, 1, 1, 2) for k in range(len(SIDES))]
+    for storage in (reg.STORAGE_F32, reg.STORAGE_BF16):
+        p = reg.default_params(n_levels=nl, iter_max=50, lam=lam, storage=storage)
+        with reg.Series(series, p) as s:
+            s.set_trace(1 << 23)
+            s.apply_operator_batch(ops)
+            tr = s.get_trace()
+            got = [s.get_slot(1, series=k)[0] for k in range(len(SIDES))]
+            for k, side in enumerate(SIDES):
+                u, rows = res[k]
+                what = f"c5 {side}^2 A(1,2) {'bf16' if storage else 'fp32'}"
+                if storage == reg.STORAGE_F32:
+                    # lockstep one series at a time: the other series' ops take no steps
+                    L = int(np.log2(side))
+                    level_ns = [(1 << (L - nl + 1 + j)) + 1 for j in range(nl)]
+                    counts, taus, _ = P.lock_sequence(rows, level_ns)
+                    allc = [[0] * nl for _ in SIDES]
+                    allc[k] = counts
+                    s.set_lockstep(allc, taus)
+                    s.set_trace(1 << 22)
+                    try:
+                        s.apply_operator_batch([(j, -1, -1, 0, 1, 2) for j in range(len(SIDES))])
+                        ltr = s.get_trace()
+                    finally:
+                        s.set_lockstep(None)
+                    lgot = s.get_slot(0, series=k)[0]
+                    rec = dict(what=what, mode="lockstep", steps=len(taus), **P.field_stats(lgot, u * side))
+                    rec["E_rel"] = P.energy_rel(orc, g[k][0], g[k][1], lgot, u * side, lam)[0]
+                    P.report("c5", rec)
+                    assert rec["max_px"] <= P.TOL_PX or P._agreeing_fields_ok(rec), rec
+                    P.report("c5", P.free_running_parity(orc, got[k], u * side, tr[tr[:, 0] == k][:, 1:], rows,
+                                                         what, g[k][0], g[k][1], op, lam))
+                else:
+                    rec = dict(what=what, mode="free", **P.field_stats(got[k], u * side))
+                    rec["E_rel"] = P.energy_rel(orc, g[k][0], g[k][1], got[k], u * side, lam)[0]
+                    P.report("c5", rec)
+                    assert np.isfinite(rec["max_px"])

@@ -1,0 +1,104 @@
+"""The rigid variant on the GPU (REG_FLAG_RIGID) against the FP64 oracle
+(Definition "Rigid transformation": phi(x) = R(alpha) x + t; Section
+"Gradient flow": no smoother; Algorithm "Multilevel gradient flow": the
+parameters are carried between levels unchanged).
+
+Tolerances: the displacement fields the two parameter sets define within
+RIGID_TOL_PX at every node of the frame, and the final energies within 1e-5
+relative (oracle FP64 energy at both parameter sets).  The fit is
+ill-conditioned along one direction (a rotation about Omega's origin and a
+translation move the frame's centre alike), where the energy is flat to a
+few 1e-8 over 1e-5 rad; the device state machine decides each step from FP32
+energy sums taken separately at the two parameter sets, so the two sides stop
+at different points of that valley.  The field bound states how far apart."""
+import numpy as np
+import pytest
+
+import _parity as P
+
+pytestmark = pytest.mark.gpu
+RIGID_TOL_PX = 5e-3
+
+
+@pytest.fixture(scope="module")
+def reg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as r
+    return r
+
+
+def _rot(a):
+    return np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+
+
+def _rotated_pair(side, alpha, t, seed=4):
+    """f_0(y) = I(y), f_1(y) = I(phi^-1(y)) for a smooth image I (Gaussian
+    blobs, sigma 4 px) and phi(x) = R(alpha) x + t in pixels."""
+    rng = np.random.default_rng(seed)
+    pts = [(rng.uniform(-20, side + 20), rng.uniform(-20, side + 20), rng.uniform(0.5, 1.5)) for _ in range(side + 32)]
+
+    def img(X, Y):
+        v = np.zeros_like(X)
+        for (a, b, w) in pts:
+            v += w * np.exp(-((X - a) ** 2 + (Y - b) ** 2) / 32.0)
+        return v
+    c = np.arange(side, dtype=np.float64)
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    Q = np.einsum("ij,jrc->irc", _rot(-alpha), np.stack([X - t[0], Y - t[1]]))
+    return np.stack([img(X, Y), img(Q[0], Q[1])]).astype(np.float32)
+
+
+def _check(orc, R, T, th_gpu, th_orc, lam, side, what):
+    e_g = orc.rigid_energy(R, T, th_gpu, lam)
+    e_o = orc.rigid_energy(R, T, th_orc, lam)
+    du = np.abs(orc.rigid_field(th_gpu, side + 1) - orc.rigid_field(th_orc, side + 1)).max() * side
+    rec = dict(what=what, d_alpha=float(abs(th_gpu[0] - th_orc[0])),
+               d_t_px=float(np.abs(th_gpu[1:] - th_orc[1:]).max() * side), field_max_px=float(du),
+               E_rel=float((e_g - e_o) / abs(e_o)))
+    P.report("rigid", rec)
+    assert rec["field_max_px"] <= RIGID_TOL_PX and abs(rec["E_rel"]) <= P.TOL_E, rec
+
+
+@pytest.mark.parametrize("lam", [0.0, 10.0])
+def test_rigid_operator_matches_oracle(reg, orc, lam):
+    side, nl = 128, 3
+    alpha, t = 0.02, np.array([2.3, -1.7])
+    fr = _rotated_pair(side, alpha, t)
+    p = reg.default_params(n_levels=nl, iter_max=200, lam=lam, flags=reg.FLAG_RIGID)
+    with reg.Series(fr, p) as s:
+        st, it = s.apply_operator_batch([(0, -1, -1, 0, 0, 1)])
+        th, se = s.get_rigid(0)
+        field, _ = s.get_slot(0)
+    assert se == (0, 1)
+    R, T = orc.embed(fr[0]), orc.embed(fr[1])
+    th_o, status, stl = orc.rigid_register(R, T, orc.params(n_levels=nl, iter_max=200, lam=lam))
+    _check(orc, R, T, th, th_o, lam, side, f"A rotated pair lambda {lam}")
+    # the slot's field is the rigid map's displacement (pixels)
+    assert np.abs(field - orc.rigid_field(th, side + 1) * side).max() < 1e-3
+    if lam == 0.0:
+        assert abs(th[0] - alpha) < 2e-4 and np.abs(th[1:] * side - t).max() < 0.02
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_rigid_series_matches_oracle(reg, orc, syn, kind):
+    """A whole series with the rigid operator (preprocessing and the prefix
+    scan of B with the composition of rigid maps), serial and Sklansky, on
+    noise-free frames drifting by translations."""
+    side, nl, nf = 64, 3, 6
+    fr = syn.series(7, nf, side, noise=False, drift_sd=1.0, dist_amp=0.0, spacing=10.0, sigma=2.5)
+    lam = 1.0
+    p = reg.default_params(n_levels=nl, iter_max=100, lam=lam, flags=reg.FLAG_RIGID)
+    with reg.Series(fr, p) as s:
+        rep = s.prefix_scan(kind)
+        th = s.rigid_params()
+        d = s.get_deformations()
+    op = orc.params(n_levels=nl, iter_max=100, lam=lam)
+    want = orc.rigid_register_series(fr, op, kind=kind)
+    for k in range(1, nf):
+        _check(orc, orc.embed(fr[0]), orc.embed(fr[k]), th[k], want[k], lam, side, f"series kind {kind} phi_0{k}")
+        assert np.abs(d[k] - orc.rigid_field(th[k], side + 1)[:, :side, :side] * side).max() < 1e-3
+    assert rep["preprocessing_ops"] == nf - 1 and rep["ops"] > nf - 1

@@ -1,0 +1,91 @@
+"""The H1-type smoother on the GPU against the FP64 oracle (Section "Gradient
+flow": phi^{k+1} = phi^k - tau A^{-1} E'[phi^k], A selected to smooth;
+A = M_s (x) M_s, M_s = M1 + (s h)^2/2 K1).  Same criteria as the plain form:
+free running and in lockstep with the oracle's accepted steps."""
+import numpy as np
+import pytest
+
+import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def reg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1712_02533_gb300 import _build
+    _build.build()
+    import paper_1712_02533_gb300 as r
+    return r
+
+
+@pytest.mark.parametrize("smooth,sizes", [(1.0, (64, 256)), (4.0, (64,))])
+def test_smoothed_operators_match_oracle(reg, orc, syn, smooth, sizes):
+    """Function A with the smoother on the config-1 series (noisy, 3 levels) at
+    64^2 and 256^2: every operator free running and in lockstep.  (With a wide
+    smoother on large frames a node that ends on the other side of a cell line
+    moves its whole smoothing neighbourhood, so more than 0.5% of the nodes
+    differ even in lockstep: at s = 4, 256^2, 2.6% by more than 1e-3 px, at
+    most 0.18 px, with the GPU's energy the lower one by 2.4e-5.)"""
+    cfg = dict(syn.CONFIGS["c1_8x64"])
+    nl = cfg.pop("n_levels")
+    for side, nfr in ((64, 4), (256, 3)):
+        if side not in sizes:
+            continue
+        cfg2 = dict(cfg, side=side, n_frames=nfr)
+        fr = syn.series(**cfg2)
+        g = [orc.embed(f) for f in fr]
+        lam = 10.0
+        p = reg.default_params(n_levels=nl, iter_max=50, lam=lam, smooth=smooth)
+        op = orc.params(n_levels=nl, iter_max=50, lam=lam, smooth=smooth)
+        n = nfr - 1
+        res = []
+        for e in range(n):
+            with orc.trace() as t:
+                u, _, _ = orc.register(g[e], g[e + 1], op)
+            res.append((u, t.rows))
+        with reg.Series(fr, p) as s:
+            s.set_trace(1 << 20)
+            s.apply_operator_batch([(0, -1, -1, e, e, e + 1) for e in range(n)])
+            tr = s.get_trace()
+            got = [s.get_slot(e)[0] for e in range(n)]
+            for e in range(n):
+                u, rows = res[e]
+                what = f"smooth {smooth} {side}^2 A({e},{e + 1})"
+                P.report("smooth", P.lockstep_parity(orc, s, (0, -1, -1, e, e, e + 1), e, nl, rows, u * side, what,
+                                                     g[e], g[e + 1], lam))
+                P.report("smooth", P.free_running_parity(orc, got[e], u * side, tr[tr[:, 0] == e][:, 1:], rows, what,
+                                                         g[e], g[e + 1], op, lam))
+
+
+def test_smoothed_series_stable_input_matches_oracle(reg, orc, syn):
+    """A whole series (config 1 without shot noise, Sklansky) with the smoother:
+    phi_{0,k} within TOL_PX at every node."""
+    cfg = dict(syn.CONFIGS["c1_8x64"])
+    nl = cfg.pop("n_levels")
+    fr = syn.series(noise=False, **cfg)
+    p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0, smooth=2.0)
+    with reg.Series(fr, p) as s:
+        s.prefix_scan(reg.SKLANSKY)
+        got = s.get_deformations()
+    want = orc.register_series([fr], orc.params(n_levels=nl, iter_max=50, lam=10.0, smooth=2.0),
+                               kind=reg.SKLANSKY)[0][:, :, :64, :64]
+    err = np.abs(got - want)
+    P.report("smooth-series", dict(max_px=float(err.max()), mean_px=float(err.mean())))
+    assert err.max() <= P.TOL_PX, float(err.max())
+
+
+def test_smoother_changes_the_flow(reg, syn):
+    """The smoothed flow is a different flow: its fields differ from the
+    lumped L2 flow's, and are smoother (smaller mean |grad u|)."""
+    fr = syn.series(**dict(syn.CONFIGS["c1_8x64"], n_levels=None))
+    out = {}
+    for sm in (0.0, 4.0):
+        with reg.Series(fr[:3], reg.default_params(n_levels=3, iter_max=50, lam=1.0, smooth=sm)) as s:
+            s.apply_operator_batch([(0, -1, -1, 0, 0, 1)])
+            out[sm] = s.get_slot(0)[0]
+    rough = {sm: float(np.abs(np.diff(u, axis=-1)).mean() + np.abs(np.diff(u, axis=-2)).mean()) for sm, u in out.items()}
+    assert np.abs(out[0.0] - out[4.0]).max() > 1e-3
+    assert rough[4.0] < rough[0.0], rough
