@@ -314,6 +314,13 @@ reg_status reg_cnn_forward(reg_cnn_t h, const float *x, int32_t batch, float *y,
  * *loss (host) receives the mean squared error. */
 reg_status reg_cnn_loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
                              float *grad_out);
+/* reg_cnn_loss_grad with the training on the tensor cores: the forward of
+ * the four 32-channel layers, their weight gradients and the data gradients
+ * of the three stride-1 ones take BF16 operands with FP32 accumulation; the
+ * first and last layers and the stride-2 layer's data gradient stay in FP32
+ * on the CUDA cores; bias gradients sum the FP32 output gradients. */
+reg_status reg_cnn_loss_grad_tc(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                                float *grad_out);
 /* One Adam step (bias-corrected) with the last gradient. */
 reg_status reg_cnn_adam_step(reg_cnn_t h, double lr, double beta1, double beta2, double eps);
 reg_status reg_cnn_destroy(reg_cnn_t h);

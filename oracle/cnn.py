@@ -117,17 +117,30 @@ def loss(theta, x, target):
     return float(np.mean((y - target) ** 2))
 
 
-def loss_and_grad(theta, x, target):
-    """Mean squared error and its gradient with respect to the flat parameters."""
+def loss_and_grad(theta, x, target, bf16_layers=(), bf16_data=(), bf16_weights=()):
+    """Mean squared error and its gradient with respect to the flat parameters.
+
+    The tensor-core form of training takes BF16 operands in three places,
+    modelled here by rounding those operands (the contraction itself exact):
+    the forward of the layers in bf16_layers (their input and weights), the
+    data gradient of the layers in bf16_data (the output gradient and the
+    weights), and the weight gradient of the layers in bf16_weights (the
+    output gradient and the layer's input).  Bias gradients sum the
+    unrounded output gradient."""
     layers = unpack(theta)
-    y, cache = forward(theta, x, keep=True)
+    y, cache = forward(theta, x, keep=True, bf16_layers=bf16_layers)
     g = 2.0 * (y - target) / y.size
     grads = [None] * len(LAYERS)
     for k in range(len(LAYERS) - 1, -1, -1):
         a, z = cache[k]
         if k < len(LAYERS) - 1:
             g = g * (z > 0.0)  # ReLU
-        ga, gW, gb = conv_backward(a, layers[k][0], LAYERS[k][2], g)
+        W, s = layers[k][0], LAYERS[k][2]
+        ga, gW, gb = conv_backward(a, W, s, g)
+        if k in bf16_data:
+            ga = conv_backward(a, round_bf16(W), s, round_bf16(g))[0]
+        if k in bf16_weights:
+            gW = conv_backward(round_bf16(a), W, s, round_bf16(g))[1]
         grads[k] = (gW, gb)
         g = ga
     return float(np.mean((y - target) ** 2)), pack(grads)

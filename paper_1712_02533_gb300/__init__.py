@@ -114,6 +114,7 @@ def _load():
         "reg_cnn_forward": ([vp, vp, i32, vp, i32], ctypes.c_int),
         "reg_cnn_loss_grad": ([vp, vp, vp, i32, P(d), vp], ctypes.c_int),
         "reg_cnn_adam_step": ([vp, d, d, d, d], ctypes.c_int),
+        "reg_cnn_loss_grad_tc": ([vp, vp, vp, i32, P(d), vp], ctypes.c_int),
         "reg_cnn_destroy": ([vp], ctypes.c_int),
         "reg_cnn_pairs": ([vp, i32, i32, i32, vp], ctypes.c_int),
         "reg_cnn_init_series": ([vp, i32, vp, i32], ctypes.c_int),
@@ -412,11 +413,12 @@ class Cnn:
         _check(_load().reg_cnn_forward(self.h, x.data_ptr(), b, y.data_ptr(), int(bool(tensor_cores))))
         return y
 
-    def loss_grad(self, x, target, want_grad=False):
+    def loss_grad(self, x, target, want_grad=False, tensor_cores=False):
         loss = ctypes.c_double()
         g = np.empty(self.num_params(), np.float32) if want_grad else None
-        _check(_load().reg_cnn_loss_grad(self.h, x.data_ptr(), target.data_ptr(), int(x.shape[0]),
-                                         ctypes.byref(loss), g.ctypes.data if want_grad else None))
+        fn = _load().reg_cnn_loss_grad_tc if tensor_cores else _load().reg_cnn_loss_grad
+        _check(fn(self.h, x.data_ptr(), target.data_ptr(), int(x.shape[0]), ctypes.byref(loss),
+                  g.ctypes.data if want_grad else None))
         return (loss.value, g) if want_grad else loss.value
 
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -251,6 +251,7 @@ struct reg_cnn {
     float *gy = nullptr;
     double *partial = nullptr, *loss = nullptr;
     uint32_t *wpack = nullptr;  // the 32 -> 32 layers' weights in the tensor-core layout
+    float *wpart = nullptr;     // per-block partial weight gradients of the tensor-core training
     int64_t step = 0;
 };
 
@@ -317,6 +318,8 @@ reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t
 extern "C" {
 
 int64_t reg_cnn_num_params(void) { return total_params(); }
+reg_status reg_cnn_loss_grad_tc(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                                float *grad_out);
 
 reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, reg_cnn_t *out)
 {
@@ -339,7 +342,8 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
          alloc((void **)&h->g1, sizeof(float) * big * max_batch) &&
          alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
          alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double)) &&
-         alloc((void **)&h->wpack, sizeof(uint32_t) * 4 * cnn_conv32_tc_words());
+         alloc((void **)&h->wpack, sizeof(uint32_t) * 4 * cnn_conv32_tc_words()) &&
+         alloc((void **)&h->wpart, sizeof(float) * (size_t)cnn_wgrad32_tc_blocks() * 32 * 288);
     if (!ok) {
         reg_cnn_destroy(h);
         return cnn_fail(REG_ENOMEM, "device allocation failed");
@@ -385,13 +389,32 @@ reg_status reg_cnn_forward(reg_cnn_t h, const float *x, int32_t batch, float *y,
     return REG_OK;
 }
 
+static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                            float *grad_out, bool tc);
+
 reg_status reg_cnn_loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
                              float *grad_out)
+{
+    return loss_grad(h, x, target, batch, loss, grad_out, false);
+}
+
+reg_status reg_cnn_loss_grad_tc(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                                float *grad_out)
+{
+    return loss_grad(h, x, target, batch, loss, grad_out, true);
+}
+
+// Loss and gradient; tc: the four 32 -> 32 layers' forward and weight
+// gradients and the three stride-1 layers' data gradients on the tensor cores
+// (BF16 operands, FP32 accumulation); the 2 -> 32 and 32 -> 2 layers and the
+// stride-2 32 -> 32 layer's data gradient on the CUDA cores in FP32.
+static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
+                            float *grad_out, bool tc)
 {
     if (!h || !x || !target || batch < 1 || batch > h->max_batch) return cnn_fail(REG_EINVAL, "bad argument");
     cudaStream_t st = h->stream;
     const int S = h->side, B = batch;
-    reg_status rs = cnn_forward(h, x, B, nullptr, st, false);
+    reg_status rs = cnn_forward(h, x, B, nullptr, st, tc);
     if (rs != REG_OK) return rs;
     const int64_t ny = act_elems(NL - 1, S) * B;
     const int nb = (int)std::min<int64_t>(1024, (ny + 255) / 256);
@@ -406,6 +429,19 @@ reg_status reg_cnn_loss_grad(reg_cnn_t h, const float *x, const float *target, i
         float *gr = h->grad + param_offset(k);
         float *gx = k == 0 ? nullptr : bufs[k & 1];
         const float *below = k == 0 ? nullptr : h->act[k - 1];
+        if (tc && k >= 1 && k <= 4) {
+            rs = cnn_wgrad32_tc(in, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
+            if (rs != REG_OK) return rs;
+            if (LAYERS[k].S == 1) {
+                rs = cnn_dgrad32_tc(gz, H, th, below, gx, B, st, h->wpack + (k - 1) * cnn_conv32_tc_words());
+                if (rs != REG_OK) return rs;
+            } else {
+                const int Ho = (H + 2 - 3) / LAYERS[k].S + 1, total = B * H * H;
+                k_conv_bwd_data<32, 32, 2><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, th, below, gx, H, total);
+            }
+            gz = gx;
+            continue;
+        }
         switch (k) {
         case 0: bwd<2, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
         case 1: bwd<32, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
@@ -448,6 +484,7 @@ reg_status reg_cnn_destroy(reg_cnn_t h)
     cudaFree(h->g1);
     cudaFree(h->gy);
     cudaFree(h->wpack);
+    cudaFree(h->wpart);
     cudaFree(h->partial);
     cudaFree(h->loss);
     delete h;

@@ -20,5 +20,16 @@ int cnn_max_batch(const reg_cnn *h);
 reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
                          uint32_t *wpack);
 int cnn_conv32_tc_words();
+// Data gradient of a stride-1 32 -> 32 layer on the tensor cores: gx (B x 32 x
+// H x H) = mask(> 0) * conv(gz, W flipped and transposed), gz the gradient with
+// respect to the layer's pre-activation output.
+reg_status cnn_dgrad32_tc(const float *gz, int H, const float *theta, const float *mask, float *gx, int B,
+                          cudaStream_t st, uint32_t *wpack);
+// Weight and bias gradient of a 32 -> 32 layer of stride S on the tensor cores
+// into grad (the layer's W then b); part: device scratch of
+// cnn_wgrad32_tc_blocks() x 32 x 288 floats.
+reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
+                          cudaStream_t st);
+int cnn_wgrad32_tc_blocks();
 // Record an error message for reg_last_error().
 reg_status reg_internal_fail(reg_status st, const char *msg);

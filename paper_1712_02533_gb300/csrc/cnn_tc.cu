@@ -18,6 +18,8 @@
 // 16-byte loads.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "cnn_internal.h"
 
 namespace {
@@ -66,10 +68,15 @@ __global__ void k_pack_w32(const float *__restrict__ theta, uint32_t *__restrict
     wpack[i] = v;
 }
 
-template <int S>
+// DGRAD: the data gradient of a stride-1 layer as the same implicit GEMM --
+// input the output gradient, weights flipped and transposed (k_pack_w32_dgrad),
+// no bias, and the result multiplied by the ReLU mask of the layer below
+// (mask > 0).
+template <int S, bool DGRAD>
 __global__ void __launch_bounds__(128) k_conv32_tc(const float *__restrict__ in, int H,
                                                    const float *__restrict__ theta, const uint32_t *__restrict__ wpack,
-                                                   float *__restrict__ out, int Ho, int tiles_x, int tiles_y)
+                                                   const float *__restrict__ mask, float *__restrict__ out, int Ho,
+                                                   int tiles_x, int tiles_y)
 {
     constexpr int IR = in_rows(S), IC = in_cols(S), PW = pix_words(S);
     extern __shared__ uint32_t smem[];
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(128) k_conv32_tc(const float *__restrict__ in,
         uint4 *dst = reinterpret_cast<uint4 *>(ws);
         for (int i = tid; i < 9 * TC_O * TC_WS / 4; i += blockDim.x) dst[i] = src[i];
     }
-    if (tid < TC_O) bias[tid] = theta[TC_O * TC_K + tid];
+    if (tid < TC_O) bias[tid] = DGRAD ? 0.f : theta[TC_O * TC_K + tid];
     // stage the input tile: one channel pair of one pixel per item (columns fastest)
     const float *img = in + (int64_t)b * TC_C * H * H;
 #pragma unroll 4
@@ -147,36 +154,215 @@ __global__ void __launch_bounds__(128) k_conv32_tc(const float *__restrict__ in,
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const int ox = ox0 + g + 8 * (i >> 1), o = 8 * j + 2 * t + (i & 1);
-                if (ox < Ho)
-                    out[(((int64_t)b * TC_O + o) * Ho + oy) * Ho + ox] = fmaxf(acc[m][j][i] + bias[o], 0.f);
+                if (ox < Ho) {
+                    const int64_t idx = (((int64_t)b * TC_O + o) * Ho + oy) * Ho + ox;
+                    if (DGRAD) out[idx] = mask[idx] > 0.f ? acc[m][j][i] : 0.f;
+                    else out[idx] = fmaxf(acc[m][j][i] + bias[o], 0.f);
+                }
             }
     }
 }
 
-template <int S>
-reg_status launch(const float *in, int H, const float *theta, float *out, int B, cudaStream_t st,
+// Data gradient of a stride-1 layer as a forward convolution of the output
+// gradient: K'[c][o][ey][ex] = W[o][c][2 - ey][2 - ex], packed like
+// k_pack_w32 (tap 3 ey + ex, output channel c, input channel pairs o).
+__global__ void k_pack_w32_dgrad(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * TC_O * TC_WS) return;
+    const int op = i % TC_WS, r2 = i / TC_WS, c = r2 % TC_O, tap = r2 / TC_O;
+    uint32_t v = 0;
+    if (op < TC_C / 2) {
+        const float *w = theta + (int64_t)(2 * op) * TC_K + c * 9 + (8 - tap);
+        v = pack_bf16(w[0], w[TC_K]);
+    }
+    wpack[i] = v;
+}
+
+template <int S, bool DGRAD>
+reg_status launch(const float *in, int H, const float *theta, const float *mask, float *out, int B, cudaStream_t st,
                   uint32_t *wpack)
 {
     const int nw = 9 * TC_O * TC_WS;
-    k_pack_w32<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
+    if (DGRAD) k_pack_w32_dgrad<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
+    else k_pack_w32<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
     const size_t bytes = sizeof(uint32_t) * smem_words(S);
-    if (cudaFuncSetAttribute(k_conv32_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_conv32_tc<S, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
         return reg_internal_fail(REG_ECUDA, "tensor-core convolution: shared memory attribute");
     const int Ho = (H + 2 - 3) / S + 1;
     const int tx = (Ho + TC_TW - 1) / TC_TW, ty = (Ho + TC_TH - 1) / TC_TH;
-    k_conv32_tc<S><<<B * tx * ty, 128, bytes, st>>>(in, H, theta, wpack, out, Ho, tx, ty);
+    k_conv32_tc<S, DGRAD><<<B * tx * ty, 128, bytes, st>>>(in, H, theta, wpack, mask, out, Ho, tx, ty);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core convolution launch");
     return REG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 32 -> 32 layer on the tensor cores:
+//   gW[o][n] = sum_p gz[o][p] A[p][n],  n = (3 dy + dx) * 32 + c,
+// A the im2col of the layer's input (A[p][n] = in_pad[c][S y + dy][S x + dx]
+// for output pixel p = (y, x)), an implicit GEMM with M = 32 output channels,
+// N = 288 and the reduction over all output pixels of the batch, BF16
+// operands and FP32 accumulation (mma.sync m16n8k16).  A block walks output
+// tiles of 8 x 16 pixels (grid-stride), stages per tile the output gradient as
+// BF16 pairs of pixels and the input tile with its halo as BF16, and keeps the
+// 32 x 288 partial in registers: each warp holds both m-tiles of 16 channels
+// and 9 of the 36 n-tiles.  The partials of the blocks are summed in a fixed
+// order by k_wgrad_reduce (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int WG_PW = 68;  // words per output channel row of the staged gradient: 64 pixel pairs + pad
+
+template <int S>
+__global__ void __launch_bounds__(128) k_wgrad32_tc(const float *__restrict__ in, int H, const float *__restrict__ gz,
+                                                    int Ho, int tiles_x, int tiles_y, int n_tiles,
+                                                    float *__restrict__ part)
+{
+    constexpr int IR = in_rows(S), IC = in_cols(S);
+    __shared__ uint32_t gs[TC_O * WG_PW];
+    __shared__ __nv_bfloat16 xs[TC_C * IR * IC];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    float acc[2][9][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int j = 0; j < 9; j++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[m][j][i] = 0.f;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int tx = tile % tiles_x, rest = tile / tiles_x;
+        const int ty = rest % tiles_y, b = rest / tiles_y;
+        const int oy0 = ty * TC_TH, ox0 = tx * TC_TW;
+        const int iy0 = S * oy0 - 1, ix0 = S * ox0 - 1;
+        __syncthreads();  // the previous tile's operands are no longer read
+        // output gradient: pixel pair q of channel o -> pixels 2q, 2q+1 of the tile
+        for (int i = tid; i < TC_O * 64; i += blockDim.x) {
+            const int o = i / 64, q = i % 64, py = q / 8, px = 2 * (q % 8);
+            const int oy = oy0 + py, ox = ox0 + px;
+            float v0 = 0.f, v1 = 0.f;
+            if (oy < Ho) {
+                const float *r = gz + (((int64_t)b * TC_O + o) * Ho + oy) * Ho;
+                if (ox < Ho) v0 = r[ox];
+                if (ox + 1 < Ho) v1 = r[ox + 1];
+            }
+            gs[o * WG_PW + q] = pack_bf16(v0, v1);
+        }
+        // input tile with its halo, BF16, [c][iy][ix]
+        const float *img = in + (int64_t)b * TC_C * H * H;
+        for (int i = tid; i < TC_C * IR * IC; i += blockDim.x) {
+            const int ix = i % IC, r2 = i / IC, iy = r2 % IR, c = r2 / IR;
+            const int gy = iy0 + iy, gx = ix0 + ix;
+            float v = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < H) v = img[((int64_t)c * H + gy) * H + gx];
+            xs[i] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int ks = 0; ks < TC_TH; ks++) {  // one output row of 16 pixels per k-step
+            uint32_t a[2][4];
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                const uint32_t *r0 = gs + (16 * m + g) * WG_PW + 8 * ks + t;
+                const uint32_t *r1 = r0 + 8 * WG_PW;
+                a[m][0] = r0[0];
+                a[m][1] = r1[0];
+                a[m][2] = r0[4];
+                a[m][3] = r1[4];
+            }
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                const int n = (9 * warp + j) * 8 + g;  // im2col column of this thread's B element
+                const int tap = n >> 5, c = n & 31, dy = tap / 3, dx = tap - 3 * dy;
+                const __nv_bfloat16 *row = xs + (c * IR + S * ks + dy) * IC + dx;
+                const uint32_t b0 = (uint32_t)__bfloat16_as_ushort(row[S * (2 * t)]) |
+                                    ((uint32_t)__bfloat16_as_ushort(row[S * (2 * t + 1)]) << 16);
+                const uint32_t b1 = (uint32_t)__bfloat16_as_ushort(row[S * (2 * t + 8)]) |
+                                    ((uint32_t)__bfloat16_as_ushort(row[S * (2 * t + 9)]) << 16);
+#pragma unroll
+                for (int m = 0; m < 2; m++) mma_bf16(acc[m][j], a[m], b0, b1);
+            }
+        }
+    }
+    // this block's partial: part[block][o][n]
+    float *dst = part + (int64_t)blockIdx.x * TC_O * TC_K;
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const int n = (9 * warp + j) * 8 + 2 * t, o = 16 * m + g;
+            *reinterpret_cast<float2 *>(dst + o * TC_K + n) = make_float2(acc[m][j][0], acc[m][j][1]);
+            *reinterpret_cast<float2 *>(dst + (o + 8) * TC_K + n) = make_float2(acc[m][j][2], acc[m][j][3]);
+        }
+}
+
+// Sum of the blocks' partials in block order; scatter to the parameter layout
+// W[o][c][dy][dx] (n = (3 dy + dx) * 32 + c).
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int nblk, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TC_O * TC_K) return;
+    float s = 0.f;
+    for (int k = 0; k < nblk; k++) s += part[(int64_t)k * TC_O * TC_K + i];
+    const int o = i / TC_K, n = i % TC_K, tap = n >> 5, c = n & 31;
+    grad[(o * TC_C + c) * 9 + tap] = s;
+}
+
+// Bias gradient: gb[o] = sum over the batch's output pixels of gz (one block
+// per channel, fixed order).
+__global__ void k_bias_grad(const float *__restrict__ gz, int per, int B, float *__restrict__ gb)
+{
+    const int o = blockIdx.x;
+    float s = 0.f;
+    for (int b = 0; b < B; b++)
+        for (int p = threadIdx.x; p < per; p += blockDim.x) s += gz[((int64_t)b * TC_O + o) * per + p];
+    __shared__ float red[8];
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+        gb[o] = tot;
+    }
+}
+
+template <int S>
+reg_status launch_wgrad(const float *in, int H, const float *gz, int B, float *grad, float *part, int max_blocks,
+                        cudaStream_t st)
+{
+    const int Ho = (H + 2 - 3) / S + 1;
+    const int tx = (Ho + TC_TW - 1) / TC_TW, ty = (Ho + TC_TH - 1) / TC_TH, nt = B * tx * ty;
+    const int nblk = std::min(nt, max_blocks);
+    k_wgrad32_tc<S><<<nblk, 128, 0, st>>>(in, H, gz, Ho, tx, ty, nt, part);
+    k_wgrad_reduce<<<(TC_O * TC_K + 255) / 256, 256, 0, st>>>(part, nblk, grad);
+    k_bias_grad<<<TC_O, 256, 0, st>>>(gz, Ho * Ho, B, grad + TC_O * TC_K);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core weight gradient launch");
+    return REG_OK;
+}
+
 }  // namespace
+
+int cnn_wgrad32_tc_blocks() { return 2 * 152; }
+
+reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
+                          cudaStream_t st)
+{
+    if (S == 1) return launch_wgrad<1>(in, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
+    if (S == 2) return launch_wgrad<2>(in, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
+    return reg_internal_fail(REG_EINVAL, "tensor-core weight gradient: stride must be 1 or 2");
+}
+
+reg_status cnn_dgrad32_tc(const float *gz, int H, const float *theta, const float *mask, float *gx, int B,
+                          cudaStream_t st, uint32_t *wpack)
+{
+    return launch<1, true>(gz, H, theta, mask, gx, B, st, wpack);
+}
 
 int cnn_conv32_tc_words() { return 9 * TC_O * TC_WS; }
 
 reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
                          uint32_t *wpack)
 {
-    if (S == 1) return launch<1>(in, H, theta, out, B, st, wpack);
-    if (S == 2) return launch<2>(in, H, theta, out, B, st, wpack);
+    if (S == 1) return launch<1, false>(in, H, theta, nullptr, out, B, st, wpack);
+    if (S == 2) return launch<2, false>(in, H, theta, nullptr, out, B, st, wpack);
     return reg_internal_fail(REG_EINVAL, "tensor-core convolution: stride must be 1 or 2");
 }

@@ -59,17 +59,18 @@ def training_set(n_pairs, seed=100, frames_per_series=64, n_levels=3, iter_max=5
     return x, t
 
 
-def train(cnn: Cnn, x, t, epochs=4, batch=64, lr=1e-3, log=None, lr_final=None):
+def train(cnn: Cnn, x, t, epochs=4, batch=64, lr=1e-3, log=None, lr_final=None, tensor_cores=False):
     """Adam on contiguous minibatches, the rate decaying geometrically from lr
     to lr_final (if given) over the epochs; returns the mean loss of each
-    epoch."""
+    epoch.  tensor_cores: the loss and gradients of the 32-channel layers on
+    the tensor cores (BF16 operands, FP32 accumulation)."""
     n = int(x.shape[0])
     hist = []
     for ep in range(epochs):
         rate = lr if lr_final is None or epochs < 2 else lr * (lr_final / lr) ** (ep / (epochs - 1))
         tot, cnt = 0.0, 0
         for i in range(0, n - batch + 1, batch):
-            loss = cnn.loss_grad(x[i:i + batch], t[i:i + batch])
+            loss = cnn.loss_grad(x[i:i + batch], t[i:i + batch], tensor_cores=tensor_cores)
             cnn.adam_step(rate)
             tot += loss
             cnt += 1
@@ -85,6 +86,28 @@ def train(cnn: Cnn, x, t, epochs=4, batch=64, lr=1e-3, log=None, lr_final=None):
 _SHAPES = [(2, 32, 128), (32, 32, 64), (32, 32, 64), (32, 32, 64), (32, 32, 64), (32, 2, 64)]  # C, O, output side
 FLOP_PER_PAIR = sum(2 * q * q * o * c * 9 for c, o, q in _SHAPES)
 TC_FLOP_PER_PAIR = sum(2 * q * q * o * c * 9 for c, o, q in _SHAPES[1:5])
+
+
+def training_rate(cnn: Cnn, batch=64, reps=10, tensor_cores=True, seed=0):
+    """Loss-and-gradient passes (forward + backward) of `batch` random pairs
+    and targets, timed with CUDA events on the current stream after two
+    warm-up passes: (ms per pass, TFLOP/s counting 3x the forward's FLOPs:
+    forward, data and weight gradients)."""
+    torch = _torch()
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.randn((batch, 2, 256, 256), generator=g, device="cuda")
+    t = torch.randn((batch, 2, 64, 64), generator=g, device="cuda")
+    for _ in range(2):
+        cnn.loss_grad(x, t, tensor_cores=tensor_cores)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        cnn.loss_grad(x, t, tensor_cores=tensor_cores)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, 3 * FLOP_PER_PAIR * batch / (ms * 1e-3) / 1e12
 
 
 def forward_rate(cnn: Cnn, batch=64, reps=20, tensor_cores=True, seed=0):
@@ -170,7 +193,19 @@ def main(argv=None):
     ap.add_argument("--weights-in", default=None, help="skip training, load parameters (.npy)")
     ap.add_argument("--forward-rate", type=int, default=0, metavar="BATCH",
                     help="only time the forward pass (FP32 and tensor cores) on BATCH random pairs")
+    ap.add_argument("--training-rate", type=int, default=0, metavar="BATCH",
+                    help="only time loss-and-gradient passes (FP32 and tensor cores) on BATCH random pairs")
+    ap.add_argument("--tc-train", action="store_true", help="train with the tensor-core loss and gradients")
     a = ap.parse_args(argv)
+    if a.training_rate:
+        with Cnn(synth.cnn_params(1), side=256, max_batch=a.training_rate) as net:
+            res = {}
+            for tc in (False, True):
+                ms, tf = training_rate(net, batch=a.training_rate, tensor_cores=tc)
+                res["tensor_cores" if tc else "fp32"] = dict(ms_per_pass=ms, tflops_network=tf,
+                                                             pairs_per_s=a.training_rate / ms * 1e3)
+        print(json.dumps(dict(batch=a.training_rate, flop_per_pair=3 * FLOP_PER_PAIR, **res)))
+        return
     if a.forward_rate:
         with Cnn(synth.cnn_params(1), side=256, max_batch=a.forward_rate) as net:
             res = {}
@@ -192,7 +227,8 @@ def main(argv=None):
                             series_kw=gen)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        hist = train(net, x, t, epochs=a.epochs, batch=a.batch, lr=a.lr, lr_final=a.lr_final)
+        hist = train(net, x, t, epochs=a.epochs, batch=a.batch, lr=a.lr, lr_final=a.lr_final,
+                     tensor_cores=a.tc_train)
         torch.cuda.synchronize()
         out.update(pairs=a.pairs, epochs=a.epochs, data_s=t1 - t0, train_s=time.perf_counter() - t1,
                    target_ms_px2=float(t.pow(2).mean()), loss_first=hist[0], loss_last=hist[-1])

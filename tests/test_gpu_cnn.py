@@ -209,3 +209,58 @@ def test_trained_network_gains_over_the_identity_start(reg, syn):
             err[name] = float(np.abs(d[1:] - gt[1:])[:, :, 16:-16, 16:-16].mean())
     assert err["learned"] < 0.8 * err["identity"], err
     assert err["learned_tc"] < 0.8 * err["identity"], err
+
+
+@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3)])
+def test_tensor_core_training_gradients_match_the_bf16_operand_oracle(reg, side, batch):
+    """Training on the tensor cores (reg_cnn_loss_grad_tc): the 32-channel
+    layers' forward and weight gradients and the stride-1 layers' data
+    gradients take BF16 operands.  Against the oracle with the same operand
+    rounding the loss and every parameter gradient agree to FP32 accumulation
+    plus the rare operand that rounds the other way; against the exact oracle
+    they differ by the BF16 operand error.  Side 36 gives ragged tiles."""
+    import torch
+    import synth
+    from oracle import cnn as ocnn
+    rng = np.random.default_rng(side + 1)
+    theta = (synth.cnn_params(9) + 0.01 * rng.standard_normal(ocnn.n_params())).astype(np.float32)
+    x = rng.standard_normal((batch, 2, side, side)).astype(np.float32)
+    q = side // 4
+    t = rng.standard_normal((batch, 2, q, q)).astype(np.float32)
+    with reg.Cnn(theta, side=side, max_batch=batch) as net:
+        loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), want_grad=True,
+                                tensor_cores=True)
+    th, x64, t64 = theta.astype(np.float64), x.astype(np.float64), t.astype(np.float64)
+    lb, gb = ocnn.loss_and_grad(th, x64, t64, bf16_layers=(1, 2, 3, 4), bf16_data=(2, 3, 4),
+                                bf16_weights=(1, 2, 3, 4))
+    le, ge = ocnn.loss_and_grad(th, x64, t64)
+    assert abs(loss - lb) <= 1e-4 * lb, (loss, lb, le)
+    worst_b, worst_e = 0.0, 0.0
+    for k, ((gw, gbias), (bw, bb), (ew, eb)) in enumerate(zip(ocnn.unpack(g.astype(np.float64)), ocnn.unpack(gb),
+                                                             ocnn.unpack(ge))):
+        sc = np.abs(bw).max()
+        err = np.abs(gw - bw)
+        assert err.max() <= 2e-2 * sc and np.median(err) <= 2e-4 * sc, (k, err.max() / sc, np.median(err) / sc)
+        assert np.abs(gbias - bb).max() <= 2e-2 * np.abs(bb).max(), k
+        worst_b = max(worst_b, float(err.max() / sc))
+        worst_e = max(worst_e, float(np.abs(gw - ew).max() / np.abs(ew).max()))
+    print(f"TC training gradients: max rel. error {worst_b:.2e} against the BF16-operand oracle, "
+          f"{worst_e:.2e} against the exact oracle")
+    assert worst_e <= 0.2
+
+
+def test_tensor_core_training_learns(reg, syn):
+    """A network trained with the tensor-core loss and gradients (512
+    large-motion pairs, plain-method targets) lowers its loss like the FP32
+    training does, and its training passes are faster."""
+    from paper_1712_02533_gb300 import learned
+    X, T = learned.training_set(512, seed=100)
+    hist = {}
+    for tc in (False, True):
+        with reg.Cnn(syn.cnn_params(1), side=256, max_batch=64) as net:
+            hist[tc] = learned.train(net, X, T, epochs=6, batch=32, lr=1e-3, tensor_cores=tc)
+            ms, tf = learned.training_rate(net, batch=32, tensor_cores=tc)
+            print(f"training {'tensor cores' if tc else 'CUDA cores'}: losses {[round(h, 5) for h in hist[tc]]}, "
+                  f"{ms:.3f} ms per 32-pair pass, {tf:.1f} TFLOP/s")
+    assert hist[True][-1] < 0.6 * hist[True][0]
+    assert hist[True][-1] < 1.2 * hist[False][-1]

@@ -257,15 +257,17 @@ def test_series_stable_input_matches_oracle(reg, orc, syn, kind, chunks, global_
 @pytest.mark.slow
 def test_config2_stable_series_matches_oracle(reg, orc, syn):
     """A series of config 2's frame size, generator and depth without shot
-    noise (32 x 512^2, 4 levels; 32 of the 128 frames keep the oracle's scan
-    to about a minute), registered as a whole by the Sklansky (=
+    noise (8 x 512^2, 4 levels), registered as a whole by the Sklansky (=
     Ladner-Fischer) tree on both sides: phi_{0,k} within TOL_PX at every node
-    of every frame.  The oracle's result for this input moves by less than
-    1e-5 px under 1e-7 relative perturbations of the frames (measured), so any
-    larger difference is the GPU's."""
+    of every frame.  The oracle's result for this input moves by at most
+    1.5e-6 px under 1e-7 relative perturbations of the frames (measured), so
+    any larger difference is the GPU's.  (Longer series of this size are not
+    stable even without shot noise: with 32 frames the oracle itself moves by
+    up to 0.08 px from frame 9 on, so the node-wise bound would test the
+    method's chaos, not the implementation.)"""
     cfg = dict(syn.CONFIGS["c2_128x512"])
     nl = cfg.pop("n_levels")
-    cfg["n_frames"] = 32
+    cfg["n_frames"] = 8
     fr = syn.series(noise=False, **cfg)
     p = reg.default_params(n_levels=nl, iter_max=50, lam=10.0)
     with reg.Series(fr, p) as s:

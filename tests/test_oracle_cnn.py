@@ -154,3 +154,24 @@ def test_bf16_forward_error_is_within_the_operand_rounding_bound():
     bound = cnn.conv_forward(np.abs(a), np.abs(W), 0 * b, 2) * (2.0 ** -7 + 2.0 ** -16)
     assert np.all(np.abs(rounded - exact) <= bound)
     assert np.abs(rounded - exact).max() > 0
+
+
+def test_bf16_operand_gradients_reduce_to_the_exact_ones_on_bf16_values():
+    """With every operand already a BF16 value (parameters, inputs and a target
+    that keep the intermediate values exact is not possible, so instead: the
+    rounding hooks change nothing when the listed sets are empty, and with all
+    sets listed the result differs from the exact gradient by about the BF16
+    operand error (2^-8 relative), not more."""
+    from oracle import cnn as ocnn
+    import synth
+    rng = np.random.default_rng(5)
+    theta = synth.cnn_params(2).astype(np.float64)
+    x = rng.standard_normal((1, 2, 32, 32))
+    t = rng.standard_normal((1, 2, 8, 8))
+    l0, g0 = ocnn.loss_and_grad(theta, x, t)
+    l1, g1 = ocnn.loss_and_grad(theta, x, t, (), (), ())
+    assert l0 == l1 and np.array_equal(g0, g1)
+    l2, g2 = ocnn.loss_and_grad(theta, x, t, bf16_layers=(1, 2, 3, 4), bf16_data=(2, 3, 4), bf16_weights=(1, 2, 3, 4))
+    rel = np.abs(g2 - g0).max() / np.abs(g0).max()
+    assert 1e-5 < rel < 0.1, rel
+    assert abs(l2 - l0) < 0.05 * l0
