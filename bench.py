@@ -54,14 +54,12 @@ def _args():
     return ap.parse_args()
 
 
-# DRAM bytes (read + written) per algorithmic byte of the step kernels, from an
-# ncu capture of every launch of one kernel family (dram__bytes_read.sum +
-# dram__bytes_write.sum over all launches of the 16-frame 1024^2 preprocessing
-# batch, divided by the algorithmic bytes that the library counts for the same
-# command).  A launch of the full workload processes more nodes of the same
-# kinds, so its traffic scales with its algorithmic bytes.  The figures hold
-# for the kernel source they were taken on: another source reports no traffic.
-TRAFFIC_CAPTURE = {"kernels_cu_sha1": "2c869b02ba391cf4d6c3e08d497d8ee87c132d9e", "trial": 1.059, "grad": 1.119}
+# DRAM bytes (read + written) per algorithmic byte of the step kernels from an
+# ncu capture, for the kernel source it was taken on (a hash of kernels.cu);
+# another source reports no traffic.  No ratio is recorded for the current
+# source: the per-launch captures in profiles/ give DRAM bytes per launch, but
+# not the algorithmic bytes of that one launch.
+TRAFFIC_CAPTURE = {"kernels_cu_sha1": None}
 
 
 def _traffic(family, algo_bytes_per_launch):

@@ -134,17 +134,25 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
 // in_pad[b, c, S y + dy, S x + dx] and gb[o] = sum gz[b, o, ., .].  One block per
 // (o, c), a fixed-order reduction (deterministic).
 // ---------------------------------------------------------------------------
+//
+// With split > 1 the pixels are cut into `split` contiguous parts, one block
+// each (grid O C split), and each block writes its 10 sums to part; the
+// layers with few (o, c) pairs (2 -> 32, 32 -> 2) keep the GPU busy that way,
+// and k_bwd_weight_sum adds the parts in order.
 template <int C, int O, int S>
 __global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict__ in, int H,
                                                          const float *__restrict__ gz, int Ho, int B,
-                                                         float *__restrict__ grad)
+                                                         float *__restrict__ grad, int split,
+                                                         float *__restrict__ part)
 {
-    const int o = blockIdx.x / C, c = blockIdx.x % C;
+    const int oc = blockIdx.x / split, sp = blockIdx.x % split;
+    const int o = oc / C, c = oc % C;
     float acc[10];
 #pragma unroll
     for (int k = 0; k < 10; k++) acc[k] = 0.f;
     const int per = Ho * Ho, total = B * per;
-    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    const int chunk = (total + split - 1) / split, p0 = sp * chunk, p1 = min(total, p0 + chunk);
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const int b = p / per, q = p % per, y = q / Ho, x = q % Ho;
         const float g = gz[((int64_t)b * O + o) * per + q];
         const float *src = in + ((int64_t)b * C + c) * H * H;
@@ -169,9 +177,26 @@ __global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict
     if (threadIdx.x < 10) {
         float t = 0.f;
         for (int w = 0; w < 8; w++) t += red[w][threadIdx.x];
-        if (threadIdx.x < 9) grad[(o * C + c) * 9 + threadIdx.x] = t;
-        else if (c == 0) grad[O * C * 9 + o] = t;
+        if (split > 1) {
+            part[(int64_t)blockIdx.x * 10 + threadIdx.x] = t;
+        } else {
+            if (threadIdx.x < 9) grad[(o * C + c) * 9 + threadIdx.x] = t;
+            else if (c == 0) grad[O * C * 9 + o] = t;
+        }
     }
+}
+
+// The parts of k_conv_bwd_weight in order (one thread per (o, c) and sum).
+template <int C, int O>
+__global__ void k_bwd_weight_sum(const float *__restrict__ part, int split, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= O * C * 10) return;
+    const int oc = i / 10, k = i % 10, o = oc / C, c = oc % C;
+    float t = 0.f;
+    for (int sp = 0; sp < split; sp++) t += part[((int64_t)oc * split + sp) * 10 + k];
+    if (k < 9) grad[(o * C + c) * 9 + k] = t;
+    else if (c == 0) grad[O * C * 9 + o] = t;
 }
 
 // Mean squared error: per-block partial sums (double), then one block adds them
@@ -229,10 +254,13 @@ void fwd(const float *in, int H, const float *theta, float *out, int B, cudaStre
 
 template <int C, int O, int S>
 void bwd(const float *in, int H, const float *gz, const float *theta, const float *a_below, float *gx, float *grad,
-         int B, cudaStream_t st)
+         int B, cudaStream_t st, float *part)
 {
     const int Ho = (H + 2 - 3) / S + 1;
-    k_conv_bwd_weight<C, O, S><<<O * C, 256, 0, st>>>(in, H, gz, Ho, B, grad);
+    // (o, c) pairs times parts of the pixel range: about a thousand blocks
+    const int split = (O * C >= 512) ? 1 : std::min(64, 1024 / (O * C));
+    k_conv_bwd_weight<C, O, S><<<O * C * split, 256, 0, st>>>(in, H, gz, Ho, B, grad, split, part);
+    if (split > 1) k_bwd_weight_sum<C, O><<<(O * C * 10 + 255) / 256, 256, 0, st>>>(part, split, grad);
     if (gx) {
         const int total = B * H * H;
         k_conv_bwd_data<C, O, S><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
@@ -343,7 +371,7 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
          alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
          alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double)) &&
          alloc((void **)&h->wpack, sizeof(uint32_t) * 4 * cnn_conv32_tc_words()) &&
-         alloc((void **)&h->wpart, sizeof(float) * (size_t)cnn_wgrad32_tc_blocks() * 32 * 288);
+         alloc((void **)&h->wpart, sizeof(float) * (size_t)(cnn_wgrad32_tc_blocks() + 1) * 32 * 288);
     if (!ok) {
         reg_cnn_destroy(h);
         return cnn_fail(REG_ENOMEM, "device allocation failed");
@@ -443,12 +471,12 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
             continue;
         }
         switch (k) {
-        case 0: bwd<2, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
-        case 1: bwd<32, 32, 2>(in, H, gz, th, below, gx, gr, B, st); break;
+        case 0: bwd<2, 32, 2>(in, H, gz, th, below, gx, gr, B, st, h->wpart); break;
+        case 1: bwd<32, 32, 2>(in, H, gz, th, below, gx, gr, B, st, h->wpart); break;
         case 2:
         case 3:
-        case 4: bwd<32, 32, 1>(in, H, gz, th, below, gx, gr, B, st); break;
-        default: bwd<32, 2, 1>(in, H, gz, th, below, gx, gr, B, st); break;
+        case 4: bwd<32, 32, 1>(in, H, gz, th, below, gx, gr, B, st, h->wpart); break;
+        default: bwd<32, 2, 1>(in, H, gz, th, below, gx, gr, B, st, h->wpart); break;
         }
         gz = gx;
     }

@@ -27,7 +27,7 @@ reg_status cnn_dgrad32_tc(const float *gz, int H, const float *theta, const floa
                           cudaStream_t st, uint32_t *wpack);
 // Weight and bias gradient of a 32 -> 32 layer of stride S on the tensor cores
 // into grad (the layer's W then b); part: device scratch of
-// cnn_wgrad32_tc_blocks() x 32 x 288 floats.
+// (cnn_wgrad32_tc_blocks() + 1) x 32 x 288 floats.
 reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
                           cudaStream_t st);
 int cnn_wgrad32_tc_blocks();

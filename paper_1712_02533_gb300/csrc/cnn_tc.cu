@@ -306,14 +306,21 @@ __global__ void k_wgrad_reduce(const float *__restrict__ part, int nblk, float *
     grad[(o * TC_C + c) * 9 + tap] = s;
 }
 
-// Bias gradient: gb[o] = sum over the batch's output pixels of gz (one block
-// per channel, fixed order).
-__global__ void k_bias_grad(const float *__restrict__ gz, int per, int B, float *__restrict__ gb)
+// Bias gradient: gb[o] = sum over the batch's output pixels of gz.  Block
+// (o, part) sums one contiguous part of channel o's B x per values into
+// bpart; k_bias_grad_sum adds the parts in order (deterministic).
+constexpr int BG_SPLIT = 32;
+
+__global__ void k_bias_grad(const float *__restrict__ gz, int per, int B, float *__restrict__ bpart)
 {
-    const int o = blockIdx.x;
+    const int o = blockIdx.x / BG_SPLIT, sp = blockIdx.x % BG_SPLIT;
+    const int total = B * per, chunk = (total + BG_SPLIT - 1) / BG_SPLIT;
+    const int q0 = sp * chunk, q1 = min(total, q0 + chunk);
     float s = 0.f;
-    for (int b = 0; b < B; b++)
-        for (int p = threadIdx.x; p < per; p += blockDim.x) s += gz[((int64_t)b * TC_O + o) * per + p];
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const int b = q / per, p = q - b * per;
+        s += gz[((int64_t)b * TC_O + o) * per + p];
+    }
     __shared__ float red[8];
     for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -321,8 +328,17 @@ __global__ void k_bias_grad(const float *__restrict__ gz, int per, int B, float 
     if (threadIdx.x == 0) {
         float tot = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
-        gb[o] = tot;
+        bpart[blockIdx.x] = tot;
     }
+}
+
+__global__ void k_bias_grad_sum(const float *__restrict__ bpart, float *__restrict__ gb)
+{
+    const int o = threadIdx.x;
+    if (o >= TC_O) return;
+    float t = 0.f;
+    for (int sp = 0; sp < BG_SPLIT; sp++) t += bpart[o * BG_SPLIT + sp];
+    gb[o] = t;
 }
 
 template <int S>
@@ -334,14 +350,26 @@ reg_status launch_wgrad(const float *in, int H, const float *gz, int B, float *g
     const int nblk = std::min(nt, max_blocks);
     k_wgrad32_tc<S><<<nblk, 128, 0, st>>>(in, H, gz, Ho, tx, ty, nt, part);
     k_wgrad_reduce<<<(TC_O * TC_K + 255) / 256, 256, 0, st>>>(part, nblk, grad);
-    k_bias_grad<<<TC_O, 256, 0, st>>>(gz, Ho * Ho, B, grad + TC_O * TC_K);
+    // the bias parts after the weight partials in the scratch (part has room:
+    // max_blocks x 32 x 288 floats, the weight partials use nblk of them)
+    float *bpart = part + (int64_t)nblk * TC_O * TC_K;
+    k_bias_grad<<<TC_O * BG_SPLIT, 256, 0, st>>>(gz, Ho * Ho, B, bpart);
+    k_bias_grad_sum<<<1, 32, 0, st>>>(bpart, grad + TC_O * TC_K);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core weight gradient launch");
     return REG_OK;
 }
 
 }  // namespace
 
-int cnn_wgrad32_tc_blocks() { return 2 * 152; }
+// Blocks of the weight-gradient kernel: three resident per SM (its register
+// limit) on every SM of the current device.
+int cnn_wgrad32_tc_blocks()
+{
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 152;
+    return 3 * nsm;
+}
 
 reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
                           cudaStream_t st)

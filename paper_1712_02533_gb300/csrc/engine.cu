@@ -21,7 +21,9 @@
 // kernels (kernels.cu)
 __global__ void k_embed(const float *, int64_t, int64_t, int, float *, int64_t, int);
 __global__ void k_restrict_img(const float *, int64_t, int, int, float *, int64_t, int);
-__global__ void k_image_stats(const float *, int64_t, int, int, double *);
+void launch_image_stats(const float *img, int64_t stride, int pitch, int n, int n_img, double *part, double *out,
+                        cudaStream_t st);
+int image_stats_part_doubles(int n_img);
 __global__ void k_normalize(const float *, int64_t, int, int, const double *, void *, int64_t, int, int);
 __global__ void k_mass_image(const void *, int64_t, int, int, int, float *, int64_t);
 __global__ void k_compose(BatchDev);
@@ -933,8 +935,8 @@ void build_levels(reg_series *s, SeriesInfo &si, float *rawf, int f0, int nf, do
             rawf + si.img_off[k + 1], (int64_t)si.frame_block, si.pitch[k + 1], si.n[k + 1],
             rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k]);
     for (int k = 0; k < si.nl; k++) {
-        k_image_stats<<<nf, 512, 0, s->stream>>>(rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k],
-                                                 si.n[k], stats);
+        launch_image_stats(rawf + si.img_off[k], (int64_t)si.frame_block, si.pitch[k], si.n[k], nf, stats + 2 * nf,
+                           stats, s->stream);
         size_t esz = s->bf16 ? 2 : 4;
         char *dst = (char *)si.pyr + ((size_t)f0 * si.frame_block + si.img_off[k]) * esz;
         k_normalize<<<dim3(cdiv(si.n[k], 32), cdiv(si.n[k], 8), nf), blk, 0, s->stream>>>(
@@ -1128,7 +1130,8 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         void *raw = nullptr, *stage = nullptr, *stats = nullptr;
         size_t raw_bytes = (size_t)chunk * si.frame_block * 4;
         if ((st = dalloc(s, &raw, raw_bytes)) != REG_OK) return cleanup(st);
-        if ((st = dalloc(s, &stats, sizeof(double) * 2 * chunk)) != REG_OK) return cleanup(st);
+        if ((st = dalloc(s, &stats, sizeof(double) * (2 * chunk + image_stats_part_doubles(chunk)))) != REG_OK)
+            return cleanup(st);
         size_t stage_bytes = (size_t)chunk * si.side * si.side * 4;
         if (!frames_on_device && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
         for (int f0 = 0; f0 < si.n_frames; f0 += chunk) {
@@ -1394,7 +1397,7 @@ reg_status reg_average_series(reg_series_t s, int32_t series, int32_t iterations
     const int kL = si.nl - 1, nL = si.n[kL];
     void *raw = nullptr, *stats = nullptr;
     RET(dalloc(s, &raw, si.frame_block * sizeof(float)));
-    reg_status st = dalloc(s, &stats, 2 * sizeof(double));
+    reg_status st = dalloc(s, &stats, sizeof(double) * (2 + image_stats_part_doubles(1)));
     if (st != REG_OK) {
         dfree(s, raw, 0);
         return st;

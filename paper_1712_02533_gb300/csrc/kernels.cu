@@ -187,51 +187,70 @@ __global__ void k_restrict_img(const float *__restrict__ fine, int64_t fstride, 
 }
 
 // Per image: FE mean (w^T F) and FE standard deviation ((F-mean)^T M (F-mean))^1/2,
-// two passes over the cells in double; one block per image.
-__global__ void k_image_stats(const float *__restrict__ img, int64_t stride, int pitch, int n, double *out)
+// two passes over the cells in double.  Each image's cell rows are cut into
+// STATS_SPLIT parts, one block each (grid: parts, images); the parts' sums
+// go to `part` and are added in order by k_image_stats_fin (deterministic).
+constexpr int STATS_SPLIT = 32;
+
+__device__ __forceinline__ double block_sum_d(double v, double *red)
 {
-    const float *F = img + blockIdx.x * stride;
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// pass 0: sum of the cell means; pass 1: sum of the cell mass forms of F - mean
+__global__ void k_image_stats_part(const float *__restrict__ img, int64_t stride, int pitch, int n, int pass,
+                                   const double *__restrict__ stats, double *__restrict__ part)
+{
+    const float *F = img + blockIdx.y * stride;
     __shared__ double red[32];
-    __shared__ double mean_s;
-    int cells = (n - 1) * (n - 1);
-    double h2 = 1.0 / ((double)(n - 1) * (n - 1));
+    const int rows = n - 1, per = (rows + STATS_SPLIT - 1) / STATS_SPLIT;
+    const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+    const double m = pass ? stats[2 * blockIdx.y] : 0.0;
     double s = 0.0;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        int r = k / (n - 1), c = k % (n - 1);
+    for (int k = threadIdx.x; k < (r1 - r0) * (n - 1); k += blockDim.x) {
+        const int r = r0 + k / (n - 1), c = k % (n - 1);
         const float *p = F + (int64_t)r * pitch + c;
-        s += 0.25 * ((double)p[0] + p[1] + p[pitch] + p[pitch + 1]);
-    }
-    s = warp_sum_d(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        v = warp_sum_d(v);
-        if (threadIdx.x == 0) mean_s = v * h2;
-    }
-    __syncthreads();
-    double m = mean_s;
-    double q = 0.0;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        int r = k / (n - 1), c = k % (n - 1);
-        const float *p = F + (int64_t)r * pitch + c;
-        double a = p[0] - m, b = p[1] - m, cc = p[pitch + 1] - m, d = p[pitch] - m;  // cyclic a b c d
-        q += (4.0 * (a * a + b * b + cc * cc + d * d) + 4.0 * (a * b + b * cc + cc * d + d * a) +
-              2.0 * (a * cc + b * d)) / 36.0;
-    }
-    q = warp_sum_d(q);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        v = warp_sum_d(v);
-        if (threadIdx.x == 0) {
-            out[2 * blockIdx.x] = m;
-            out[2 * blockIdx.x + 1] = sqrt(v * h2);
+        if (!pass) {
+            s += 0.25 * ((double)p[0] + p[1] + p[pitch] + p[pitch + 1]);
+        } else {
+            const double a = p[0] - m, b = p[1] - m, cc = p[pitch + 1] - m, d = p[pitch] - m;  // cyclic a b c d
+            s += (4.0 * (a * a + b * b + cc * cc + d * d) + 4.0 * (a * b + b * cc + cc * d + d * a) +
+                  2.0 * (a * cc + b * d)) / 36.0;
         }
     }
+    const double t = block_sum_d(s, red);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * STATS_SPLIT + blockIdx.x] = t;
 }
+
+// One thread per image: the parts in order; pass 0 writes the mean, pass 1 sigma.
+__global__ void k_image_stats_fin(int n_img, int n, int pass, const double *__restrict__ part, double *__restrict__ out)
+{
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= n_img) return;
+    double t = 0.0;
+    for (int k = 0; k < STATS_SPLIT; k++) t += part[(int64_t)z * STATS_SPLIT + k];
+    const double h2 = 1.0 / ((double)(n - 1) * (n - 1));
+    if (!pass) out[2 * z] = t * h2;
+    else out[2 * z + 1] = sqrt(t * h2);
+}
+
+void launch_image_stats(const float *img, int64_t stride, int pitch, int n, int n_img, double *part, double *out,
+                        cudaStream_t st)
+{
+    for (int pass = 0; pass < 2; pass++) {
+        k_image_stats_part<<<dim3(STATS_SPLIT, n_img), 256, 0, st>>>(img, stride, pitch, n, pass, out, part);
+        k_image_stats_fin<<<(n_img + 127) / 128, 128, 0, st>>>(n_img, n, pass, part, out);
+    }
+}
+
+int image_stats_part_doubles(int n_img) { return n_img * STATS_SPLIT; }
 
 // F~ = (F - mean) / sigma into float or bf16 storage. grid (x, y, images).
 __global__ void k_normalize(const float *__restrict__ img, int64_t stride, int pitch, int n, const double *stats,
