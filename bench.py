@@ -50,6 +50,8 @@ def _args():
                     help="pairs in the tile autotuner's sample batch before timing (0: default tiles)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cnn", action="store_true", help="skip the CNN tensor-core roofline entry")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser leg")
+    ap.add_argument("--learned-pairs", type=int, default=2048, help="training pairs of the learned leg")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -172,6 +174,57 @@ def cnn_roofline(reg, s, torch, batch=64, reps=20):
             "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tflops / peak, 5),
             "peak_source": src, "batch": batch, "ms_per_forward": round(ms, 4),
             "gflop_per_pair": round(flop_pair / 1e9, 4), "traffic": None}
+
+
+def learned_leg(reg, fd, cfg, kind, chunks, plain_d, tiles, n_pairs=2048, epochs=10):
+    """The learned form on the benchmark's series: a network trained on the
+    tensor cores on n_pairs neighbour pairs of other generator series of the
+    same shape (targets: the plain method's displacements), then the series
+    registered with the network's start on the finest level (the plain method
+    judging every start), timed with CUDA events from resident frames to all
+    deformations, network inference included; its distance to the plain
+    result of the timed steps is reported beside the time."""
+    import torch
+    import synth
+    from paper_1712_02533_gb300 import learned
+    gen = {k: v for k, v in synth.CONFIGS["c3_400x1024"].items() if k not in ("seed", "n_frames", "side", "n_levels")}
+    t0 = time.time()
+    x, t = learned.training_set(n_pairs, seed=4000, frames_per_series=64, n_levels=cfg["n_levels"], side=cfg["side"],
+                                series_kw=gen)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    net = reg.Cnn(synth.cnn_params(1), side=256, max_batch=64)
+    hist = learned.train(net, x, t, epochs=epochs, batch=32, lr=1e-3, lr_final=1e-4, tensor_cores=True)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    del x, t
+    p = reg.default_params(n_levels=cfg["n_levels"], iter_max=cfg["iter_max"], lam=cfg["lam"], init_levels=1)
+    if tiles:
+        p.trials_per_pass = tiles["trials_per_pass"]
+    with reg.Series([fd], p) as s:
+        for lv in (tiles or {}).get("levels", []):
+            s.set_tile_rows(lv["level"], lv["grad_rows"], lv["trial_rows"])
+        s.cnn_init(net, tensor_cores=True)  # warm-up run (graph capture, workspace)
+        s.prefix_scan(kind, chunks, reg.KOGGE_STONE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.cnn_init(net, tensor_cores=True)
+        rep = s.prefix_scan(kind, chunks, reg.KOGGE_STONE)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        d = torch.empty_like(plain_d)
+        s.get_deformations(out=d)
+    net.close()
+    m = 32
+    dev = (d[1:] - plain_d[1:]).abs()[:, :, m:-m, m:-m]
+    return {"form": "learned start on the finest level (network trained on the tensor cores)",
+            "series_ms": round(ms, 2), "op_apps_per_s": round(rep["ops"] / (ms * 1e-3), 3),
+            "dev_from_plain_mean_px": float(dev.mean()), "dev_from_plain_max_px": float(dev.max()),
+            "frac_within_0.05px": float((dev <= 0.05).float().mean()), "judged": rep.get("learned"),
+            "iters": rep["iters"], "train_pairs": n_pairs, "epochs": epochs, "loss_first": hist[0],
+            "loss_last": hist[-1], "data_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1)}
 
 
 class ClockSampler:
@@ -391,6 +444,13 @@ def main():
     roofline["profiled_step_ms"] = round(prof_rep["ms"], 2) if prof_rep.get("ms") else None
     gpu_launches = int(sum(v["launches"] for k, v in timed.items() if k in FAMILIES))
     roofline_cnn = None if a.preprocess_only or a.no_cnn else cnn_roofline(reg, s, torch)
+    learned_res = None
+    if not (a.preprocess_only or a.no_learned) and world == 1:
+        plain_d = torch.empty((cfg["n_frames"], 2, cfg["side"], cfg["side"]), dtype=torch.float32, device=dev)
+        s.get_deformations(out=plain_d)
+        learned_res = learned_leg(reg, fd, cfg, kind, a.chunks, plain_d, tiles, n_pairs=a.learned_pairs)
+        learned_res["plain_series_ms"] = round(ms_step, 2)
+        learned_res["speedup_vs_plain"] = round(ms_step / learned_res["series_ms"], 4)
 
     # end to end through the C-ABI with host buffers (upload, pyramid, scan, download)
     e2e = None
@@ -439,7 +499,7 @@ def main():
                        "l2": "working set (GBs) larger than L2; no flush",
                        "tiles": tiles,
                        "generator_s": round(gen_s, 1), "create_ms": round(create_s * 1e3, 1)},
-            "roofline": roofline, "roofline_cnn": roofline_cnn, "cpu_baseline": cb, "e2e": e2e,
+            "roofline": roofline, "roofline_cnn": roofline_cnn, "learned": learned_res, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }

@@ -189,6 +189,7 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=400)
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--init-levels", default="5,4,3,1")
+    ap.add_argument("--iter-max", type=int, default=50, help="gradient steps per level of the compared forms")
     ap.add_argument("--weights-out", default=None, help="save the trained parameters (.npy)")
     ap.add_argument("--weights-in", default=None, help="skip training, load parameters (.npy)")
     ap.add_argument("--forward-rate", type=int, default=0, metavar="BATCH",
@@ -236,7 +237,8 @@ def main(argv=None):
         if a.weights_out:
             np.save(a.weights_out, net.get_params())
     frames, gt, _ = synth.series(a.eval_seed, a.frames, a.side, ground_truth=True, **gen)
-    out["rows"] = compare(net, frames, gt, init_levels=tuple(int(v) for v in a.init_levels.split(",")))
+    out["iter_max"] = a.iter_max
+    out["rows"] = compare(net, frames, gt, iter_max=a.iter_max, init_levels=tuple(int(v) for v in a.init_levels.split(",")))
     print(json.dumps(out))
 
 

@@ -115,11 +115,18 @@ def _agreeing_fields_ok(rec):
             and rec["E_rel"] <= TOL_E)
 
 
-def energy_rel(orc, R, T, gpu_px, orc_px, lam):
-    """Oracle FP64 energy at both fields: (E at the GPU field - E at the oracle
-    field) / |E at the oracle field|."""
-    side = gpu_px.shape[-1] - 1
-    eg, _ = orc.energy(R, T, np.asarray(gpu_px, np.float64) / side, lam)
+def gpu_energy_fn(series, frame_i, frame_k, level, series_index=0):
+    """The GPU's own energy of a field of its (reg_eval_energy, itself held to
+    the oracle's energy to 1e-5 of |NCC| + |reg| and measured at ~1e-8)."""
+    return lambda u: float(series.eval_energy(frame_i, frame_k, level, np.asarray(u, np.float32),
+                                              series=series_index)["E"])
+
+
+def energy_rel(gpu_energy, gpu_px, orc, R, T, orc_px, lam):
+    """(E of the GPU's field, by the GPU - E of the oracle's field, by the
+    oracle) / |E of the oracle's field|: every oracle input is the oracle's."""
+    side = np.asarray(orc_px).shape[-1] - 1
+    eg = gpu_energy(gpu_px)
     eo, _ = orc.energy(R, T, np.asarray(orc_px, np.float64) / side, lam)
     return (eg - eo) / abs(eo), eo
 
@@ -167,21 +174,24 @@ def perturbed_spread(orc, R, T, p, u_init_omega, orc_px, lam, n=2, seed=0):
     rng = np.random.default_rng(seed)
     Ts = [T * (1.0 + PERTURB_REL * rng.standard_normal(T.shape)) for _ in range(n)]
 
+    eo, _ = orc.energy(R, T, np.asarray(orc_px, np.float64) / side, lam)
+
     def one(Tp):
         u, _, _ = orc.register(R, Tp, p, u_init=u_init_omega)
-        e_rel, _ = energy_rel(orc, R, T, u * side, orc_px, lam)
-        return float(np.abs(u * side - orc_px).max()), abs(e_rel)
+        ep, _ = orc.energy(R, T, u, lam)
+        return float(np.abs(u * side - orc_px).max()), abs(ep - eo) / abs(eo)
 
     with ThreadPoolExecutor(max_workers=n) as ex:
         res = list(ex.map(one, Ts))
     return max(r[0] for r in res), max(r[1] for r in res)
 
 
-def free_running_parity(orc, gpu_px, orc_px, gtr, otr, what, R, T, p, lam, u_init_omega=None):
-    """Free-running comparison of one operator (see the module docstring).
-    Returns the record of what was compared."""
+def free_running_parity(orc, gpu_px, orc_px, gtr, otr, what, R, T, p, lam, gpu_energy, u_init_omega=None):
+    """Free-running comparison of one operator (see the module docstring);
+    gpu_energy: the GPU's energy of a field (gpu_energy_fn).  Returns the
+    record of what was compared."""
     rec = dict(what=what, mode="free", **field_stats(gpu_px, orc_px))
-    e_rel, e0 = energy_rel(orc, R, T, gpu_px, orc_px, lam)
+    e_rel, e0 = energy_rel(gpu_energy, gpu_px, orc, R, T, orc_px, lam)
     rec["E_rel"] = e_rel
     if rec["max_px"] <= TOL_PX:
         rec["criterion"] = "fields"
@@ -225,7 +235,7 @@ def lockstep_parity(orc, series, op, dst, n_levels, otr, orc_px, what, R, T, lam
         series.set_lockstep(None)
     got, _ = series.get_slot(dst, series=slot_series)
     rec = dict(what=what, mode="lockstep", steps=int(len(taus)), **field_stats(got, orc_px))
-    e_rel, e0 = energy_rel(orc, R, T, got, orc_px, lam)
+    e_rel, e0 = energy_rel(gpu_energy_fn(series, op[4], op[5], L, op[0]), got, orc, R, T, orc_px, lam)
     rec["E_rel"] = e_rel
     assert len(gtr) == len(taus), (rec, len(gtr))
     assert np.array_equal(gtr[:, 3], taus), rec

@@ -99,13 +99,15 @@ def test_config5_sampled_operators_against_the_oracle(reg, orc, syn):
                         s.set_lockstep(None)
                     lgot = s.get_slot(0, series=k)[0]
                     rec = dict(what=what, mode="lockstep", steps=len(taus), **P.field_stats(lgot, u * side))
-                    rec["E_rel"] = P.energy_rel(orc, g[k][0], g[k][1], lgot, u * side, lam)[0]
+                    gpu_e = P.gpu_energy_fn(s, 1, 2, L, k)
+                    rec["E_rel"] = P.energy_rel(gpu_e, lgot, orc, g[k][0], g[k][1], u * side, lam)[0]
                     P.report("c5", rec)
                     assert rec["max_px"] <= P.TOL_PX or P._agreeing_fields_ok(rec), rec
                     P.report("c5", P.free_running_parity(orc, got[k], u * side, tr[tr[:, 0] == k][:, 1:], rows,
-                                                         what, g[k][0], g[k][1], op, lam))
+                                                         what, g[k][0], g[k][1], op, lam, gpu_e))
                 else:
                     rec = dict(what=what, mode="free", **P.field_stats(got[k], u * side))
-                    rec["E_rel"] = P.energy_rel(orc, g[k][0], g[k][1], got[k], u * side, lam)[0]
+                    rec["E_rel"] = P.energy_rel(P.gpu_energy_fn(s, 1, 2, int(np.log2(side)), k), got[k], orc,
+                                                g[k][0], g[k][1], u * side, lam)[0]
                     P.report("c5", rec)
                     assert np.isfinite(rec["max_px"])

@@ -15,11 +15,6 @@ TOL_PX = P.TOL_PX
 TOL_E = P.TOL_E
 
 
-def orc_energy(R, T, u, lam):
-    import oracle
-    return oracle.energy(R, T, u, lam)
-
-
 @pytest.fixture(scope="module")
 def reg():
     import torch
@@ -112,14 +107,17 @@ def test_trial_pass_matches_oracle(reg, orc, syn, side, nl):
             level = L - nl + 1 + k
             for seed, amp in [(0, 0.5), (3, 2.5)]:
                 ug = _rand_u(n, seed, amp).astype(np.float32)
+                uo = ug.astype(np.float64) * h
+                # the oracle's own direction (the GPU's agrees to ~1e-7 of its
+                # maximum, test_direction_matches_oracle) and step sizes from it
+                do = -orc.gradient(Rp[k], Tp[k], uo, lam) / orc.lumped(n)
+                taus = moves / float(np.abs(do / h).max())
                 d0, _ = s.eval_direction(0, 1, level, ug)
-                taus = moves / float(np.abs(d0).max())
                 d, dE = s.eval_trials(0, 1, level, ug, taus)
                 assert np.array_equal(d, d0)
-                uo = ug.astype(np.float64) * h
                 E0, _ = orc.energy(Rp[k], Tp[k], uo, lam)
                 for j, t in enumerate(taus):
-                    E1, _ = orc.energy(Rp[k], Tp[k], uo + t * d.astype(np.float64) * h, lam)
+                    E1, _ = orc.energy(Rp[k], Tp[k], uo + t * do, lam)
                     want = E1 - E0
                     assert abs(dE[j] - want) <= 1e-4 * abs(want) + 1e-9 * abs(E0), (level, seed, moves[j], dE[j], want)
 
@@ -186,7 +184,8 @@ def test_config1_operators_match_oracle(reg, orc, syn):
         n_exact = 0
         for e in range(n):
             u, status, stl, rows = res[e]
-            rec = P.free_running_parity(orc, got[e], u * 64, gtr[e], rows, f"c1 A({e},{e + 1})", g[e], g[e + 1], op, lam)
+            rec = P.free_running_parity(orc, got[e], u * 64, gtr[e], rows, f"c1 A({e},{e + 1})", g[e], g[e + 1], op, lam,
+                                        P.gpu_energy_fn(s, e, e + 1, 6))
             P.report("c1", rec)
             n_exact += rec["criterion"] == "fields"
             P.report("c1", P.lockstep_parity(orc, s, (0, -1, -1, e, e, e + 1), e, nl, rows, u * 64,
@@ -219,7 +218,7 @@ def test_config1_scan_operators_match_oracle(reg, orc, syn):
             u, _, _, rows = _orc_traced(orc, g[0], g[k + 1], op, orc.compose(left, right))
             what = f"c1 B(0,{k},{k + 1})"
             P.report("c1", P.free_running_parity(orc, got, u * 64, gtr, rows, what, g[0], g[k + 1], op, lam,
-                                                  u_init_omega=orc.compose(left, right)))
+                                                  P.gpu_energy_fn(s, 0, k + 1, 6), u_init_omega=orc.compose(left, right)))
             s.set_slot(0, acc, 0, k)
             s.set_slot(1, A[k], k, k + 1)
             P.report("c1", P.lockstep_parity(orc, s, (0, 0, 1, 2, 0, k + 1), 2, nl, rows, u * 64, what,
@@ -308,7 +307,8 @@ def test_config2_sampled_operators_match_oracle(reg, orc, syn):
             what = f"c2 A({e},{e + 1})"
             P.report("c2", P.lockstep_parity(orc, s, (0, -1, -1, 5, e, e + 1), 5, nl, rows, u * side, what,
                                              g[e], g[e + 1], lam))
-            P.report("c2", P.free_running_parity(orc, got[e], u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam))
+            P.report("c2", P.free_running_parity(orc, got[e], u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam,
+                                                  P.gpu_energy_fn(s, e, e + 1, 9)))
         # B(0,1,2) on the oracle's A(0,1) and A(1,2), rounded to float32 pixels
         a01, a12 = _f32_px(res[0][0], side), _f32_px(res[1][0], side)
         left, right = a01.astype(np.float64) / side, a12.astype(np.float64) / side
@@ -322,7 +322,7 @@ def test_config2_sampled_operators_match_oracle(reg, orc, syn):
         gotb = s.get_slot(2)[0]
         gtr2 = s.get_trace()[:, 1:]
         P.report("c2", P.free_running_parity(orc, gotb, u * side, gtr2, rows, "c2 B(0,1,2)", g[0], g[2], op, lam,
-                                              u_init_omega=orc.compose(left, right)))
+                                              P.gpu_energy_fn(s, 0, 2, 9), u_init_omega=orc.compose(left, right)))
 
 
 def test_identical_frames_give_zero_displacement(reg, syn):
@@ -375,7 +375,8 @@ def test_full_size_sampled_operators_match_oracle(reg, orc, syn):
             what = f"c3 A({e},{e + 1})"
             P.report("c3", P.lockstep_parity(orc, s, (0, -1, -1, 5, e, e + 1), 5, nl, rows, u * side, what,
                                              g[e], g[e + 1], lam))
-            P.report("c3", P.free_running_parity(orc, u_gpu, u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam))
+            P.report("c3", P.free_running_parity(orc, u_gpu, u * side, gtr[e], rows, what, g[e], g[e + 1], op, lam,
+                                                  P.gpu_energy_fn(s, e, e + 1, 10)))
         a01, a12 = _f32_px(res[0][0], side), _f32_px(res[1][0], side)
         left, right = a01.astype(np.float64) / side, a12.astype(np.float64) / side
         u, _, _, rows = _orc_traced(orc, g[0], g[2], op, orc.compose(left, right))
@@ -388,4 +389,4 @@ def test_full_size_sampled_operators_match_oracle(reg, orc, syn):
         gotb = s.get_slot(2)[0]
         gtr2 = s.get_trace()[:, 1:]
         P.report("c3", P.free_running_parity(orc, gotb, u * side, gtr2, rows, "c3 B(0,1,2)", g[0], g[2], op, lam,
-                                              u_init_omega=orc.compose(left, right)))
+                                              P.gpu_energy_fn(s, 0, 2, 10), u_init_omega=orc.compose(left, right)))

@@ -52,13 +52,14 @@ def _rotated_pair(side, alpha, t, seed=4):
     return np.stack([img(X, Y), img(Q[0], Q[1])]).astype(np.float32)
 
 
-def _check(orc, R, T, th_gpu, th_orc, lam, side, what):
-    e_g = orc.rigid_energy(R, T, th_gpu, lam)
+def _check(orc, R, T, th_gpu, field_gpu, e_gpu, th_orc, lam, side, what):
+    """The GPU's parameters, the field its slot holds (pixels) and its own
+    energy of that field, against the oracle's parameters, field and energy."""
     e_o = orc.rigid_energy(R, T, th_orc, lam)
-    du = np.abs(orc.rigid_field(th_gpu, side + 1) - orc.rigid_field(th_orc, side + 1)).max() * side
+    du = np.abs(field_gpu - orc.rigid_field(th_orc, side + 1) * side).max()
     rec = dict(what=what, d_alpha=float(abs(th_gpu[0] - th_orc[0])),
                d_t_px=float(np.abs(th_gpu[1:] - th_orc[1:]).max() * side), field_max_px=float(du),
-               E_rel=float((e_g - e_o) / abs(e_o)))
+               E_rel=float((e_gpu - e_o) / abs(e_o)))
     P.report("rigid", rec)
     assert rec["field_max_px"] <= RIGID_TOL_PX and abs(rec["E_rel"]) <= P.TOL_E, rec
 
@@ -73,12 +74,17 @@ def test_rigid_operator_matches_oracle(reg, orc, lam):
         st, it = s.apply_operator_batch([(0, -1, -1, 0, 0, 1)])
         th, se = s.get_rigid(0)
         field, _ = s.get_slot(0)
+        e_gpu = s.eval_energy(0, 1, int(np.log2(side)), field)["E"]
     assert se == (0, 1)
     R, T = orc.embed(fr[0]), orc.embed(fr[1])
     th_o, status, stl = orc.rigid_register(R, T, orc.params(n_levels=nl, iter_max=200, lam=lam))
-    _check(orc, R, T, th, th_o, lam, side, f"A rotated pair lambda {lam}")
-    # the slot's field is the rigid map's displacement (pixels)
-    assert np.abs(field - orc.rigid_field(th, side + 1) * side).max() < 1e-3
+    _check(orc, R, T, th, field, e_gpu, th_o, lam, side, f"A rotated pair lambda {lam}")
+    # the slot's field is the rigid map's displacement (pixels): exact for a linear field
+    x = np.arange(side + 1, dtype=np.float64)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    ca, sa = np.cos(th[0]), np.sin(th[0])
+    want = np.stack([(ca - 1) * X - sa * Y + th[1] * side, sa * X + (ca - 1) * Y + th[2] * side])
+    assert np.abs(field - want).max() < 1e-3
     if lam == 0.0:
         assert abs(th[0] - alpha) < 2e-4 and np.abs(th[1:] * side - t).max() < 0.02
 
@@ -92,13 +98,15 @@ def test_rigid_series_matches_oracle(reg, orc, syn, kind):
     fr = syn.series(7, nf, side, noise=False, drift_sd=1.0, dist_amp=0.0, spacing=10.0, sigma=2.5)
     lam = 1.0
     p = reg.default_params(n_levels=nl, iter_max=100, lam=lam, flags=reg.FLAG_RIGID)
+    op = orc.params(n_levels=nl, iter_max=100, lam=lam)
+    want = orc.rigid_register_series(fr, op, kind=kind)
     with reg.Series(fr, p) as s:
         rep = s.prefix_scan(kind)
         th = s.rigid_params()
+        for k in range(1, nf):
+            field, _ = s.get_slot(k - 1)
+            e_gpu = s.eval_energy(0, k, int(np.log2(side)), field)["E"]
+            _check(orc, orc.embed(fr[0]), orc.embed(fr[k]), th[k], field, e_gpu, want[k], lam, side,
+                   f"series kind {kind} phi_0{k}")
         d = s.get_deformations()
-    op = orc.params(n_levels=nl, iter_max=100, lam=lam)
-    want = orc.rigid_register_series(fr, op, kind=kind)
-    for k in range(1, nf):
-        _check(orc, orc.embed(fr[0]), orc.embed(fr[k]), th[k], want[k], lam, side, f"series kind {kind} phi_0{k}")
-        assert np.abs(d[k] - orc.rigid_field(th[k], side + 1)[:, :side, :side] * side).max() < 1e-3
     assert rep["preprocessing_ops"] == nf - 1 and rep["ops"] > nf - 1

@@ -57,7 +57,8 @@ def test_smoothed_operators_match_oracle(reg, orc, syn, smooth, sizes):
                 P.report("smooth", P.lockstep_parity(orc, s, (0, -1, -1, e, e, e + 1), e, nl, rows, u * side, what,
                                                      g[e], g[e + 1], lam))
                 P.report("smooth", P.free_running_parity(orc, got[e], u * side, tr[tr[:, 0] == e][:, 1:], rows, what,
-                                                         g[e], g[e + 1], op, lam))
+                                                         g[e], g[e + 1], op, lam,
+                                                         P.gpu_energy_fn(s, e, e + 1, int(np.log2(side)))))
 
 
 def test_smoothed_series_stable_input_matches_oracle(reg, orc, syn):
