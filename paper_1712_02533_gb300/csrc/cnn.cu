@@ -9,9 +9,13 @@
 // (4i, 4j).  Loss: mean squared difference to a target displacement.
 // Parameters: one flat float vector, layer by layer W (O x C x 3 x 3) then b.
 //
-// Layout: activations NCHW in float, one buffer per layer.  Training kernels
-// run on the CUDA cores in FP32; the inference path can run the four
-// 32 -> 32 layers on the tensor cores (BF16 operands, FP32 accumulation).
+// Layout: the FP32 path keeps activations NCHW in float, one buffer per layer,
+// on the CUDA cores.  The tensor-core path runs the four 32 -> 32 layers with
+// BF16 operands and FP32 accumulation (forward and stride-1 data gradients by
+// tcgen05 with TMEM accumulators, weight gradients by mma.sync); the outputs
+// of layers 0..3 are then BF16 in a channel-group planar layout
+// [b][c / 8][y][x][c % 8], the operand layout of those kernels, and layer 4
+// writes FP32 NCHW for the last layer.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,12 +45,20 @@ int64_t param_offset(int k)
 }
 int64_t total_params() { return param_offset(NL); }
 
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
 // ---------------------------------------------------------------------------
 // Forward: one thread per output pixel (b, y, x) computes all O channels.
 // ---------------------------------------------------------------------------
-template <int C, int O, int S, bool RELU>
+// OUT_PLANAR: out is BF16 in the planar layout of the tensor-core layers,
+// [b][o / 8][y][x][o % 8] (O = 32), instead of FP32 NCHW.
+template <int C, int O, int S, bool RELU, bool OUT_PLANAR = false>
 __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, int H, const float *__restrict__ theta,
-                                                  float *__restrict__ out, int Ho, int total)
+                                                  void *__restrict__ out, int Ho, int total)
 {
     __shared__ float w[O * C * 9];
     __shared__ float bias[O];
@@ -77,10 +89,21 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, 
         }
     }
 #pragma unroll
-    for (int o = 0; o < O; o++) {
-        float r = acc[o];
-        if (RELU) r = fmaxf(r, 0.f);
-        out[(((int64_t)b * O + o) * Ho + y) * Ho + x] = r;
+    for (int o = 0; o < O; o++)
+        if (RELU) acc[o] = fmaxf(acc[o], 0.f);
+    if (OUT_PLANAR) {
+        static_assert(!OUT_PLANAR || O == 32, "planar output has 32 channels");
+        uint4 *o16 = reinterpret_cast<uint4 *>(out);
+#pragma unroll
+        for (int g = 0; g < O / 8; g++) {
+            const float *q = acc + 8 * g;
+            o16[((int64_t)(4 * b + g) * Ho + y) * Ho + x] =
+                make_uint4(bf16x2(q[0], q[1]), bf16x2(q[2], q[3]), bf16x2(q[4], q[5]), bf16x2(q[6], q[7]));
+        }
+    } else {
+        float *o32 = reinterpret_cast<float *>(out);
+#pragma unroll
+        for (int o = 0; o < O; o++) o32[(((int64_t)b * O + o) * Ho + y) * Ho + x] = acc[o];
     }
 }
 
@@ -89,10 +112,12 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, 
 // and S ox + dx - 1 = ix of W[o, c, dy, dx] gz[b, o, oy, ox], times the ReLU
 // mask of the layer below (its output a > 0).  One thread per input pixel.
 // ---------------------------------------------------------------------------
-template <int C, int O, int S>
+// MASK_PLANAR: a_below is BF16 in the planar layout of the tensor-core layers
+// (C = 32) instead of FP32 NCHW.
+template <int C, int O, int S, bool MASK_PLANAR = false>
 __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__ gz, int Ho,
                                                        const float *__restrict__ theta,
-                                                       const float *__restrict__ a_below, float *__restrict__ gx,
+                                                       const void *__restrict__ a_below, float *__restrict__ gx,
                                                        int H, int total)
 {
     __shared__ float w[O * C * 9];
@@ -125,7 +150,15 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
 #pragma unroll
     for (int c = 0; c < C; c++) {
         const int64_t i = (((int64_t)b * C + c) * H + iy) * H + ix;
-        gx[i] = a_below[i] > 0.f ? acc[c] : 0.f;
+        bool pos;
+        if (MASK_PLANAR) {
+            const uint16_t v = reinterpret_cast<const uint16_t *>(
+                a_below)[(((int64_t)(4 * b + c / 8) * H + iy) * H + ix) * 8 + (c & 7)];
+            pos = v != 0 && !(v & 0x8000u);
+        } else {
+            pos = reinterpret_cast<const float *>(a_below)[i] > 0.f;
+        }
+        gx[i] = pos ? acc[c] : 0.f;
     }
 }
 
@@ -245,11 +278,11 @@ __global__ void k_adam(float *__restrict__ theta, const float *__restrict__ g, f
     }
 }
 
-template <int C, int O, int S, bool RELU>
-void fwd(const float *in, int H, const float *theta, float *out, int B, cudaStream_t st)
+template <int C, int O, int S, bool RELU, bool OUT_PLANAR = false>
+void fwd(const float *in, int H, const float *theta, void *out, int B, cudaStream_t st)
 {
     const int Ho = (H + 2 - 3) / S + 1, total = B * Ho * Ho;
-    k_conv_fwd<C, O, S, RELU><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
+    k_conv_fwd<C, O, S, RELU, OUT_PLANAR><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
 }
 
 template <int C, int O, int S>
@@ -278,7 +311,10 @@ struct reg_cnn {
     float *g0 = nullptr, *g1 = nullptr;  // gradient ping-pong (largest activation)
     float *gy = nullptr;
     double *partial = nullptr, *loss = nullptr;
-    uint32_t *wpack = nullptr;  // the 32 -> 32 layers' weights in the tensor-core layout
+    uint16_t *actb[4] = {nullptr};  // tensor-core path: outputs of layers 0..3, BF16 planar [b][c/8][y][x][c%8]
+    uint32_t *wpack_u = nullptr;  // the 32 -> 32 layers' weights in the tcgen05 operand layout
+    int *uerr = nullptr;          // error word of the tcgen05 kernels (a wait ran out): device view
+    int *uerr_host = nullptr;     // the same word, pinned host memory mapped into the device
     float *wpart = nullptr;     // per-block partial weight gradients of the tensor-core training
     int64_t step = 0;
 };
@@ -307,6 +343,17 @@ int64_t act_elems(int k, int side) { return (int64_t)LAYERS[k].O * out_side(k, s
 }  // namespace
 
 int64_t cnn_output_side(const reg_cnn *h) { return out_side(NL - 1, h->side); }
+
+reg_status cnn_check_device_error(reg_cnn *h)
+{
+    volatile int *w = h->uerr_host;
+    const int e = *w;
+    if (e == 0) return REG_OK;
+    *w = 0;
+    return cnn_fail(REG_ECUDA, e == 1   ? "tcgen05 convolution: a copy did not complete in time"
+                               : e == 2 ? "tcgen05 convolution: the tensor-core work did not complete in time"
+                                        : "tcgen05 convolution: shared memory not 128-byte aligned");
+}
 int cnn_input_side(const reg_cnn *h) { return h->side; }
 int cnn_max_batch(const reg_cnn *h) { return h->max_batch; }
 
@@ -321,9 +368,15 @@ reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t
         const int H = in_side(k, S);
         const float *th = h->theta + param_offset(k);
         float *out = (k == NL - 1 && y) ? y : h->act[k];
-        if (tc && k >= 1 && k <= 4) {
-            // 32 -> 32 layers on the tensor cores
-            reg_status rs = cnn_conv32_tc(a, H, th, out, B, LAYERS[k].S, st, h->wpack + (k - 1) * cnn_conv32_tc_words());
+        if (tc && k <= 4) {
+            // tensor-core path: layer 0 writes BF16 planar activations, the
+            // 32 -> 32 layers run on tcgen05 from them (layer 4 back to FP32
+            // NCHW for the last layer)
+            reg_status rs = REG_OK;
+            if (k == 0) fwd<2, 32, 2, true, true>(a, H, th, h->actb[0], B, st);
+            else
+                rs = cnn_conv32_umma(h->actb[k - 1], H, th, k == 4 ? (void *)out : (void *)h->actb[k], k == 4, B,
+                                     LAYERS[k].S, st, h->wpack_u + (k - 1) * cnn_conv32_umma_words(), h->uerr);
             if (rs != REG_OK) return rs;
         } else {
             switch (k) {
@@ -363,6 +416,7 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
     int64_t big = 0;
     for (int k = 0; k < NL && ok; k++) {
         ok = alloc((void **)&h->act[k], sizeof(float) * act_elems(k, side) * max_batch);
+        if (ok && k < 4) ok = alloc((void **)&h->actb[k], sizeof(uint16_t) * act_elems(k, side) * max_batch);
         big = std::max(big, act_elems(k, side));
     }
     big = std::max(big, (int64_t)2 * side * side);
@@ -370,7 +424,9 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
          alloc((void **)&h->g1, sizeof(float) * big * max_batch) &&
          alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
          alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double)) &&
-         alloc((void **)&h->wpack, sizeof(uint32_t) * 4 * cnn_conv32_tc_words()) &&
+         alloc((void **)&h->wpack_u, sizeof(uint32_t) * 4 * cnn_conv32_umma_words()) &&
+         cudaHostAlloc((void **)&h->uerr_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer((void **)&h->uerr, h->uerr_host, 0) == cudaSuccess &&
          alloc((void **)&h->wpart, sizeof(float) * (size_t)(cnn_wgrad32_tc_blocks() + 1) * 32 * 288);
     if (!ok) {
         reg_cnn_destroy(h);
@@ -383,6 +439,7 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
         reg_cnn_destroy(h);
         return cnn_fail(REG_ECUDA, "init");
     }
+    *reinterpret_cast<volatile int *>(h->uerr_host) = 0;
     *out = h;
     return REG_OK;
 }
@@ -414,7 +471,7 @@ reg_status reg_cnn_forward(reg_cnn_t h, const float *x, int32_t batch, float *y,
     reg_status st = cnn_forward(h, x, batch, y, h->stream, tensor_cores != 0);
     if (st != REG_OK) return st;
     CKC(cudaStreamSynchronize(h->stream));
-    return REG_OK;
+    return cnn_check_device_error(h);
 }
 
 static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
@@ -458,14 +515,17 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
         float *gx = k == 0 ? nullptr : bufs[k & 1];
         const float *below = k == 0 ? nullptr : h->act[k - 1];
         if (tc && k >= 1 && k <= 4) {
-            rs = cnn_wgrad32_tc(in, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
+            // the layer's input and the mask below: BF16 planar
+            const uint16_t *inb = h->actb[k - 1];
+            rs = cnn_wgrad32_tc(inb, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
             if (rs != REG_OK) return rs;
             if (LAYERS[k].S == 1) {
-                rs = cnn_dgrad32_tc(gz, H, th, below, gx, B, st, h->wpack + (k - 1) * cnn_conv32_tc_words());
+                rs = cnn_dgrad32_umma(gz, H, th, inb, gx, B, st, h->wpack_u + (k - 1) * cnn_conv32_umma_words(),
+                                      h->uerr);
                 if (rs != REG_OK) return rs;
             } else {
                 const int Ho = (H + 2 - 3) / LAYERS[k].S + 1, total = B * H * H;
-                k_conv_bwd_data<32, 32, 2><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, th, below, gx, H, total);
+                k_conv_bwd_data<32, 32, 2, true><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, th, inb, gx, H, total);
             }
             gz = gx;
             continue;
@@ -484,7 +544,7 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
     if (loss) CKC(cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grad_out) CKC(cudaMemcpyAsync(grad_out, h->grad, sizeof(float) * h->n, cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
-    return REG_OK;
+    return cnn_check_device_error(h);
 }
 
 reg_status reg_cnn_adam_step(reg_cnn_t h, double lr, double beta1, double beta2, double eps)
@@ -508,10 +568,12 @@ reg_status reg_cnn_destroy(reg_cnn_t h)
     cudaFree(h->m);
     cudaFree(h->v);
     for (int k = 0; k < NL; k++) cudaFree(h->act[k]);
+    for (int k = 0; k < 4; k++) cudaFree(h->actb[k]);
     cudaFree(h->g0);
     cudaFree(h->g1);
     cudaFree(h->gy);
-    cudaFree(h->wpack);
+    cudaFree(h->wpack_u);
+    if (h->uerr_host) cudaFreeHost(h->uerr_host);
     cudaFree(h->wpart);
     cudaFree(h->partial);
     cudaFree(h->loss);

@@ -13,23 +13,35 @@ reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t
 int64_t cnn_output_side(const reg_cnn *h);
 int cnn_input_side(const reg_cnn *h);
 int cnn_max_batch(const reg_cnn *h);
-// 32 -> 32 channel 3x3 convolution with ReLU on the tensor cores (BF16 operands,
-// FP32 accumulation): in (B x 32 x H x H), out (B x 32 x Ho x Ho), stride S;
-// theta: the layer's W then b; wpack: device scratch of cnn_conv32_tc_words()
-// words for the packed weights.
-reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
-                         uint32_t *wpack);
-int cnn_conv32_tc_words();
-// Data gradient of a stride-1 32 -> 32 layer on the tensor cores: gx (B x 32 x
-// H x H) = mask(> 0) * conv(gz, W flipped and transposed), gz the gradient with
-// respect to the layer's pre-activation output.
-reg_status cnn_dgrad32_tc(const float *gz, int H, const float *theta, const float *mask, float *gx, int B,
-                          cudaStream_t st, uint32_t *wpack);
+// The tensor-core layers exchange activations as BF16 in a channel-group
+// planar layout, [b][c / 8][y][x][c % 8] (16 bytes per pixel and group of 8
+// channels): "planar" below.
+//
 // Weight and bias gradient of a 32 -> 32 layer of stride S on the tensor cores
-// into grad (the layer's W then b); part: device scratch of
+// into grad (the layer's W then b): in the layer's input (planar, B x 32 x H
+// x H), gz the output gradient (FP32 NCHW); part: device scratch of
 // (cnn_wgrad32_tc_blocks() + 1) x 32 x 288 floats.
-reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
+reg_status cnn_wgrad32_tc(const uint16_t *in, int H, const float *gz, int B, int S, float *grad, float *part,
                           cudaStream_t st);
 int cnn_wgrad32_tc_blocks();
+// 32 -> 32 channel 3x3 convolution (zero padding 1, stride S = 1 or 2) with
+// bias and ReLU on the fifth-generation tensor cores (tcgen05.mma, accumulator
+// in TMEM, BF16 operands, FP32 accumulation): in (planar, B x 32 x H x H, read
+// by TMA; H even for S = 2), out (B x 32 x Ho x Ho) planar, or FP32 NCHW with
+// out_f32; theta: the layer's W then b; wpack: device scratch of
+// cnn_conv32_umma_words() words, 16-byte aligned; err: a device word set to
+// nonzero when a wait of the kernel ran out (the result is then invalid).
+reg_status cnn_conv32_umma(const uint16_t *in, int H, const float *theta, void *out, bool out_f32, int B, int S,
+                           cudaStream_t st, uint32_t *wpack, int *err);
+// Data gradient of a stride-1 32 -> 32 layer on the tensor cores: gx (FP32
+// NCHW, B x 32 x H x H) = (mask > 0) * conv(gz, W flipped and transposed), gz
+// (FP32 NCHW) the gradient with respect to the layer's pre-activation output,
+// mask the activation below (planar).
+reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
+                            cudaStream_t st, uint32_t *wpack, int *err);
+int cnn_conv32_umma_words();
+// After the handle's stream has been synchronised: REG_ECUDA if a tcgen05
+// kernel reported a wait that ran out since the last check (and clear it).
+reg_status cnn_check_device_error(reg_cnn *h);
 // Record an error message for reg_last_error().
 reg_status reg_internal_fail(reg_status st, const char *msg);

@@ -1,21 +1,7 @@
-// Tensor-core forward of the learned initialiser's 32 -> 32 channel layers:
-// a 3x3 convolution (zero padding 1, stride 1 or 2) with bias and ReLU as an
-// implicit GEMM, D[pixel][o] = sum_k A[pixel][k] W[o][k], with the reduction
-// index ordered k = (3 dy + dx) * 32 + c (K = 288 = 18 steps of 16).
-// Operands are BF16, accumulation FP32 (mma.sync m16n8k16).
-//
-// A block computes an output tile of 8 rows x 16 columns of one image for all
-// 32 output channels; each of its 4 warps takes two rows (two m-tiles of 16
-// pixels) and all four n-tiles of 8 channels.  The block first stages, in
-// shared memory as BF16 pairs of channels (channels innermost):
-//   - the input tile with its halo, (S*7 + 3) x (S*15 + 3) pixels, read from
-//     the FP32 NCHW activations (zero outside the image);
-//   - the layer's weights, W[3 dy + dx][o][c].
-// Every fragment register is then one 32-bit shared load.  Pixel and weight
-// rows are padded (20 or 18 words) so that the eight rows a fragment load
-// touches fall into distinct banks.  The weights are packed into that layout
-// once per layer and call (k_pack_w32), and each block copies them with
-// 16-byte loads.
+// Weight gradients of the learned initialiser's 32 -> 32 channel layers on the
+// tensor cores (BF16 operands, FP32 accumulation, mma.sync m16n8k16), and the
+// bias gradients of those layers.  (Their forward and stride-1 data gradients
+// run on tcgen05 in cnn_umma.cu.)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -26,16 +12,9 @@ namespace {
 
 constexpr int TC_C = 32, TC_O = 32, TC_K = TC_C * 9;
 constexpr int TC_TH = 8, TC_TW = 16;  // output tile (rows, columns)
-constexpr int TC_WS = 20;             // words per (tap, output channel) weight row: 16 channel pairs + pad
-
+// the input tile of an output tile, with its halo
 __host__ __device__ constexpr int in_rows(int S) { return S * (TC_TH - 1) + 3; }
 __host__ __device__ constexpr int in_cols(int S) { return S * (TC_TW - 1) + 3; }
-// words per staged input pixel: 16 channel pairs + pad (bank spread for the stride)
-__host__ __device__ constexpr int pix_words(int S) { return S == 1 ? 20 : 18; }
-// the staged input tile, rounded up to 16 bytes so that the weights after it
-// can be written with 16-byte stores
-__host__ __device__ constexpr int xs_words(int S) { return (in_rows(S) * in_cols(S) * pix_words(S) + 3) / 4 * 4; }
-__host__ __device__ constexpr int smem_words(int S) { return xs_words(S) + 9 * TC_O * TC_WS + TC_O; }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -53,150 +32,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// W[o][c][dy][dx] (FP32) -> [3 dy + dx][o][c pair] (BF16 pairs, rows of TC_WS
-// words, the padding zero).
-__global__ void k_pack_w32(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * TC_O * TC_WS) return;
-    const int cp = i % TC_WS, r2 = i / TC_WS, o = r2 % TC_O, tap = r2 / TC_O;
-    uint32_t v = 0;
-    if (cp < TC_C / 2) {
-        const float *w = theta + (int64_t)o * TC_K + (2 * cp) * 9 + tap;
-        v = pack_bf16(w[0], w[9]);
-    }
-    wpack[i] = v;
-}
-
-// DGRAD: the data gradient of a stride-1 layer as the same implicit GEMM --
-// input the output gradient, weights flipped and transposed (k_pack_w32_dgrad),
-// no bias, and the result multiplied by the ReLU mask of the layer below
-// (mask > 0).
-template <int S, bool DGRAD>
-__global__ void __launch_bounds__(128) k_conv32_tc(const float *__restrict__ in, int H,
-                                                   const float *__restrict__ theta, const uint32_t *__restrict__ wpack,
-                                                   const float *__restrict__ mask, float *__restrict__ out, int Ho,
-                                                   int tiles_x, int tiles_y)
-{
-    constexpr int IR = in_rows(S), IC = in_cols(S), PW = pix_words(S);
-    extern __shared__ uint32_t smem[];
-    uint32_t *xs = smem;               // [IR][IC][PW]
-    uint32_t *ws = xs + xs_words(S);   // [9][32][TC_WS], 16-byte aligned
-    float *bias = reinterpret_cast<float *>(ws + 9 * TC_O * TC_WS);
-    const int tid = threadIdx.x;
-    const int tx = blockIdx.x % tiles_x, rest = blockIdx.x / tiles_x;
-    const int ty = rest % tiles_y, b = rest / tiles_y;
-    const int oy0 = ty * TC_TH, ox0 = tx * TC_TW;
-    const int iy0 = S * oy0 - 1, ix0 = S * ox0 - 1;
-    // the packed weights and the biases
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
-        uint4 *dst = reinterpret_cast<uint4 *>(ws);
-        for (int i = tid; i < 9 * TC_O * TC_WS / 4; i += blockDim.x) dst[i] = src[i];
-    }
-    if (tid < TC_O) bias[tid] = DGRAD ? 0.f : theta[TC_O * TC_K + tid];
-    // stage the input tile: one channel pair of one pixel per item (columns fastest)
-    const float *img = in + (int64_t)b * TC_C * H * H;
-#pragma unroll 4
-    for (int i = tid; i < (TC_C / 2) * IR * IC; i += blockDim.x) {
-        const int ix = i % IC, r2 = i / IC, iy = r2 % IR, cp = r2 / IR;
-        const int gy = iy0 + iy, gx = ix0 + ix;
-        float v0 = 0.f, v1 = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < H) {
-            const int64_t o = ((int64_t)(2 * cp) * H + gy) * H + gx;
-            v0 = img[o];
-            v1 = img[o + (int64_t)H * H];
-        }
-        xs[(iy * IC + ix) * PW + cp] = pack_bf16(v0, v1);
-    }
-    __syncthreads();
-
-    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int m = 0; m < 2; m++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int i = 0; i < 4; i++) acc[m][j][i] = 0.f;
-#pragma unroll 2
-    for (int ks = 0; ks < 18; ks++) {
-        const int tap = ks >> 1, ch = (ks & 1) * 8;  // channel-pair offset of this k-step
-        const int dy = tap / 3, dx = tap - 3 * dy;
-        uint32_t bf[4][2];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint32_t *wr = ws + (tap * TC_O + 8 * j + g) * TC_WS + ch + t;
-            bf[j][0] = wr[0];
-            bf[j][1] = wr[4];
-        }
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-            const int oy = 2 * warp + m;  // output row within the tile
-            const uint32_t *p0 = xs + ((S * oy + dy) * IC + S * g + dx) * PW + ch + t;  // pixel g
-            const uint32_t *p1 = p0 + S * 8 * PW;                                      // pixel g + 8
-            uint32_t a[4];
-            a[0] = p0[0];
-            a[1] = p1[0];
-            a[2] = p0[4];
-            a[3] = p1[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) mma_bf16(acc[m][j], a, bf[j][0], bf[j][1]);
-        }
-    }
-    // D fragment: (row g, cols 2t, 2t+1) and (row g+8, same cols) of each n-tile
-#pragma unroll
-    for (int m = 0; m < 2; m++) {
-        const int oy = oy0 + 2 * warp + m;
-        if (oy >= Ho) continue;
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int ox = ox0 + g + 8 * (i >> 1), o = 8 * j + 2 * t + (i & 1);
-                if (ox < Ho) {
-                    const int64_t idx = (((int64_t)b * TC_O + o) * Ho + oy) * Ho + ox;
-                    if (DGRAD) out[idx] = mask[idx] > 0.f ? acc[m][j][i] : 0.f;
-                    else out[idx] = fmaxf(acc[m][j][i] + bias[o], 0.f);
-                }
-            }
-    }
-}
-
-// Data gradient of a stride-1 layer as a forward convolution of the output
-// gradient: K'[c][o][ey][ex] = W[o][c][2 - ey][2 - ex], packed like
-// k_pack_w32 (tap 3 ey + ex, output channel c, input channel pairs o).
-__global__ void k_pack_w32_dgrad(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * TC_O * TC_WS) return;
-    const int op = i % TC_WS, r2 = i / TC_WS, c = r2 % TC_O, tap = r2 / TC_O;
-    uint32_t v = 0;
-    if (op < TC_C / 2) {
-        const float *w = theta + (int64_t)(2 * op) * TC_K + c * 9 + (8 - tap);
-        v = pack_bf16(w[0], w[TC_K]);
-    }
-    wpack[i] = v;
-}
-
-template <int S, bool DGRAD>
-reg_status launch(const float *in, int H, const float *theta, const float *mask, float *out, int B, cudaStream_t st,
-                  uint32_t *wpack)
-{
-    const int nw = 9 * TC_O * TC_WS;
-    if (DGRAD) k_pack_w32_dgrad<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
-    else k_pack_w32<<<(nw + 255) / 256, 256, 0, st>>>(theta, wpack);
-    const size_t bytes = sizeof(uint32_t) * smem_words(S);
-    if (cudaFuncSetAttribute(k_conv32_tc<S, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
-        return reg_internal_fail(REG_ECUDA, "tensor-core convolution: shared memory attribute");
-    const int Ho = (H + 2 - 3) / S + 1;
-    const int tx = (Ho + TC_TW - 1) / TC_TW, ty = (Ho + TC_TH - 1) / TC_TH;
-    k_conv32_tc<S, DGRAD><<<B * tx * ty, 128, bytes, st>>>(in, H, theta, wpack, mask, out, Ho, tx, ty);
-    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tensor-core convolution launch");
-    return REG_OK;
-}
-
 // ---------------------------------------------------------------------------
 // Weight gradient of a 32 -> 32 layer on the tensor cores:
 //   gW[o][n] = sum_p gz[o][p] A[p][n],  n = (3 dy + dx) * 32 + c,
@@ -205,7 +40,8 @@ reg_status launch(const float *in, int H, const float *theta, const float *mask,
 // N = 288 and the reduction over all output pixels of the batch, BF16
 // operands and FP32 accumulation (mma.sync m16n8k16).  A block walks output
 // tiles of 8 x 16 pixels (grid-stride), stages per tile the output gradient as
-// BF16 pairs of pixels and the input tile with its halo as BF16, and keeps the
+// BF16 pairs of pixels and the input tile with its halo (from the BF16 planar
+// activations [b][c / 8][y][x][c % 8]) as [c][y][x], and keeps the
 // 32 x 288 partial in registers: each warp holds both m-tiles of 16 channels
 // and 9 of the 36 n-tiles.  The partials of the blocks are summed in a fixed
 // order by k_wgrad_reduce (deterministic).
@@ -213,7 +49,7 @@ reg_status launch(const float *in, int H, const float *theta, const float *mask,
 constexpr int WG_PW = 68;  // words per output channel row of the staged gradient: 64 pixel pairs + pad
 
 template <int S>
-__global__ void __launch_bounds__(128) k_wgrad32_tc(const float *__restrict__ in, int H, const float *__restrict__ gz,
+__global__ void __launch_bounds__(128) k_wgrad32_tc(const uint4 *__restrict__ in, int H, const float *__restrict__ gz,
                                                     int Ho, int tiles_x, int tiles_y, int n_tiles,
                                                     float *__restrict__ part)
 {
@@ -246,14 +82,20 @@ __global__ void __launch_bounds__(128) k_wgrad32_tc(const float *__restrict__ in
             }
             gs[o * WG_PW + q] = pack_bf16(v0, v1);
         }
-        // input tile with its halo, BF16, [c][iy][ix]
-        const float *img = in + (int64_t)b * TC_C * H * H;
-        for (int i = tid; i < TC_C * IR * IC; i += blockDim.x) {
-            const int ix = i % IC, r2 = i / IC, iy = r2 % IR, c = r2 / IR;
+        // input tile with its halo, BF16, [c][iy][ix], from the planar input
+        // (one 16-byte group of 8 channels per item)
+        for (int i = tid; i < (TC_C / 8) * IR * IC; i += blockDim.x) {
+            const int ix = i % IC, r2 = i / IC, iy = r2 % IR, cg = r2 / IR;
             const int gy = iy0 + iy, gx = ix0 + ix;
-            float v = 0.f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < H) v = img[((int64_t)c * H + gy) * H + gx];
-            xs[i] = __float2bfloat16_rn(v);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < H) v = in[((int64_t)(4 * b + cg) * H + gy) * H + gx];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            __nv_bfloat16 *dst = xs + ((8 * cg) * IR + iy) * IC + ix;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                dst[(2 * j) * IR * IC] = __ushort_as_bfloat16((unsigned short)(w[j] & 0xFFFFu));
+                dst[(2 * j + 1) * IR * IC] = __ushort_as_bfloat16((unsigned short)(w[j] >> 16));
+            }
         }
         __syncthreads();
 #pragma unroll 1
@@ -342,7 +184,7 @@ __global__ void k_bias_grad_sum(const float *__restrict__ bpart, float *__restri
 }
 
 template <int S>
-reg_status launch_wgrad(const float *in, int H, const float *gz, int B, float *grad, float *part, int max_blocks,
+reg_status launch_wgrad(const uint4 *in, int H, const float *gz, int B, float *grad, float *part, int max_blocks,
                         cudaStream_t st)
 {
     const int Ho = (H + 2 - 3) / S + 1;
@@ -371,26 +213,11 @@ int cnn_wgrad32_tc_blocks()
     return 3 * nsm;
 }
 
-reg_status cnn_wgrad32_tc(const float *in, int H, const float *gz, int B, int S, float *grad, float *part,
+reg_status cnn_wgrad32_tc(const uint16_t *in, int H, const float *gz, int B, int S, float *grad, float *part,
                           cudaStream_t st)
 {
-    if (S == 1) return launch_wgrad<1>(in, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
-    if (S == 2) return launch_wgrad<2>(in, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
+    const uint4 *inq = reinterpret_cast<const uint4 *>(in);
+    if (S == 1) return launch_wgrad<1>(inq, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
+    if (S == 2) return launch_wgrad<2>(inq, H, gz, B, grad, part, cnn_wgrad32_tc_blocks(), st);
     return reg_internal_fail(REG_EINVAL, "tensor-core weight gradient: stride must be 1 or 2");
-}
-
-reg_status cnn_dgrad32_tc(const float *gz, int H, const float *theta, const float *mask, float *gx, int B,
-                          cudaStream_t st, uint32_t *wpack)
-{
-    return launch<1, true>(gz, H, theta, mask, gx, B, st, wpack);
-}
-
-int cnn_conv32_tc_words() { return 9 * TC_O * TC_WS; }
-
-reg_status cnn_conv32_tc(const float *in, int H, const float *theta, float *out, int B, int S, cudaStream_t st,
-                         uint32_t *wpack)
-{
-    if (S == 1) return launch<1, false>(in, H, theta, nullptr, out, B, st, wpack);
-    if (S == 2) return launch<2, false>(in, H, theta, nullptr, out, B, st, wpack);
-    return reg_internal_fail(REG_EINVAL, "tensor-core convolution: stride must be 1 or 2");
 }

@@ -1,0 +1,636 @@
+// The learned initialiser's 32 -> 32 channel 3x3 convolutions (zero padding 1,
+// stride 1 or 2) on the fifth-generation tensor cores: tcgen05.mma with the
+// accumulator in tensor memory (TMEM), BF16 operands, FP32 accumulation.
+//
+// Implicit GEMM per output tile of 16 rows x 8 columns of one image:
+//   D[m][o] = sum_k A[m][k] W[o][k],   m = 8 (tile row) + (tile column),
+//   k = (3 dy + dx) * 32 + c,          M = 128, N = 32, K = 288 = 18 steps of 16,
+// A[m][k] = in_pad[c][S y + dy][S x + dx] for output pixel (y, x) of tile row m.
+//
+// Activations between the 32-channel layers are BF16 in a channel-group
+// planar layout, [b][cg][y][x][8 channels] (cg = c / 8): 16 bytes per pixel
+// and channel group.  It is the K-major operand layout of the tensor cores, so
+// a tile's input needs no conversion.
+//
+// Shared-memory operands in the K-major layout without swizzling: "core
+// matrices" of 8 rows x 16 bytes (8 BF16 values along k), each stored as 128
+// contiguous bytes, rows 16 bytes apart.  A descriptor gives the start address
+// and two strides: between core matrices adjacent along M (or N) and along K.
+//   - Weights, packed once per call by k_pack_w32_umma: [tap][cg][o][8
+//     channels] BF16, 18 KB.  For a k-step (tap, half h) the operand starts at
+//     ((4 tap + 2 h) 32) 16 bytes; N-stride 128 B, K-stride 512 B.  They reach
+//     shared memory by a bulk asynchronous copy (cp.async.bulk).
+//   - The input tile with its halo, [cg][halo row][halo column][8 channels].
+//     Every 8 output pixels of a tile row read 8 consecutive halo columns for
+//     any tap, so each tap of the 3 x 3 window is the same operand with a
+//     shifted start address: tap (dy, dx) starts at halo row dy, column dx.
+//     The forward loads the tile with one TMA tensor copy
+//     (cp.async.bulk.tensor, 18 rows x 10 columns x 4 groups; zeros outside
+//     the image).  With stride 2 the output columns x read halo columns
+//     2 x + dx, so the halo is loaded as two copies, the columns of one
+//     parity each (a view of the activations with the column split into
+//     (x / 2, x % 2)), and a tap starts in the copy of its parity dx & 1 at
+//     column dx >> 1; the M-stride then covers two halo rows.
+//
+// One thread issues the tile's TMA copy and its 18 MMAs, committed to an
+// mbarrier; each warp then reads its 32 TMEM lanes (= tile rows 32 w .. 32 w
+// + 31) with tcgen05.ld and writes bias + ReLU, as BF16 in the planar layout
+// (or FP32 NCHW for the last 32-channel layer).  CTAs loop over tiles with two
+// accumulators (64 TMEM columns), so that the MMAs of a tile run while the
+// previous one is written, and (stride 1) two halo buffers, so that the next
+// tile's copy is in flight meanwhile too.  The data gradient of a stride-1
+// layer runs the same GEMM on the output gradient (FP32 NCHW, staged and
+// rounded by the CTA's threads) with flipped and transposed weights, times
+// the ReLU mask of the layer below.  Every wait on an mbarrier is bounded
+// (one second of the global timer); a wait that runs out sets the error word,
+// the CTA stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "cnn_internal.h"
+
+namespace {
+
+constexpr int UC = 32;                     // channels in and out
+constexpr int UTH = 16, UTW = 8;           // output tile: 16 rows x 8 columns = the 128 rows of the MMA
+constexpr int UW_BYTES = 9 * 4 * 32 * 16;  // packed weights
+constexpr int U_TMEM_COLS = 64;            // two FP32 accumulators of 32 columns
+constexpr uint64_t U_WAIT_NS = 1000000000ull;
+
+// The staged input tile of stride S: per copy (one, or one per column parity
+// with stride 2) [cg][rows][cols][16 bytes].
+// A TMA tensor copy writes to a 128-byte aligned shared-memory address, so
+// each copy starts on a multiple of 128 bytes.
+template <int S>
+struct Halo {
+    static constexpr int rows = S * (UTH - 1) + 3;        // 18 or 33
+    static constexpr int cols = S == 1 ? UTW + 2 : UTW + 1;  // 10, or 9 per parity
+    static constexpr int cg_bytes = rows * cols * 16;     // 2880 or 4752
+    static constexpr int copy_bytes = 4 * cg_bytes;       // what one copy writes
+    static constexpr int copy_stride = (copy_bytes + 127) / 128 * 128;
+    static constexpr int bytes = S * copy_stride;         // 11520 or 38144
+    static constexpr int sbo = S * cols * 16;             // M-stride: one output row = S halo rows
+    // start of the operand of tap (dy, dx), k-half h, relative to the buffer
+    __host__ __device__ static constexpr int tap_offset(int dy, int dx, int h)
+    {
+        return (S == 1 ? 0 : (dx & 1) * copy_stride) + 2 * h * cg_bytes + (dy * cols + (S == 1 ? dx : dx >> 1)) * 16;
+    }
+};
+
+// shared memory: [weights][halo buffers][mbarriers: weights, 2 full, 2 MMA][TMEM
+// address][bias], the halo buffers 128-byte aligned.  Stride 1 keeps two halo buffers (five CTAs per SM); the
+// stride-2 halo is four times larger, so it keeps one and more CTAs instead.
+template <int S>
+struct Smem {
+    static constexpr int nbuf = S == 1 ? 2 : 1;
+    static constexpr int w = 0;
+    static constexpr int halo = UW_BYTES;
+    static constexpr int bars = halo + nbuf * Halo<S>::bytes;  // 8-byte aligned (multiples of 16 above)
+    static constexpr int taddr = bars + 5 * 8;
+    static constexpr int bias = taddr + 8;
+    static constexpr int bytes = bias + UC * 4;
+    static_assert(halo % 128 == 0 && Halo<S>::bytes % 128 == 0 && Halo<S>::copy_stride % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after one
+// second of the global timer.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > U_WAIT_NS) return false;
+    return true;
+}
+
+// Shared-memory matrix descriptor, no swizzling: start address, K-direction
+// (leading) and M/N-direction (stride) byte offsets between core matrices, all
+// in units of 16 bytes; bits 46..48 hold the fixed value 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t U_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UC >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(U_IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// W[o][c][dy][dx] (FP32) -> [tap][cg][o][8 channels] (BF16).  DGRAD: the data
+// gradient of a stride-1 layer as a forward convolution of the output
+// gradient with K'[c][o][tap] = W[o][c][8 - tap] (output channel c, reduction
+// channel o).
+template <bool DGRAD>
+__global__ void k_pack_w32_umma(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one pair of reduction channels
+    if (i >= UW_BYTES / 4) return;
+    const int jp = i & 3, n = (i >> 2) & 31, cg = (i >> 7) & 3, tap = i >> 9;
+    const int k0 = 8 * cg + 2 * jp;  // reduction channel of the low half
+    float lo, hi;
+    if (DGRAD) {
+        lo = theta[((int64_t)k0 * UC + n) * 9 + (8 - tap)];
+        hi = theta[((int64_t)(k0 + 1) * UC + n) * 9 + (8 - tap)];
+    } else {
+        lo = theta[((int64_t)n * UC + k0) * 9 + tap];
+        hi = theta[((int64_t)n * UC + k0 + 1) * 9 + tap];
+    }
+    wpack[i] = pack2(lo, hi);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+// The 18 MMAs of one tile: halo buffer at hbase, accumulator at d.
+template <int S>
+__device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t d)
+{
+    using HL = Halo<S>;
+#pragma unroll
+    for (int ks = 0; ks < 18; ks++) {
+        const int tap = ks >> 1, h = ks & 1, dy = tap / 3, dx = tap - 3 * dy;
+        umma_bf16(d, sdesc(hbase + HL::tap_offset(dy, dx, h), HL::cg_bytes, HL::sbo),
+                  sdesc(wbase + (4 * tap + 2 * h) * 512, 512, 128), ks > 0);
+    }
+}
+
+// Common setup: TMEM columns, mbarriers, bias, and the weights' bulk copy.
+template <int S>
+__device__ __forceinline__ uint32_t umma_setup(uint8_t *smem, const float *bias_g, const uint32_t *wpack)
+{
+    using SM = Smem<S>;
+    const int tid = threadIdx.x;
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t bar_w = s_base + SM::bars;
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + SM::taddr),
+                     "r"(U_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 5; i++) mbar_init(bar_w + 8 * i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    float *bias = reinterpret_cast<float *>(smem + SM::bias);
+    if (tid < UC) bias[tid] = bias_g ? bias_g[tid] : 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        mbar_expect_tx(bar_w, UW_BYTES);
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    s_base + SM::w + h * (UW_BYTES / 2)),
+                "l"(reinterpret_cast<const uint8_t *>(wpack) + h * (UW_BYTES / 2)), "r"(UW_BYTES / 2), "r"(bar_w)
+                : "memory");
+    }
+    return *reinterpret_cast<volatile uint32_t *>(smem + SM::taddr);
+}
+
+__device__ __forceinline__ void umma_teardown(uint32_t tmem)
+{
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(U_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_x, int tiles_y, int &b, int &ty, int &tx)
+{
+    const int per_img = tiles_x * tiles_y;
+    b = tile / per_img;
+    const int r = tile - b * per_img;
+    ty = r / tiles_x;
+    tx = r - ty * tiles_x;
+}
+
+// Forward of one layer: input by TMA from the planar BF16 activations (tensor
+// map tin), output bias + ReLU as planar BF16 (OUT_F32 false) or FP32 NCHW.
+template <int S, bool OUT_F32>
+__global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__ CUtensorMap tin,
+                                                         const float *__restrict__ bias_g,
+                                                         const uint32_t *__restrict__ wpack, void *__restrict__ out,
+                                                         int Ho, int tiles_x, int tiles_y, int n_tiles,
+                                                         int *__restrict__ err)
+{
+    using HL = Halo<S>;
+    using SM = Smem<S>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t s_base = smem_u32(smem);
+    if (s_base & 127u) {  // the TMA destinations would not be 128-byte aligned
+        if (tid == 0) *reinterpret_cast<volatile int *>(err) = 3;
+        return;
+    }
+    const uint32_t bar_w = s_base + SM::bars, bar_full = bar_w + 8, bar_mma = bar_w + 24;
+    const float *bias = reinterpret_cast<const float *>(smem + SM::bias);
+    const uint32_t tmem = umma_setup<S>(smem, bias_g, wpack);
+
+    // TMA copy of a tile's halo into buffer hb (thread 0)
+    auto load_tile = [&](int tile, int hb) {
+        int b, ty, tx;
+        tile_coords(tile, tiles_x, tiles_y, b, ty, tx);
+        const int iy0 = S * UTH * ty - 1;
+        const uint32_t dst = s_base + SM::halo + hb * HL::bytes, bar = bar_full + 8 * hb;
+        mbar_expect_tx(bar, S * HL::copy_bytes);
+        if (S == 1) {
+            tma_load_4d(dst, &tin, 0, UTW * tx - 1, iy0, 4 * b, bar);
+        } else {
+            // columns 16 tx - 1 + 2 j (odd: parity 1, half index 8 tx - 1 + j),
+            // then 16 tx + 2 j (parity 0, half index 8 tx + j)
+            tma_load_5d(dst, &tin, 0, 1, UTW * tx - 1, iy0, 4 * b, bar);
+            tma_load_5d(dst + HL::copy_stride, &tin, 0, 0, UTW * tx, iy0, 4 * b, bar);
+        }
+    };
+    if (tid == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
+        if ((int)blockIdx.x < n_tiles) load_tile(blockIdx.x, 0);
+    }
+
+    int bad = 0, fail = 0;
+    int it = 0, prev = -1;
+    for (int tile = blockIdx.x;; tile += gridDim.x, ++it) {
+        const bool have = tile < n_tiles;
+        const int buf = it & 1;                       // accumulator and MMA barrier of this tile
+        const int hb = SM::nbuf == 2 ? buf : 0;       // halo buffer
+        const int huse = SM::nbuf == 2 ? it >> 1 : it;  // its use count
+        // the accumulator is free: its last reader, the epilogue two tiles
+        // back, finished before this barrier
+        tc_fence_before();
+        __syncthreads();
+        if (have && tid == 0 && !bad) {
+            bool ok = (it > 0 || mbar_wait(bar_w, 0)) && mbar_wait(bar_full + 8 * hb, huse & 1);
+            if (ok) {
+                tc_fence_after();
+                issue_tile_mmas<S>(s_base + SM::halo + hb * HL::bytes, s_base + SM::w, tmem + buf * UC);
+            }
+            umma_commit(bar_mma + 8 * buf);
+            const int next = tile + gridDim.x;
+            if (ok && next < n_tiles) {
+                // the next tile's buffer must no longer be read: by the MMAs of
+                // the last tile (two buffers) or of this one (one buffer)
+                if (SM::nbuf == 2) ok = it == 0 || mbar_wait(bar_mma + 8 * (buf ^ 1), ((it - 1) >> 1) & 1);
+                else ok = mbar_wait(bar_mma + 8 * buf, (it >> 1) & 1);
+                if (ok) load_tile(next, SM::nbuf == 2 ? hb ^ 1 : 0);
+            }
+            if (!ok) {
+                fail = 1;
+                *reinterpret_cast<volatile int *>(err) = 1;
+            }
+        }
+        // epilogue of the previous tile
+        if (prev >= 0) {
+            const int pb = buf ^ 1;
+            const bool ok = bad ? true : mbar_wait(bar_mma + 8 * pb, ((it - 1) >> 1) & 1);
+            if (!ok) *reinterpret_cast<volatile int *>(err) = 2;
+            bad = __syncthreads_or(!ok || bad || fail);
+            if (!bad) {
+                tc_fence_after();
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
+                int b, ty, tx;
+                tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
+                const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
+                if (oy < Ho && ox < Ho) {
+#pragma unroll
+                    for (int o = 0; o < UC; o++) v[o] = fmaxf(v[o] + bias[o], 0.f);
+                    if (OUT_F32) {
+                        float *o32 = reinterpret_cast<float *>(out);
+                        const int64_t o0 = ((int64_t)b * UC * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
+#pragma unroll
+                        for (int o = 0; o < UC; o++) o32[o0 + o * plane] = v[o];
+                    } else {
+                        uint4 *o16 = reinterpret_cast<uint4 *>(out);
+#pragma unroll
+                        for (int cg = 0; cg < 4; cg++) {
+                            const float *q = v + 8 * cg;
+                            o16[((int64_t)(4 * b + cg) * Ho + oy) * Ho + ox] =
+                                make_uint4(pack2(q[0], q[1]), pack2(q[2], q[3]), pack2(q[4], q[5]), pack2(q[6], q[7]));
+                        }
+                    }
+                }
+            }
+        } else if (have) {
+            bad = __syncthreads_or(bad || fail);
+        }
+        if (!have || bad) break;
+        prev = tile;
+    }
+    umma_teardown(tmem);
+}
+
+// Positive entries of a planar BF16 activation: 32 bits, one per channel.
+__device__ __forceinline__ uint32_t positive_mask(const uint4 *act, int b, int H, int y, int x)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int cg = 0; cg < 4; cg++) {
+        const uint4 q = act[((int64_t)(4 * b + cg) * H + y) * H + x];
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t lo = w[j] & 0xFFFFu, hi = w[j] >> 16;
+            m |= (uint32_t)(lo != 0 && !(lo & 0x8000u)) << (8 * cg + 2 * j);
+            m |= (uint32_t)(hi != 0 && !(hi & 0x8000u)) << (8 * cg + 2 * j + 1);
+        }
+    }
+    return m;
+}
+
+// Data gradient of a stride-1 layer: gz (FP32 NCHW, the gradient with respect
+// to the layer's pre-activation output) staged and rounded to BF16 by the
+// CTA's threads; gx (FP32 NCHW) = the GEMM with flipped, transposed weights,
+// where the planar BF16 activation below (mask) is positive, else 0.
+__global__ void __launch_bounds__(128) k_conv32_umma_dgrad(const float *__restrict__ gz, int H,
+                                                           const uint32_t *__restrict__ wpack,
+                                                           const uint4 *__restrict__ mask, float *__restrict__ gx,
+                                                           int tiles_x, int tiles_y, int n_tiles,
+                                                           int *__restrict__ err)
+{
+    using HL = Halo<1>;
+    using SM = Smem<1>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t bar_w = s_base + SM::bars, bar_mma = bar_w + 24;
+    const uint32_t tmem = umma_setup<1>(smem, nullptr, wpack);
+    int bad = 0;
+    int it = 0, prev = -1;
+    for (int tile = blockIdx.x;; tile += gridDim.x, ++it) {
+        const bool have = tile < n_tiles;
+        const int buf = it & 1;
+        if (have) {
+            // stage the tile with its halo into halo[buf] (the MMAs that last
+            // read it completed: waited on in the last iteration's epilogue)
+            int b, ty, tx;
+            tile_coords(tile, tiles_x, tiles_y, b, ty, tx);
+            const int iy0 = UTH * ty - 1, ix0 = UTW * tx - 1;
+            uint8_t *hbuf = smem + SM::halo + buf * HL::bytes;
+            const float *img = gz + (int64_t)b * UC * H * H;
+            const int64_t plane = (int64_t)H * H;
+            for (int i = tid; i < 4 * HL::rows * HL::cols; i += 128) {
+                const int ix = i % HL::cols, r3 = i / HL::cols, iy = r3 % HL::rows, cg = r3 / HL::rows;
+                const int gy = iy0 + iy, gxx = ix0 + ix;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gy >= 0 && gy < H && gxx >= 0 && gxx < H) {
+                    const float *p = img + (int64_t)(8 * cg) * plane + (int64_t)gy * H + gxx;
+                    v = make_uint4(pack2(p[0], p[plane]), pack2(p[2 * plane], p[3 * plane]),
+                                   pack2(p[4 * plane], p[5 * plane]), pack2(p[6 * plane], p[7 * plane]));
+                }
+                *reinterpret_cast<uint4 *>(hbuf + cg * HL::cg_bytes + (iy * HL::cols + ix) * 16) = v;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (have && tid == 0 && !bad) {
+            tc_fence_after();
+            if (it == 0 && !mbar_wait(bar_w, 0)) *reinterpret_cast<volatile int *>(err) = 1;
+            else issue_tile_mmas<1>(s_base + SM::halo + buf * HL::bytes, s_base + SM::w, tmem + buf * UC);
+            umma_commit(bar_mma + 8 * buf);
+        }
+        if (prev >= 0) {
+            const int pb = buf ^ 1;
+            const bool ok = bad ? true : mbar_wait(bar_mma + 8 * pb, ((it - 1) >> 1) & 1);
+            if (!ok) *reinterpret_cast<volatile int *>(err) = 2;
+            bad = __syncthreads_or(!ok || bad);
+            if (!bad) {
+                tc_fence_after();
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
+                int b, ty, tx;
+                tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
+                const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
+                if (oy < H && ox < H) {
+                    const uint32_t pm = positive_mask(mask, b, H, oy, ox);
+                    const int64_t o0 = ((int64_t)b * UC * H + oy) * H + ox, plane = (int64_t)H * H;
+#pragma unroll
+                    for (int o = 0; o < UC; o++) gx[o0 + o * plane] = ((pm >> o) & 1u) ? v[o] : 0.f;
+                }
+            }
+        }
+        if (!have || bad) break;
+        prev = tile;
+    }
+    umma_teardown(tmem);
+}
+
+// cuTensorMapEncodeTiled from the driver, found once.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of B planar BF16 images of side H: [b][cg][y][x][8], as
+// (8 channels, x, y, 4 b + cg) with boxes of one halo tile (stride 1), or as
+// (8 channels, x % 2, x / 2, y, 4 b + cg) with boxes of one column parity
+// (stride 2; H even).
+bool encode_input_map(CUtensorMap *map, const void *act, int H, int B, int S)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t row = 16ull * H, img = 16ull * H * H;
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    CUresult r;
+    if (S == 1) {
+        const cuuint64_t dims[4] = {8, (cuuint64_t)H, (cuuint64_t)H, 4ull * B};
+        const cuuint64_t strides[3] = {16, row, img};
+        const cuuint32_t box[4] = {8, Halo<1>::cols, Halo<1>::rows, 4};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(act), dims, strides, box, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        if (H % 2) return false;
+        const cuuint64_t dims[5] = {8, 2, (cuuint64_t)H / 2, (cuuint64_t)H, 4ull * B};
+        const cuuint64_t strides[4] = {16, 32, row, img};
+        const cuuint32_t box[5] = {8, 1, Halo<2>::cols, Halo<2>::rows, 4};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(act), dims, strides, box, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS;
+}
+
+// Launch shape: one CTA per tile up to the resident CTAs of every SM (by
+// shared memory, at most 8: 8 x 64 TMEM columns fill the 512 columns of an
+// SM, so an allocation never waits on another CTA).
+template <typename K>
+bool grid_for(K kern, int bytes, int n_tiles, int &grid)
+{
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess)
+        return false;
+    int dev = 0, nsm = 0, smem_sm = 0, smem_rsv = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return false;
+    const int per_sm = std::max(1, std::min(512 / U_TMEM_COLS, smem_sm / (bytes + smem_rsv)));
+    grid = std::min(n_tiles, nsm * per_sm);
+    return true;
+}
+
+template <int S, bool OUT_F32>
+reg_status launch_fwd(const uint16_t *in, int H, const float *theta, void *out, int B, cudaStream_t st,
+                      uint32_t *wpack, int *err)
+{
+    CUtensorMap map;
+    if (!encode_input_map(&map, in, H, B, S))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 convolution: tensor map of the input");
+    k_pack_w32_umma<false><<<(UW_BYTES / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    const int Ho = (H + 2 - 3) / S + 1;
+    const int tx = (Ho + UTW - 1) / UTW, ty = (Ho + UTH - 1) / UTH, nt = B * tx * ty;
+    auto kern = k_conv32_umma_fwd<S, OUT_F32>;
+    int grid = 0;
+    if (!grid_for(kern, Smem<S>::bytes, nt, grid))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 convolution: launch attributes");
+    kern<<<grid, 128, Smem<S>::bytes, st>>>(map, theta + UC * UC * 9, wpack, out, Ho, tx, ty, nt, err);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 convolution launch");
+    return REG_OK;
+}
+
+}  // namespace
+
+int cnn_conv32_umma_words() { return UW_BYTES / 4; }
+
+reg_status cnn_conv32_umma(const uint16_t *in, int H, const float *theta, void *out, bool out_f32, int B, int S,
+                           cudaStream_t st, uint32_t *wpack, int *err)
+{
+    if (S == 1)
+        return out_f32 ? launch_fwd<1, true>(in, H, theta, out, B, st, wpack, err)
+                       : launch_fwd<1, false>(in, H, theta, out, B, st, wpack, err);
+    if (S == 2)
+        return out_f32 ? launch_fwd<2, true>(in, H, theta, out, B, st, wpack, err)
+                       : launch_fwd<2, false>(in, H, theta, out, B, st, wpack, err);
+    return reg_internal_fail(REG_EINVAL, "tcgen05 convolution: stride must be 1 or 2");
+}
+
+reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
+                            cudaStream_t st, uint32_t *wpack, int *err)
+{
+    k_pack_w32_umma<true><<<(UW_BYTES / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    const int tx = (H + UTW - 1) / UTW, ty = (H + UTH - 1) / UTH, nt = B * tx * ty;
+    int grid = 0;
+    if (!grid_for(k_conv32_umma_dgrad, Smem<1>::bytes, nt, grid))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient: launch attributes");
+    k_conv32_umma_dgrad<<<grid, 128, Smem<1>::bytes, st>>>(gz, H, wpack, reinterpret_cast<const uint4 *>(mask), gx,
+                                                            tx, ty, nt, err);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient launch");
+    return REG_OK;
+}

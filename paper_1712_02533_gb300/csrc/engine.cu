@@ -2135,6 +2135,7 @@ reg_status reg_cnn_init_series(reg_series_t s, int32_t series, reg_cnn_t h, int3
         if (st == REG_OK && cudaGetLastError() != cudaSuccess) st = fail(REG_ECUDA, "learned initialiser kernels");
     }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess && st == REG_OK) st = fail(REG_ECUDA, "sync");
+    if (st == REG_OK) st = cnn_check_device_error(h);
     dfree(s, x, 0);
     dfree(s, y, 0);
     if (st == REG_OK) si.pre_from_slots = true;

@@ -41,14 +41,16 @@ def test_forward_loss_and_gradients_match_the_oracle(reg):
         assert np.abs(gb - ob).max() <= 1e-5 * np.abs(ob).max(), k
 
 
-@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3)])
+@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3), (88, 3)])
 def test_tensor_core_forward_matches_the_bf16_operand_oracle(reg, side, batch):
     """The 32 -> 32 layers on the tensor cores take BF16 operands and accumulate
     in FP32: against the oracle with the same operand rounding the output agrees
     to FP32 accumulation plus the rare operand that rounds the other way (its
     FP32 input differs from the FP64 one in the last bits); against the exact
     oracle it differs by the BF16 operand error.  Side 36 leaves 81 pixels per
-    pair in the 32-channel layers, a ragged last tile."""
+    pair in the 32-channel layers, a ragged last tile; side 88 gives the
+    stride-1 layers 22 x 22 pixels, several tiles of 16 x 8 with ragged rows
+    and columns."""
     import torch
     import synth
     from oracle import cnn as ocnn
@@ -211,14 +213,21 @@ def test_trained_network_gains_over_the_identity_start(reg, syn):
     assert err["learned_tc"] < 0.8 * err["identity"], err
 
 
-@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3)])
+@pytest.mark.parametrize("side,batch", [(64, 2), (36, 3), (88, 3)])
 def test_tensor_core_training_gradients_match_the_bf16_operand_oracle(reg, side, batch):
     """Training on the tensor cores (reg_cnn_loss_grad_tc): the 32-channel
     layers' forward and weight gradients and the stride-1 layers' data
     gradients take BF16 operands.  Against the oracle with the same operand
     rounding the loss and every parameter gradient agree to FP32 accumulation
     plus the rare operand that rounds the other way; against the exact oracle
-    they differ by the BF16 operand error.  Side 36 gives ragged tiles."""
+    they differ by the BF16 operand error.  Sides 36 and 88 give ragged tiles.
+
+    An operand that rounds the other way moves the pre-activations of its
+    cone by about a BF16 unit, which can turn a ReLU mask near zero; a turned
+    mask passes a full gradient term.  The oracle shows the same sensitivity:
+    its own gradients move that much when its input moves by one FP32 unit.
+    The bound per layer is therefore the larger of a fixed floor and four
+    times that spread (elementwise maximum over two perturbations)."""
     import torch
     import synth
     from oracle import cnn as ocnn
@@ -234,13 +243,23 @@ def test_tensor_core_training_gradients_match_the_bf16_operand_oracle(reg, side,
     lb, gb = ocnn.loss_and_grad(th, x64, t64, bf16_layers=(1, 2, 3, 4), bf16_data=(2, 3, 4),
                                 bf16_weights=(1, 2, 3, 4))
     le, ge = ocnn.loss_and_grad(th, x64, t64)
+    spread = np.zeros_like(gb)
+    for seed in (7, 8):
+        xp = x64 * (1.0 + 2.0 ** -24 * np.random.default_rng(seed).standard_normal(x.shape))
+        spread = np.maximum(spread, np.abs(ocnn.loss_and_grad(th, xp, t64, bf16_layers=(1, 2, 3, 4),
+                                                              bf16_data=(2, 3, 4), bf16_weights=(1, 2, 3, 4))[1] - gb))
     assert abs(loss - lb) <= 1e-4 * lb, (loss, lb, le)
     worst_b, worst_e = 0.0, 0.0
-    for k, ((gw, gbias), (bw, bb), (ew, eb)) in enumerate(zip(ocnn.unpack(g.astype(np.float64)), ocnn.unpack(gb),
-                                                             ocnn.unpack(ge))):
+    for k, ((gw, gbias), (bw, bb), (ew, eb), (sw, _)) in enumerate(zip(ocnn.unpack(g.astype(np.float64)),
+                                                                       ocnn.unpack(gb), ocnn.unpack(ge),
+                                                                       ocnn.unpack(spread))):
         sc = np.abs(bw).max()
         err = np.abs(gw - bw)
-        assert err.max() <= 2e-2 * sc and np.median(err) <= 2e-4 * sc, (k, err.max() / sc, np.median(err) / sc)
+        tol_max = max(2e-2 * sc, 4.0 * sw.max())
+        tol_med = max(2e-4 * sc, 4.0 * np.median(sw))
+        print(f"layer {k}: max {err.max() / sc:.2e} (bound {tol_max / sc:.2e}), median {np.median(err) / sc:.2e} "
+              f"(bound {tol_med / sc:.2e}) of the largest gradient")
+        assert err.max() <= tol_max and np.median(err) <= tol_med, (k, err.max() / sc, np.median(err) / sc)
         assert np.abs(gbias - bb).max() <= 2e-2 * np.abs(bb).max(), k
         worst_b = max(worst_b, float(err.max() / sc))
         worst_e = max(worst_e, float(np.abs(gw - ew).max() / np.abs(ew).max()))
