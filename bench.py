@@ -169,7 +169,7 @@ def cnn_roofline(reg, s, torch, batch=64, reps=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
     tflops = flop_pair * batch / (ms * 1e-3) / 1e12
-    return {"bound": "tensor", "kernel": "CNN forward (k_conv32_tc on the four 32->32 layers, BF16 operands, FP32 "
+    return {"bound": "tensor", "kernel": "CNN forward (k_conv32_umma_fwd, tcgen05 + TMA, on the four 32->32 layers, BF16 operands, FP32 "
                                         "accumulation; the 2->32 and 32->2 layers on the CUDA cores)",
             "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tflops / peak, 5),
             "peak_source": src, "batch": batch, "ms_per_forward": round(ms, 4),
