@@ -1155,9 +1155,9 @@ __device__ __forceinline__ void start_tile(const OpState &s, const LevelDesc &Lv
 // and cells with such a corner.  A window of up to TW rows is then finished
 // cooperatively, one queued node or cell per lane, so that the exact path
 // runs on full warps instead of on the few lanes of a row that need it.
-constexpr int TW = 8;    // rows per window
-constexpr int TQ = 64;   // queued nodes (a row adds at most 32)
-constexpr int TC = 128;  // queued cells (a row adds at most 31)
+constexpr int TW = 12;   // rows per window
+constexpr int TQ = 96;   // queued nodes (a row adds at most 32)
+constexpr int TC = 192;  // queued cells (a row adds at most 31)
 template <int JM>
 struct TrialScratch {
     float A[TW + 1][32], B[TW + 1][32];  // A, B of the window's rows; slot 0: the row before the window
