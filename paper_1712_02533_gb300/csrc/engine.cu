@@ -38,6 +38,8 @@ void launch_smooth(int grid, cudaStream_t st, const BatchDev &b);
 int step_blocks_per_sm(int which, int J);
 __global__ void k_control(BatchDev);
 __global__ void k_slot_to_planes(const float2 *, int, int, float *);
+__global__ void k_slots_to_planes(const float2 *slots, int64_t slot_elems, int k0, const float2 *slot0, int pitch,
+                                  int side, float *out);
 __global__ void k_planes_to_slot(const float *, int, float2 *, int);
 void launch_rigid(int bf16, int tiles, int n_ops, cudaStream_t st, const RigidLevel *lv, const RigidReq *req,
                   double *part, double *sums);
@@ -138,6 +140,12 @@ enum { F_P = 0, F_G, F_T, F_C, F_PLAN, F_SETUP };
 struct reg_series {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    // host transfers: a copy stream, two staging buffers (HOST_STAGE_BYTES
+    // each) and their events, so that copies overlap the kernels that fill or
+    // drain the staging buffers
+    cudaStream_t copy_stream = nullptr;
+    void *host_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_drained[2] = {nullptr, nullptr};
     reg_params p{};
     int bf16 = 0;
     int nsm = 0;
@@ -243,6 +251,21 @@ void untrack(reg_series *s, void *ptr)
             s->allocs.erase(s->allocs.begin() + i, s->allocs.begin() + i + 2);
             return;
         }
+}
+
+// The copy stream, the two staging buffers and their events of host transfers
+// (created once per handle; the buffers are tracked allocations).
+constexpr size_t HOST_STAGE_BYTES = 64ull << 20;
+
+reg_status host_transfer_setup(reg_series *s)
+{
+    if (!s->copy_stream) CK(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++) {
+        if (!s->ev_filled[i]) CK(cudaEventCreateWithFlags(&s->ev_filled[i], cudaEventDisableTiming));
+        if (!s->ev_drained[i]) CK(cudaEventCreateWithFlags(&s->ev_drained[i], cudaEventDisableTiming));
+        if (!s->host_stage[i]) RET(track(s, &s->host_stage[i], HOST_STAGE_BYTES));
+    }
+    return REG_OK;
 }
 
 BatchDev make_batch(reg_series *s)
@@ -1127,24 +1150,42 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         SeriesInfo &si = s->S[i];
         int nL = si.side + 1;
         int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(si.n_frames, (512ll << 20) / ((int64_t)nL * nL * 4 * 2)));
+        const size_t frame_bytes = (size_t)si.side * si.side * 4;
+        // host frames: chunks that fit a staging buffer, each copied on the copy
+        // stream while the pyramid kernels of the chunk before run
+        const bool staged = !frames_on_device && frame_bytes <= HOST_STAGE_BYTES;
+        if (!frames_on_device) {
+            if ((st = host_transfer_setup(s)) != REG_OK) return cleanup(st);
+            if (staged) chunk = (int)std::min<size_t>(chunk, HOST_STAGE_BYTES / frame_bytes);
+        }
         void *raw = nullptr, *stage = nullptr, *stats = nullptr;
         size_t raw_bytes = (size_t)chunk * si.frame_block * 4;
         if ((st = dalloc(s, &raw, raw_bytes)) != REG_OK) return cleanup(st);
         if ((st = dalloc(s, &stats, sizeof(double) * (2 * chunk + image_stats_part_doubles(chunk)))) != REG_OK)
             return cleanup(st);
-        size_t stage_bytes = (size_t)chunk * si.side * si.side * 4;
-        if (!frames_on_device && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
-        for (int f0 = 0; f0 < si.n_frames; f0 += chunk) {
+        size_t stage_bytes = (size_t)chunk * frame_bytes;
+        if (!frames_on_device && !staged && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
+        int nc = 0;
+        for (int f0 = 0; f0 < si.n_frames; f0 += chunk, nc++) {
             int nf = std::min(chunk, si.n_frames - f0);
+            const int b = nc & 1;
             // series i starts after all rows of the series before it (side_j rows of
             // pitch_elems per frame); frame f0 of it after f0 * side rows of its own
             const float *src = frames + (row_off + (int64_t)f0 * si.side) * pitch_elems;
             int64_t fstride = (int64_t)si.side * pitch_elems, pitch = pitch_elems;
             if (!frames_on_device) {
-                cudaError_t e = cudaMemcpy2DAsync(stage, si.side * 4, src, pitch_elems * 4, si.side * 4,
-                                                  (size_t)si.side * nf, cudaMemcpyHostToDevice, s->stream);
+                void *dst = staged ? s->host_stage[b] : stage;
+                cudaStream_t cst = staged ? s->copy_stream : s->stream;
+                cudaError_t e = cudaSuccess;
+                // the kernels that read this staging buffer two chunks ago are done
+                if (staged && nc >= 2) e = cudaStreamWaitEvent(cst, s->ev_drained[b], 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(dst, si.side * 4, src, pitch_elems * 4, si.side * 4, (size_t)si.side * nf,
+                                          cudaMemcpyHostToDevice, cst);
+                if (e == cudaSuccess && staged) e = cudaEventRecord(s->ev_filled[b], cst);
+                if (e == cudaSuccess && staged) e = cudaStreamWaitEvent(s->stream, s->ev_filled[b], 0);
                 if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "frame upload: %s", cudaGetErrorString(e)));
-                src = (const float *)stage;
+                src = (const float *)dst;
                 fstride = (int64_t)si.side * si.side;
                 pitch = si.side;
             }
@@ -1154,6 +1195,7 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
             k_embed<<<dim3(cdiv(nL, 32), cdiv(nL, 8), nf), blk, 0, s->stream>>>(
                 src, fstride, pitch, si.side, rawf + si.img_off[kL], (int64_t)si.frame_block, si.pitch[kL]);
             build_levels(s, si, rawf, f0, nf, (double *)stats);
+            if (staged) cudaEventRecord(s->ev_drained[b], s->stream);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cleanup(fail(REG_ECUDA, "pyramid kernels: %s", cudaGetErrorString(e)));
         }
@@ -1172,6 +1214,11 @@ reg_status reg_destroy_series(reg_series_t s)
     if (!s) return REG_OK;
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    for (int i = 0; i < 2; i++) {
+        if (s->ev_filled[i]) cudaEventDestroy(s->ev_filled[i]);
+        if (s->ev_drained[i]) cudaEventDestroy(s->ev_drained[i]);
+    }
     for (size_t i = 0; i + 1 < s->allocs.size(); i += 2) dfree(s, s->allocs[i], reinterpret_cast<size_t>(s->allocs[i + 1]));
     cudaStreamSynchronize(s->stream);
     if (s->h_ops) cudaFreeHost(s->h_ops);
@@ -1563,31 +1610,53 @@ reg_status reg_get_deformations(reg_series_t s, int32_t series, int32_t first, i
     SeriesInfo &si = s->S[series];
     if (first < 0 || count < 0 || first + count > si.n_frames) return fail(REG_EINVAL, "frame range out of range");
     size_t per = (size_t)2 * si.side * si.side;
-    void *tmp = nullptr;
-    float *dst = out;
-    if (!out_on_device && count > 0) {
-        RET(dalloc(s, &tmp, per * count * sizeof(float)));
-        dst = (float *)tmp;
+    for (int k = std::max(first, 1); k < first + count; k++) {
+        const SlotMeta &m = si.meta[k - 1];
+        if (m.start != 0 || m.end != k) return fail(REG_ESTATE, "phi_{0,%d} not available (run reg_prefix_scan first)", k);
     }
-    for (int k = first; k < first + count; k++) {
-        const float2 *src = nullptr;
-        if (k == 0 && si.refined) src = si.slots + (size_t)si.n_slots * si.slot_elems;
-        if (k > 0) {
-            const SlotMeta &m = si.meta[k - 1];
-            if (m.start != 0 || m.end != k) {
-                if (tmp) dfree(s, tmp, 0);
-                return fail(REG_ESTATE, "phi_{0,%d} not available (run reg_prefix_scan first)", k);
-            }
-            src = si.slots + (size_t)(k - 1) * si.slot_elems;
-        }
-        k_slot_to_planes<<<dim3(cdiv(si.side, 32), cdiv(si.side, 8)), dim3(32, 8), 0, s->stream>>>(
-            src, si.pitch[si.nl - 1], si.side, dst + (size_t)(k - first) * per);
+    const float2 *slot0 = si.refined ? si.slots + (size_t)si.n_slots * si.slot_elems : nullptr;
+    const dim3 blk(32, 8), grd(cdiv(si.side, 32), cdiv(si.side, 8));
+    auto convert = [&](int k0, int nk, float *dst) {
+        k_slots_to_planes<<<dim3(grd.x, grd.y, nk), blk, 0, s->stream>>>(si.slots, (int64_t)si.slot_elems, k0, slot0,
+                                                                         si.pitch[si.nl - 1], si.side, dst);
+    };
+    if (out_on_device || count == 0) {
+        for (int k0 = first; k0 < first + count; k0 += 65535) convert(k0, std::min(65535, first + count - k0), out + (size_t)(k0 - first) * per);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        return REG_OK;
     }
-    CK(cudaGetLastError());
-    if (tmp) {
+    // host output: chunks of frames converted into the two staging buffers on
+    // the handle's stream and copied out on the copy stream, each copy
+    // overlapping the next chunk's conversion
+    RET(host_transfer_setup(s));
+    const int fc = (int)std::max<size_t>(1, std::min<size_t>(65535, HOST_STAGE_BYTES / (per * sizeof(float))));
+    if (per * sizeof(float) > HOST_STAGE_BYTES) {
+        // frames larger than a staging buffer: one temporary buffer
+        void *tmp = nullptr;
+        RET(dalloc(s, &tmp, per * sizeof(float) * count));
+        convert(first, count, (float *)tmp);
         CK(cudaMemcpyAsync(out, tmp, per * count * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         dfree(s, tmp, 0);
+        CK(cudaStreamSynchronize(s->stream));
+        return REG_OK;
     }
+    int c = 0;
+    for (int k0 = first; k0 < first + count; k0 += fc, c++) {
+        const int nk = std::min(fc, first + count - k0), b = c & 1;
+        if (c >= 2) CK(cudaStreamWaitEvent(s->stream, s->ev_drained[b], 0));  // its last copy is done
+        convert(k0, nk, (float *)s->host_stage[b]);
+        CK(cudaEventRecord(s->ev_filled[b], s->stream));
+        CK(cudaStreamWaitEvent(s->copy_stream, s->ev_filled[b], 0));
+        CK(cudaMemcpyAsync(out + (size_t)(k0 - first) * per, s->host_stage[b], per * nk * sizeof(float),
+                           cudaMemcpyDeviceToHost, s->copy_stream));
+        CK(cudaEventRecord(s->ev_drained[b], s->copy_stream));
+    }
+    CK(cudaGetLastError());
+    // the handle's stream waits for the last copies (so that later work on it
+    // may reuse the buffers), then the host for both streams
+    for (int b = 0; b < 2 && b < c; b++) CK(cudaStreamWaitEvent(s->stream, s->ev_drained[b], 0));
+    CK(cudaStreamSynchronize(s->copy_stream));
     CK(cudaStreamSynchronize(s->stream));
     return REG_OK;
 }

@@ -1997,6 +1997,22 @@ __global__ void k_slot_to_planes(const float2 *__restrict__ slot, int pitch, int
     out[(int64_t)side * side + (int64_t)r * side + c] = v.y;
 }
 
+// Frames k0 .. k0 + gridDim.z - 1 of a series' deformations, planes (2 x side
+// x side each) from their slots: frame k > 0 from slot k - 1 (slots slot_elems
+// apart), frame 0 from slot0 (null: the identity, zero displacement).
+__global__ void k_slots_to_planes(const float2 *__restrict__ slots, int64_t slot_elems, int k0,
+                                  const float2 *__restrict__ slot0, int pitch, int side, float *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= side || c >= side) return;
+    const int k = k0 + blockIdx.z;
+    const float2 *slot = k == 0 ? slot0 : slots + (int64_t)(k - 1) * slot_elems;
+    const float2 v = slot ? slot[(int64_t)r * pitch + c] : make_float2(0.f, 0.f);
+    float *o = out + (int64_t)blockIdx.z * 2 * side * side;
+    o[(int64_t)r * side + c] = v.x;
+    o[(int64_t)side * side + (int64_t)r * side + c] = v.y;
+}
+
 // planes (2 x n x n) -> slot grid (n x n float2 with pitch)
 __global__ void k_planes_to_slot(const float *__restrict__ in, int n, float2 *__restrict__ slot, int pitch)
 {

@@ -59,3 +59,27 @@ def test_bf16_storage_error_against_fp32(reg, syn):
     err = np.abs(out[reg.STORAGE_BF16] - out[reg.STORAGE_F32])
     assert np.isfinite(err).all()
     assert err.max() < 0.5, float(err.max())
+
+
+def test_host_transfers_match_device_transfers(reg, syn):
+    """Frames from host memory go up in chunks through two staging buffers
+    (copies overlapping the pyramid kernels), and deformations come down the
+    same way; both must give exactly what the device-resident path gives.
+    20 frames of 1024^2 span two upload chunks (16 frames of 4 MB fill a 64 MB
+    staging buffer) and three download chunks (8 frames of 8 MB, the last one
+    ragged)."""
+    import torch
+    frames = syn.series(21, 20, 1024, spacing=16.0, sigma=2.0, peak=10.0, drift_sd=0.5, dist_amp=1.0)
+    p = reg.default_params(n_levels=5, iter_max=3, lam=10.0)
+    with reg.Series([frames], p) as s:
+        s.prefix_scan(reg.SKLANSKY)
+        u_host = s.get_deformations()
+        u_dev = torch.empty((20, 2, 1024, 1024), dtype=torch.float32, device="cuda")
+        s.get_deformations(out=u_dev)
+    with reg.Series([torch.from_numpy(frames).cuda()], p) as s:
+        s.prefix_scan(reg.SKLANSKY)
+        u_ref = torch.empty((20, 2, 1024, 1024), dtype=torch.float32, device="cuda")
+        s.get_deformations(out=u_ref)
+    assert np.array_equal(u_host, u_dev.cpu().numpy())
+    assert np.array_equal(u_host, u_ref.cpu().numpy())
+    assert np.abs(u_host[1:]).max() > 0.1  # the frames did move
