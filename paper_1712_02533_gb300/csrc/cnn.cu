@@ -60,9 +60,14 @@ template <int C, int O, int S, bool RELU, bool OUT_PLANAR = false>
 __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, int H, const float *__restrict__ theta,
                                                   void *__restrict__ out, int Ho, int total)
 {
-    __shared__ float w[O * C * 9];
+    // weights as [c][tap][o], so that one vector load brings the weights of
+    // several output channels for an input value
+    __shared__ __align__(16) float w[O * C * 9];
     __shared__ float bias[O];
-    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) w[i] = theta[i];
+    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) {
+        const int o = i / (C * 9), ck = i - o * (C * 9);
+        w[ck * O + o] = theta[i];
+    }
     for (int i = threadIdx.x; i < O; i += blockDim.x) bias[i] = theta[O * C * 9 + i];
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,11 +86,27 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, 
                 const int iy = S * y + dy - 1, ix = S * x + dx - 1;
                 v[dy * 3 + dx] = (iy >= 0 && iy < H && ix >= 0 && ix < H) ? src[iy * H + ix] : 0.f;
             }
+        // per output channel the products are added in the order (c, tap)
 #pragma unroll
-        for (int o = 0; o < O; o++) {
-            const float *wk = w + (o * C + c) * 9;
+        for (int k = 0; k < 9; k++) {
+            const float *wk = w + (c * 9 + k) * O;
+            if constexpr (O % 4 == 0) {
 #pragma unroll
-            for (int k = 0; k < 9; k++) acc[o] = fmaf(wk[k], v[k], acc[o]);
+                for (int q = 0; q < O / 4; q++) {
+                    const float4 wv = reinterpret_cast<const float4 *>(wk)[q];
+                    acc[4 * q] = fmaf(wv.x, v[k], acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(wv.y, v[k], acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(wv.z, v[k], acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(wv.w, v[k], acc[4 * q + 3]);
+                }
+            } else if constexpr (O == 2) {
+                const float2 wv = *reinterpret_cast<const float2 *>(wk);
+                acc[0] = fmaf(wv.x, v[k], acc[0]);
+                acc[1] = fmaf(wv.y, v[k], acc[1]);
+            } else {
+#pragma unroll
+                for (int o = 0; o < O; o++) acc[o] = fmaf(wk[o], v[k], acc[o]);
+            }
         }
     }
 #pragma unroll
@@ -120,8 +141,13 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
                                                        const void *__restrict__ a_below, float *__restrict__ gx,
                                                        int H, int total)
 {
-    __shared__ float w[O * C * 9];
-    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) w[i] = theta[i];
+    // weights as [o][tap][c], so that one vector load brings the weights of
+    // several input channels for an output gradient value
+    __shared__ __align__(16) float w[O * C * 9];
+    for (int i = threadIdx.x; i < O * C * 9; i += blockDim.x) {
+        const int o = i / (C * 9), r = i - o * (C * 9), c = r / 9, k = r - c * 9;
+        w[(o * 9 + k) * C + c] = theta[i];
+    }
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= total) return;
@@ -141,9 +167,20 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
             const int ox = tx / S;
             for (int o = 0; o < O; o++) {
                 const float g = gz[(((int64_t)b * O + o) * Ho + oy) * Ho + ox];
-                const float *wk = w + o * C * 9 + dy * 3 + dx;
+                const float *wk = w + (o * 9 + dy * 3 + dx) * C;
+                if constexpr (C % 4 == 0) {
 #pragma unroll
-                for (int c = 0; c < C; c++) acc[c] = fmaf(wk[c * 9], g, acc[c]);
+                    for (int q = 0; q < C / 4; q++) {
+                        const float4 wv = reinterpret_cast<const float4 *>(wk)[q];
+                        acc[4 * q] = fmaf(wv.x, g, acc[4 * q]);
+                        acc[4 * q + 1] = fmaf(wv.y, g, acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(wv.z, g, acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(wv.w, g, acc[4 * q + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; c++) acc[c] = fmaf(wk[c], g, acc[c]);
+                }
             }
         }
     }

@@ -1446,7 +1446,7 @@ __device__ __forceinline__ void write_partials(const BatchDev &b, int item, cons
 }  // namespace
 
 template <bool BF16, int JM>
-__global__ void __launch_bounds__(REG_STRIP_THREADS, 5) k_trial(BatchDev b)
+__global__ void __launch_bounds__(REG_STRIP_THREADS, 4) k_trial(BatchDev b)
 {
     __shared__ TrialScratch<JM> scratch[REG_STRIP_THREADS / 32];
     const int lane = threadIdx.x & 31;
