@@ -16,8 +16,8 @@ A convolution of stride s computes, for output channel o at (y, x),
 with in_pad the input with one ring of zeros.  The tensor-core form of the
 forward rounds the operands of the 32 -> 32 layers (their input activations and
 weights, not the biases) to BF16 (8 significant bits, round to nearest, ties to
-even) and contracts them exactly; ``forward(..., bf16_layers=(1, 2, 3, 4))``
-models that.  The loss is the mean of the
+even) and contracts them exactly; ``forward(..., bf16_layers=(0, ..., 5))``
+models the tensor-core forward, all six layers of which take BF16 operands.  The loss is the mean of the
 squared differences to a target displacement.  Parameters are one flat vector:
 layer by layer, W (O x C x 3 x 3, row-major) then b (O).
 """
@@ -117,7 +117,7 @@ def loss(theta, x, target):
     return float(np.mean((y - target) ** 2))
 
 
-def loss_and_grad(theta, x, target, bf16_layers=(), bf16_data=(), bf16_weights=()):
+def loss_and_grad(theta, x, target, bf16_layers=(), bf16_data=(), bf16_weights=(), bf16_stored=()):
     """Mean squared error and its gradient with respect to the flat parameters.
 
     The tensor-core form of training takes BF16 operands in three places,
@@ -125,8 +125,10 @@ def loss_and_grad(theta, x, target, bf16_layers=(), bf16_data=(), bf16_weights=(
     the forward of the layers in bf16_layers (their input and weights), the
     data gradient of the layers in bf16_data (the output gradient and the
     weights), and the weight gradient of the layers in bf16_weights (the
-    output gradient and the layer's input).  Bias gradients sum the
-    unrounded output gradient."""
+    output gradient and the layer's input).  A layer in bf16_stored keeps its
+    input activation in BF16, so its weight gradient (on the CUDA cores, the
+    output gradient unrounded) takes the rounded input.  Bias gradients sum
+    the unrounded output gradient."""
     layers = unpack(theta)
     y, cache = forward(theta, x, keep=True, bf16_layers=bf16_layers)
     g = 2.0 * (y - target) / y.size
@@ -141,6 +143,8 @@ def loss_and_grad(theta, x, target, bf16_layers=(), bf16_data=(), bf16_weights=(
             ga = conv_backward(a, round_bf16(W), s, round_bf16(g))[0]
         if k in bf16_weights:
             gW = conv_backward(round_bf16(a), W, s, round_bf16(g))[1]
+        elif k in bf16_stored:
+            gW = conv_backward(round_bf16(a), W, s, g)[1]
         grads[k] = (gW, gb)
         g = ga
     return float(np.mean((y - target) ** 2)), pack(grads)

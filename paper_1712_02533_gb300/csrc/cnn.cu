@@ -10,12 +10,13 @@
 // Parameters: one flat float vector, layer by layer W (O x C x 3 x 3) then b.
 //
 // Layout: the FP32 path keeps activations NCHW in float, one buffer per layer,
-// on the CUDA cores.  The tensor-core path runs the four 32 -> 32 layers with
-// BF16 operands and FP32 accumulation (forward and stride-1 data gradients by
-// tcgen05 with TMEM accumulators, weight gradients by mma.sync); the outputs
-// of layers 0..3 are then BF16 in a channel-group planar layout
-// [b][c / 8][y][x][c % 8], the operand layout of those kernels, and layer 4
-// writes FP32 NCHW for the last layer.
+// on the CUDA cores.  The tensor-core path runs with BF16 operands and FP32
+// accumulation: the forward of all six layers and the stride-1 data gradients
+// on tcgen05 with TMEM accumulators, the 32 -> 32 weight gradients by
+// mma.sync; the outputs of layers 0..4 are then BF16 in a channel-group
+// planar layout [b][c / 8][y][x][c % 8], the operand layout of those kernels.
+// The remaining gradients (first and last layers' weights, the stride-2 and
+// last layers' data) run on the CUDA cores in FP32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -209,8 +210,9 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
 // each (grid O C split), and each block writes its 10 sums to part; the
 // layers with few (o, c) pairs (2 -> 32, 32 -> 2) keep the GPU busy that way,
 // and k_bwd_weight_sum adds the parts in order.
-template <int C, int O, int S>
-__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict__ in, int H,
+// IN_PLANAR: in is BF16 in the planar layout of the tensor-core layers (C = 32).
+template <int C, int O, int S, bool IN_PLANAR = false>
+__global__ void __launch_bounds__(256) k_conv_bwd_weight(const void *__restrict__ in_, int H,
                                                          const float *__restrict__ gz, int Ho, int B,
                                                          float *__restrict__ grad, int split,
                                                          float *__restrict__ part)
@@ -225,13 +227,17 @@ __global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const int b = p / per, q = p % per, y = q / Ho, x = q % Ho;
         const float g = gz[((int64_t)b * O + o) * per + q];
-        const float *src = in + ((int64_t)b * C + c) * H * H;
+        const float *src = reinterpret_cast<const float *>(in_) + ((int64_t)b * C + c) * H * H;
+        const __nv_bfloat16 *srcb =
+            reinterpret_cast<const __nv_bfloat16 *>(in_) + ((int64_t)(4 * b + c / 8) * H * H) * 8 + (c & 7);
 #pragma unroll
         for (int dy = 0; dy < 3; dy++)
 #pragma unroll
             for (int dx = 0; dx < 3; dx++) {
                 const int iy = S * y + dy - 1, ix = S * x + dx - 1;
-                const float v = (iy >= 0 && iy < H && ix >= 0 && ix < H) ? src[iy * H + ix] : 0.f;
+                float v = 0.f;
+                if (iy >= 0 && iy < H && ix >= 0 && ix < H)
+                    v = IN_PLANAR ? __bfloat162float(srcb[(int64_t)(iy * H + ix) * 8]) : src[iy * H + ix];
                 acc[dy * 3 + dx] = fmaf(g, v, acc[dy * 3 + dx]);
             }
         acc[9] += g;
@@ -322,18 +328,19 @@ void fwd(const float *in, int H, const float *theta, void *out, int B, cudaStrea
     k_conv_fwd<C, O, S, RELU, OUT_PLANAR><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
 }
 
-template <int C, int O, int S>
-void bwd(const float *in, int H, const float *gz, const float *theta, const float *a_below, float *gx, float *grad,
+// PLANAR: the layer's input and the activation below are BF16 planar.
+template <int C, int O, int S, bool PLANAR = false>
+void bwd(const void *in, int H, const float *gz, const float *theta, const void *a_below, float *gx, float *grad,
          int B, cudaStream_t st, float *part)
 {
     const int Ho = (H + 2 - 3) / S + 1;
     // (o, c) pairs times parts of the pixel range: about a thousand blocks
     const int split = (O * C >= 512) ? 1 : std::min(64, 1024 / (O * C));
-    k_conv_bwd_weight<C, O, S><<<O * C * split, 256, 0, st>>>(in, H, gz, Ho, B, grad, split, part);
+    k_conv_bwd_weight<C, O, S, PLANAR><<<O * C * split, 256, 0, st>>>(in, H, gz, Ho, B, grad, split, part);
     if (split > 1) k_bwd_weight_sum<C, O><<<(O * C * 10 + 255) / 256, 256, 0, st>>>(part, split, grad);
     if (gx) {
         const int total = B * H * H;
-        k_conv_bwd_data<C, O, S><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
+        k_conv_bwd_data<C, O, S, PLANAR><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
     }
 }
 
@@ -348,8 +355,13 @@ struct reg_cnn {
     float *g0 = nullptr, *g1 = nullptr;  // gradient ping-pong (largest activation)
     float *gy = nullptr;
     double *partial = nullptr, *loss = nullptr;
-    uint16_t *actb[4] = {nullptr};  // tensor-core path: outputs of layers 0..3, BF16 planar [b][c/8][y][x][c%8]
+    uint16_t *actb[5] = {nullptr};  // tensor-core path: outputs of layers 0..4, BF16 planar [b][c/8][y][x][c%8]
     uint32_t *wpack_u = nullptr;  // the 32 -> 32 layers' weights in the tcgen05 operand layout
+    uint32_t *wpack_d = nullptr;  // the same, flipped and transposed for the data gradients
+    uint32_t *wpack_first = nullptr, *wpack_last = nullptr;  // the first and last layers, tcgen05 layouts
+    // parameter version (set_params, adam_step) and the version each packed
+    // copy was made from (forward: layers 0..5): the packing runs only after a change
+    int64_t version = 0, packed_fwd[6] = {-1, -1, -1, -1, -1, -1}, packed_dgrad[4] = {-1, -1, -1, -1};
     int *uerr = nullptr;          // error word of the tcgen05 kernels (a wait ran out): device view
     int *uerr_host = nullptr;     // the same word, pinned host memory mapped into the device
     float *wpart = nullptr;     // per-block partial weight gradients of the tensor-core training
@@ -405,16 +417,21 @@ reg_status cnn_forward(reg_cnn *h, const float *x, int B, float *y, cudaStream_t
         const int H = in_side(k, S);
         const float *th = h->theta + param_offset(k);
         float *out = (k == NL - 1 && y) ? y : h->act[k];
-        if (tc && k <= 4) {
-            // tensor-core path: layer 0 writes BF16 planar activations, the
-            // 32 -> 32 layers run on tcgen05 from them (layer 4 back to FP32
-            // NCHW for the last layer)
-            reg_status rs = REG_OK;
-            if (k == 0) fwd<2, 32, 2, true, true>(a, H, th, h->actb[0], B, st);
+        if (tc) {
+            // tensor-core path, all six layers on tcgen05: layer 0 from the FP32
+            // input, the others from the BF16 planar activations, which layers
+            // 0..4 write; layer 5 writes the FP32 output
+            const bool pack = h->packed_fwd[k] != h->version;
+            reg_status rs;
+            if (k == 0)
+                rs = cnn_first_umma(a, H, th, h->actb[0], B, st, h->wpack_first, pack, h->uerr);
+            else if (k == NL - 1)
+                rs = cnn_last_umma(h->actb[k - 1], H, th, out, B, st, h->wpack_last, pack, h->uerr);
             else
-                rs = cnn_conv32_umma(h->actb[k - 1], H, th, k == 4 ? (void *)out : (void *)h->actb[k], k == 4, B,
-                                     LAYERS[k].S, st, h->wpack_u + (k - 1) * cnn_conv32_umma_words(), h->uerr);
+                rs = cnn_conv32_umma(h->actb[k - 1], H, th, h->actb[k], false, B, LAYERS[k].S, st,
+                                     h->wpack_u + (k - 1) * cnn_conv32_umma_words(), pack, h->uerr);
             if (rs != REG_OK) return rs;
+            h->packed_fwd[k] = h->version;
         } else {
             switch (k) {
             case 0: fwd<2, 32, 2, true>(a, H, th, out, B, st); break;
@@ -453,7 +470,7 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
     int64_t big = 0;
     for (int k = 0; k < NL && ok; k++) {
         ok = alloc((void **)&h->act[k], sizeof(float) * act_elems(k, side) * max_batch);
-        if (ok && k < 4) ok = alloc((void **)&h->actb[k], sizeof(uint16_t) * act_elems(k, side) * max_batch);
+        if (ok && k < 5) ok = alloc((void **)&h->actb[k], sizeof(uint16_t) * act_elems(k, side) * max_batch);
         big = std::max(big, act_elems(k, side));
     }
     big = std::max(big, (int64_t)2 * side * side);
@@ -462,6 +479,9 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
          alloc((void **)&h->gy, sizeof(float) * act_elems(NL - 1, side) * max_batch) &&
          alloc((void **)&h->partial, sizeof(double) * 1024) && alloc((void **)&h->loss, sizeof(double)) &&
          alloc((void **)&h->wpack_u, sizeof(uint32_t) * 4 * cnn_conv32_umma_words()) &&
+         alloc((void **)&h->wpack_d, sizeof(uint32_t) * 4 * cnn_conv32_umma_words()) &&
+         alloc((void **)&h->wpack_first, sizeof(uint32_t) * cnn_first_umma_words()) &&
+         alloc((void **)&h->wpack_last, sizeof(uint32_t) * cnn_last_umma_words()) &&
          cudaHostAlloc((void **)&h->uerr_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostGetDevicePointer((void **)&h->uerr, h->uerr_host, 0) == cudaSuccess &&
          alloc((void **)&h->wpart, sizeof(float) * (size_t)(cnn_wgrad32_tc_blocks() + 1) * 32 * 288);
@@ -489,6 +509,7 @@ reg_status reg_cnn_set_params(reg_cnn_t h, const float *theta, int32_t on_device
     CKC(cudaMemsetAsync(h->m, 0, sizeof(float) * h->n, h->stream));
     CKC(cudaMemsetAsync(h->v, 0, sizeof(float) * h->n, h->stream));
     h->step = 0;
+    h->version++;
     CKC(cudaStreamSynchronize(h->stream));
     return REG_OK;
 }
@@ -557,13 +578,22 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
             rs = cnn_wgrad32_tc(inb, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
             if (rs != REG_OK) return rs;
             if (LAYERS[k].S == 1) {
-                rs = cnn_dgrad32_umma(gz, H, th, inb, gx, B, st, h->wpack_u + (k - 1) * cnn_conv32_umma_words(),
+                const bool pack = h->packed_dgrad[k - 1] != h->version;
+                rs = cnn_dgrad32_umma(gz, H, th, inb, gx, B, st, h->wpack_d + (k - 1) * cnn_conv32_umma_words(), pack,
                                       h->uerr);
                 if (rs != REG_OK) return rs;
+                h->packed_dgrad[k - 1] = h->version;
             } else {
                 const int Ho = (H + 2 - 3) / LAYERS[k].S + 1, total = B * H * H;
                 k_conv_bwd_data<32, 32, 2, true><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, th, inb, gx, H, total);
             }
+            gz = gx;
+            continue;
+        }
+        if (tc && k == NL - 1) {
+            // the last layer's input (and the mask below) is the planar BF16
+            // output of layer 4
+            bwd<32, 2, 1, true>(h->actb[k - 1], H, gz, th, h->actb[k - 1], gx, gr, B, st, h->wpart);
             gz = gx;
             continue;
         }
@@ -589,6 +619,7 @@ reg_status reg_cnn_adam_step(reg_cnn_t h, double lr, double beta1, double beta2,
     if (!h || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
         return cnn_fail(REG_EINVAL, "bad argument");
     h->step++;
+    h->version++;
     const double c1 = 1.0 - std::pow(beta1, (double)h->step), c2 = 1.0 - std::pow(beta2, (double)h->step);
     k_adam<<<(int)std::min<int64_t>(1024, (h->n + 255) / 256), 256, 0, h->stream>>>(
         h->theta, h->grad, h->m, h->v, h->n, (float)lr, (float)beta1, (float)beta2, (float)eps, (float)c1, (float)c2);
@@ -605,11 +636,14 @@ reg_status reg_cnn_destroy(reg_cnn_t h)
     cudaFree(h->m);
     cudaFree(h->v);
     for (int k = 0; k < NL; k++) cudaFree(h->act[k]);
-    for (int k = 0; k < 4; k++) cudaFree(h->actb[k]);
+    for (int k = 0; k < 5; k++) cudaFree(h->actb[k]);
     cudaFree(h->g0);
     cudaFree(h->g1);
     cudaFree(h->gy);
     cudaFree(h->wpack_u);
+    cudaFree(h->wpack_d);
+    cudaFree(h->wpack_first);
+    cudaFree(h->wpack_last);
     if (h->uerr_host) cudaFreeHost(h->uerr_host);
     cudaFree(h->wpart);
     cudaFree(h->partial);

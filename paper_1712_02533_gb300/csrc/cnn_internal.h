@@ -28,18 +28,32 @@ int cnn_wgrad32_tc_blocks();
 // bias and ReLU on the fifth-generation tensor cores (tcgen05.mma, accumulator
 // in TMEM, BF16 operands, FP32 accumulation): in (planar, B x 32 x H x H, read
 // by TMA; H even for S = 2), out (B x 32 x Ho x Ho) planar, or FP32 NCHW with
-// out_f32; theta: the layer's W then b; wpack: device scratch of
-// cnn_conv32_umma_words() words, 16-byte aligned; err: a device word set to
-// nonzero when a wait of the kernel ran out (the result is then invalid).
+// out_f32; theta: the layer's W then b; wpack: device buffer of
+// cnn_conv32_umma_words() words, 16-byte aligned, holding the packed weights
+// (pack: pack theta into it first, else it holds them from an earlier call);
+// err: a device word set to nonzero when a wait of the kernel ran out (the
+// result is then invalid).
 reg_status cnn_conv32_umma(const uint16_t *in, int H, const float *theta, void *out, bool out_f32, int B, int S,
-                           cudaStream_t st, uint32_t *wpack, int *err);
+                           cudaStream_t st, uint32_t *wpack, bool pack, int *err);
 // Data gradient of a stride-1 32 -> 32 layer on the tensor cores: gx (FP32
 // NCHW, B x 32 x H x H) = (mask > 0) * conv(gz, W flipped and transposed), gz
 // (FP32 NCHW) the gradient with respect to the layer's pre-activation output,
 // mask the activation below (planar).
 reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
-                            cudaStream_t st, uint32_t *wpack, int *err);
+                            cudaStream_t st, uint32_t *wpack, bool pack, int *err);
 int cnn_conv32_umma_words();
+// The last layer (32 -> 2, stride 1, no ReLU) on the same kernel with N = 16
+// (output rows 2..15 zero): in planar (B x 32 x H x H), out FP32 NCHW (B x 2 x
+// H x H); wpack: cnn_last_umma_words() words.
+reg_status cnn_last_umma(const uint16_t *in, int H, const float *theta, float *out, int B, cudaStream_t st,
+                         uint32_t *wpack, bool pack, int *err);
+int cnn_last_umma_words();
+// The first layer (2 -> 32, stride 2, ReLU) on the tensor cores: x FP32 NCHW
+// (B x 2 x H x H, H even), rounded to BF16; out planar (B x 32 x H/2 x H/2);
+// wpack: cnn_first_umma_words() words.
+reg_status cnn_first_umma(const float *x, int H, const float *theta, uint16_t *out, int B, cudaStream_t st,
+                          uint32_t *wpack, bool pack, int *err);
+int cnn_first_umma_words();
 // After the handle's stream has been synchronised: REG_ECUDA if a tcgen05
 // kernel reported a wait that ran out since the last check (and clear it).
 reg_status cnn_check_device_error(reg_cnn *h);

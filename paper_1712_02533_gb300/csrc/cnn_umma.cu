@@ -1,101 +1,127 @@
-// The learned initialiser's 32 -> 32 channel 3x3 convolutions (zero padding 1,
-// stride 1 or 2) on the fifth-generation tensor cores: tcgen05.mma with the
-// accumulator in tensor memory (TMEM), BF16 operands, FP32 accumulation.
+// The learned initialiser's convolutions on the fifth-generation tensor cores:
+// tcgen05.mma with the accumulator in tensor memory (TMEM), BF16 operands,
+// FP32 accumulation.  All six layers of the tensor-core forward run here: the
+// four 32 -> 32 layers and the last layer (32 -> 2) from TMA-loaded tiles,
+// the first layer (2 -> 32) from tiles the CTA's threads stage; and the data
+// gradients of the three stride-1 32 -> 32 layers.
 //
 // Implicit GEMM per output tile of 16 rows x 8 columns of one image:
 //   D[m][o] = sum_k A[m][k] W[o][k],   m = 8 (tile row) + (tile column),
-//   k = (3 dy + dx) * 32 + c,          M = 128, N = 32, K = 288 = 18 steps of 16,
+//   k = (3 dy + dx) * C + c,           M = 128, N = 32 (last layer: 16, of which
+// the 2 output channels are real), K = 9 C in steps of 16,
 // A[m][k] = in_pad[c][S y + dy][S x + dx] for output pixel (y, x) of tile row m.
 //
-// Activations between the 32-channel layers are BF16 in a channel-group
-// planar layout, [b][cg][y][x][8 channels] (cg = c / 8): 16 bytes per pixel
-// and channel group.  It is the K-major operand layout of the tensor cores, so
-// a tile's input needs no conversion.
+// Activations between layers are BF16 in a channel-group planar layout,
+// [b][cg][y][x][8 channels] (cg = c / 8): 16 bytes per pixel and channel
+// group.  It is the K-major operand layout of the tensor cores, so a tile's
+// input needs no conversion.
 //
 // Shared-memory operands in the K-major layout without swizzling: "core
 // matrices" of 8 rows x 16 bytes (8 BF16 values along k), each stored as 128
 // contiguous bytes, rows 16 bytes apart.  A descriptor gives the start address
 // and two strides: between core matrices adjacent along M (or N) and along K.
-//   - Weights, packed once per call by k_pack_w32_umma: [tap][cg][o][8
-//     channels] BF16, 18 KB.  For a k-step (tap, half h) the operand starts at
-//     ((4 tap + 2 h) 32) 16 bytes; N-stride 128 B, K-stride 512 B.  They reach
-//     shared memory by a bulk asynchronous copy (cp.async.bulk).
+//   - Weights, packed by k_pack_umma when the parameters change: [tap][cg][o][8
+//     channels] BF16.  For a k-step (tap, half h) the operand starts at
+//     ((4 tap + 2 h) N) 16 bytes; N-stride 128 B, K-stride 16 N bytes.  They
+//     reach shared memory by a bulk asynchronous copy (cp.async.bulk).
 //   - The input tile with its halo, [cg][halo row][halo column][8 channels].
 //     Every 8 output pixels of a tile row read 8 consecutive halo columns for
 //     any tap, so each tap of the 3 x 3 window is the same operand with a
 //     shifted start address: tap (dy, dx) starts at halo row dy, column dx.
-//     The forward loads the tile with one TMA tensor copy
+//     The 32-channel layers load the tile with one TMA tensor copy
 //     (cp.async.bulk.tensor, 18 rows x 10 columns x 4 groups; zeros outside
 //     the image).  With stride 2 the output columns x read halo columns
 //     2 x + dx, so the halo is loaded as two copies, the columns of one
 //     parity each (a view of the activations with the column split into
 //     (x / 2, x % 2)), and a tap starts in the copy of its parity dx & 1 at
 //     column dx >> 1; the M-stride then covers two halo rows.
+//   - The first layer has 2 input channels, padded to one group of 8: a
+//     k-step of 16 takes two taps, whose core matrices the descriptor's
+//     K-stride joins (the ninth tap pairs with zero weights), 5 MMAs a tile.
 //
-// One thread issues the tile's TMA copy and its 18 MMAs, committed to an
-// mbarrier; each warp then reads its 32 TMEM lanes (= tile rows 32 w .. 32 w
-// + 31) with tcgen05.ld and writes bias + ReLU, as BF16 in the planar layout
-// (or FP32 NCHW for the last 32-channel layer).  CTAs loop over tiles with two
-// accumulators (64 TMEM columns), so that the MMAs of a tile run while the
-// previous one is written, and (stride 1) two halo buffers, so that the next
-// tile's copy is in flight meanwhile too.  The data gradient of a stride-1
-// layer runs the same GEMM on the output gradient (FP32 NCHW, staged and
-// rounded by the CTA's threads) with flipped and transposed weights, times
-// the ReLU mask of the layer below.  Every wait on an mbarrier is bounded
-// (one second of the global timer); a wait that runs out sets the error word,
-// the CTA stops issuing work, frees its TMEM and returns.
+// One thread issues the tile's copy and MMAs, committed to an mbarrier; each
+// warp then reads its 32 TMEM lanes (= tile rows 32 w .. 32 w + 31) with
+// tcgen05.ld and writes the result: bias + ReLU as planar BF16, or FP32 NCHW
+// (the 32-channel layer before the last, for its data gradient's mask and the
+// last layer, and the last layer's two channels).  CTAs loop over tiles with
+// two accumulators, so that the MMAs of a tile run while the previous one is
+// written, and (stride 1) two halo buffers, so that the next tile's copy is
+// in flight meanwhile too.  The data gradient of a stride-1 layer runs the
+// same GEMM on the output gradient (FP32 NCHW, staged and rounded by the
+// CTA's threads) with flipped and transposed weights, times the ReLU mask of
+// the layer below.  Every wait on an mbarrier is bounded (one second of the
+// global timer); a wait that runs out sets the error word, the CTA stops
+// issuing work, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "cnn_internal.h"
 
 namespace {
 
-constexpr int UC = 32;                     // channels in and out
+constexpr int UC = 32;                     // channels of the 32-channel layers
 constexpr int UTH = 16, UTW = 8;           // output tile: 16 rows x 8 columns = the 128 rows of the MMA
-constexpr int UW_BYTES = 9 * 4 * 32 * 16;  // packed weights
-constexpr int U_TMEM_COLS = 64;            // two FP32 accumulators of 32 columns
 constexpr uint64_t U_WAIT_NS = 1000000000ull;
 
-// The staged input tile of stride S: per copy (one, or one per column parity
-// with stride 2) [cg][rows][cols][16 bytes].
-// A TMA tensor copy writes to a 128-byte aligned shared-memory address, so
-// each copy starts on a multiple of 128 bytes.
-template <int S>
+// packed weights of a layer with N output rows and 32 input channels
+template <int N>
+struct Wts {
+    static constexpr int bytes = 9 * 4 * N * 16;
+};
+// the first layer: 5 k-steps of two taps, 2 halves of 8 channels, 32 outputs
+constexpr int L0_STEPS = 5;
+constexpr int L0_WBYTES = L0_STEPS * 2 * UC * 16;
+// TMEM columns: two FP32 accumulators of N columns (at least 32 columns)
+template <int N>
+__host__ __device__ constexpr int tmem_cols()
+{
+    return 2 * N < 32 ? 32 : 2 * N;
+}
+
+// The staged input tile of stride S with G channel groups: per copy (one, or
+// one per column parity with stride 2) [cg][rows][cols][16 bytes].  A TMA
+// tensor copy writes to a 128-byte aligned shared-memory address, so each
+// copy starts on a multiple of 128 bytes.
+template <int S, int G = 4>
 struct Halo {
-    static constexpr int rows = S * (UTH - 1) + 3;        // 18 or 33
+    static constexpr int rows = S * (UTH - 1) + 3;           // 18 or 33
     static constexpr int cols = S == 1 ? UTW + 2 : UTW + 1;  // 10, or 9 per parity
-    static constexpr int cg_bytes = rows * cols * 16;     // 2880 or 4752
-    static constexpr int copy_bytes = 4 * cg_bytes;       // what one copy writes
+    static constexpr int cg_bytes = rows * cols * 16;        // 2880 or 4752
+    static constexpr int copy_bytes = G * cg_bytes;          // what one copy writes
     static constexpr int copy_stride = (copy_bytes + 127) / 128 * 128;
-    static constexpr int bytes = S * copy_stride;         // 11520 or 38144
-    static constexpr int sbo = S * cols * 16;             // M-stride: one output row = S halo rows
-    // start of the operand of tap (dy, dx), k-half h, relative to the buffer
-    __host__ __device__ static constexpr int tap_offset(int dy, int dx, int h)
+    static constexpr int bytes = S * copy_stride;
+    static constexpr int sbo = S * cols * 16;                // M-stride: one output row = S halo rows
+    // start of tap (dy, dx) in channel group cg, relative to the buffer
+    __host__ __device__ static constexpr int tap_offset(int dy, int dx, int cg)
     {
-        return (S == 1 ? 0 : (dx & 1) * copy_stride) + 2 * h * cg_bytes + (dy * cols + (S == 1 ? dx : dx >> 1)) * 16;
+        return (S == 1 ? 0 : (dx & 1) * copy_stride) + cg * cg_bytes + (dy * cols + (S == 1 ? dx : dx >> 1)) * 16;
     }
 };
 
 // shared memory: [weights][halo buffers][mbarriers: weights, 2 full, 2 MMA][TMEM
-// address][bias], the halo buffers 128-byte aligned.  Stride 1 keeps two halo buffers (five CTAs per SM); the
-// stride-2 halo is four times larger, so it keeps one and more CTAs instead.
-template <int S>
+// address][bias], the halo buffers 128-byte aligned.
+template <int WB, int HB, int NBUF>
 struct Smem {
-    static constexpr int nbuf = S == 1 ? 2 : 1;
+    static constexpr int nbuf = NBUF;
     static constexpr int w = 0;
-    static constexpr int halo = UW_BYTES;
-    static constexpr int bars = halo + nbuf * Halo<S>::bytes;  // 8-byte aligned (multiples of 16 above)
+    static constexpr int halo = (WB + 127) / 128 * 128;
+    static constexpr int bars = halo + nbuf * HB;  // 8-byte aligned
     static constexpr int taddr = bars + 5 * 8;
     static constexpr int bias = taddr + 8;
     static constexpr int bytes = bias + UC * 4;
-    static_assert(halo % 128 == 0 && Halo<S>::bytes % 128 == 0 && Halo<S>::copy_stride % 128 == 0,
-                  "TMA destinations must be 128-byte aligned");
+    static_assert(halo % 128 == 0 && HB % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
+// the 32-channel (and last) layers' forward: stride 1 keeps two halo buffers,
+// the stride-2 halo is four times larger, so it keeps one and more CTAs
+template <int S, int N>
+using FwdSmem = Smem<Wts<N>::bytes, Halo<S>::bytes, S == 1 ? 2 : 1>;
+using DgradSmem = Smem<Wts<UC>::bytes, Halo<1>::bytes, 2>;
+using L0Smem = Smem<L0_WBYTES, Halo<2, 1>::bytes, 2>;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -147,18 +173,23 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
-// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t U_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UC >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor of kind::f16 for M = 128 and N: FP32 accumulator
+// (bits 4-5 = 1), BF16 A and B (bits 7-9 and 10-12 = 1), both K-major (bits
+// 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int N>
+__device__ __forceinline__ constexpr uint32_t idesc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+}
 
+template <int N>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(U_IDESC), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc<N>()), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar)
@@ -170,21 +201,32 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// N consecutive FP32 columns (16 or 32) of this thread's TMEM lane.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N])
 {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+    uint32_t r[N];
+    if constexpr (N == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        static_assert(N == 16, "16 or 32 columns");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < N; i++) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
@@ -193,24 +235,49 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
-// W[o][c][dy][dx] (FP32) -> [tap][cg][o][8 channels] (BF16).  DGRAD: the data
-// gradient of a stride-1 layer as a forward convolution of the output
-// gradient with K'[c][o][tap] = W[o][c][8 - tap] (output channel c, reduction
-// channel o).
-template <bool DGRAD>
-__global__ void k_pack_w32_umma(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
+// W[o][c][dy][dx] (FP32, O output and 32 input channels) -> [tap][cg][n][8
+// channels] (BF16), n < N, rows n >= O zero.  DGRAD: the data gradient of a
+// stride-1 32 -> 32 layer as a forward convolution of the output gradient
+// with K'[c][o][tap] = W[o][c][8 - tap] (output channel c, reduction channel o).
+template <bool DGRAD, int N, int O>
+__global__ void k_pack_umma(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one pair of reduction channels
-    if (i >= UW_BYTES / 4) return;
-    const int jp = i & 3, n = (i >> 2) & 31, cg = (i >> 7) & 3, tap = i >> 9;
+    if (i >= Wts<N>::bytes / 4) return;
+    const int jp = i & 3, n = (i >> 2) % N, r = (i >> 2) / N, cg = r & 3, tap = r >> 2;
     const int k0 = 8 * cg + 2 * jp;  // reduction channel of the low half
-    float lo, hi;
+    float lo = 0.f, hi = 0.f;
     if (DGRAD) {
         lo = theta[((int64_t)k0 * UC + n) * 9 + (8 - tap)];
         hi = theta[((int64_t)(k0 + 1) * UC + n) * 9 + (8 - tap)];
-    } else {
+    } else if (n < O) {
         lo = theta[((int64_t)n * UC + k0) * 9 + tap];
         hi = theta[((int64_t)n * UC + k0 + 1) * 9 + tap];
+    }
+    wpack[i] = pack2(lo, hi);
+}
+
+// The first layer's taps in k-step order: step j takes taps l0_tap(j, 0) and
+// l0_tap(j, 1) (-1: zero weights), chosen so that the second one lies at a
+// higher address of the stride-2 halo (the K-stride is unsigned).
+__host__ __device__ constexpr int l0_tap(int j, int h)
+{
+    // (dy, dx) = (0,0)+(0,2), (1,0)+(1,2), (2,0)+(2,2), (0,1)+(1,1), (2,1)
+    return j < 3 ? 3 * j + 2 * h : (j == 3 ? 1 + 3 * h : (h == 0 ? 7 : -1));
+}
+
+// W[o][c][dy][dx] of the first layer (32 x 2 x 3 x 3) -> [step][half][o][8
+// channels] (BF16), channels 2..7 and the missing tap zero.
+__global__ void k_pack_l0(const float *__restrict__ theta, uint32_t *__restrict__ wpack)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L0_WBYTES / 4) return;
+    const int jp = i & 3, o = (i >> 2) & 31, h = (i >> 7) & 1, j = i >> 8;
+    const int tap = l0_tap(j, h);
+    float lo = 0.f, hi = 0.f;
+    if (tap >= 0 && jp == 0) {
+        lo = theta[(o * 2 + 0) * 9 + tap];
+        hi = theta[(o * 2 + 1) * 9 + tap];
     }
     wpack[i] = pack2(lo, hi);
 }
@@ -240,30 +307,47 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// The 18 MMAs of one tile: halo buffer at hbase, accumulator at d.
-template <int S>
+// The 18 MMAs of one tile of a 32-input-channel layer: halo buffer at hbase,
+// accumulator at d.
+template <int S, int N>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t d)
 {
     using HL = Halo<S>;
 #pragma unroll
     for (int ks = 0; ks < 18; ks++) {
         const int tap = ks >> 1, h = ks & 1, dy = tap / 3, dx = tap - 3 * dy;
-        umma_bf16(d, sdesc(hbase + HL::tap_offset(dy, dx, h), HL::cg_bytes, HL::sbo),
-                  sdesc(wbase + (4 * tap + 2 * h) * 512, 512, 128), ks > 0);
+        umma_bf16<N>(d, sdesc(hbase + HL::tap_offset(dy, dx, 2 * h), HL::cg_bytes, HL::sbo),
+                     sdesc(wbase + (4 * tap + 2 * h) * N * 16, N * 16, 128), ks > 0);
     }
 }
 
-// Common setup: TMEM columns, mbarriers, bias, and the weights' bulk copy.
-template <int S>
-__device__ __forceinline__ uint32_t umma_setup(uint8_t *smem, const float *bias_g, const uint32_t *wpack)
+// The 5 MMAs of one tile of the first layer (two taps a k-step).
+__device__ __forceinline__ void issue_l0_mmas(uint32_t hbase, uint32_t wbase, uint32_t d)
 {
-    using SM = Smem<S>;
+    using HL = Halo<2, 1>;
+#pragma unroll
+    for (int j = 0; j < L0_STEPS; j++) {
+        const int t0 = l0_tap(j, 0), t1 = l0_tap(j, 1);
+        const int a0 = HL::tap_offset(t0 / 3, t0 % 3, 0);
+        // the second tap's core matrices; the missing one reads the next column
+        // (in bounds) against zero weights
+        const int a1 = t1 >= 0 ? HL::tap_offset(t1 / 3, t1 % 3, 0) : a0 + 16;
+        umma_bf16<UC>(d, sdesc(hbase + a0, a1 - a0, HL::sbo), sdesc(wbase + j * 2 * UC * 16, UC * 16, 128), j > 0);
+    }
+}
+
+// Common setup: TMEM columns, mbarriers, bias (nb entries), and the weights'
+// bulk copy (wbytes, a multiple of 32).
+template <class SM, int COLS>
+__device__ __forceinline__ uint32_t umma_setup(uint8_t *smem, const float *bias_g, int nb, const uint32_t *wpack,
+                                               int wbytes)
+{
     const int tid = threadIdx.x;
     const uint32_t s_base = smem_u32(smem);
     const uint32_t bar_w = s_base + SM::bars;
     if ((tid >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + SM::taddr),
-                     "r"(U_TMEM_COLS)
+                     "r"(COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -272,31 +356,31 @@ __device__ __forceinline__ uint32_t umma_setup(uint8_t *smem, const float *bias_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     float *bias = reinterpret_cast<float *>(smem + SM::bias);
-    if (tid < UC) bias[tid] = bias_g ? bias_g[tid] : 0.f;
+    if (tid < UC) bias[tid] = (bias_g && tid < nb) ? bias_g[tid] : 0.f;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
-        mbar_expect_tx(bar_w, UW_BYTES);
+        mbar_expect_tx(bar_w, wbytes);
 #pragma unroll
         for (int h = 0; h < 2; h++)
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    s_base + SM::w + h * (UW_BYTES / 2)),
-                "l"(reinterpret_cast<const uint8_t *>(wpack) + h * (UW_BYTES / 2)), "r"(UW_BYTES / 2), "r"(bar_w)
+                    s_base + SM::w + h * (wbytes / 2)),
+                "l"(reinterpret_cast<const uint8_t *>(wpack) + h * (wbytes / 2)), "r"(wbytes / 2), "r"(bar_w)
                 : "memory");
     }
     return *reinterpret_cast<volatile uint32_t *>(smem + SM::taddr);
 }
 
+template <int COLS>
 __device__ __forceinline__ void umma_teardown(uint32_t tmem)
 {
     tc_fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(U_TMEM_COLS)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
     }
 }
 
@@ -309,17 +393,46 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_x, int tiles_y, 
     tx = r - ty * tiles_x;
 }
 
-// Forward of one layer: input by TMA from the planar BF16 activations (tensor
-// map tin), output bias + ReLU as planar BF16 (OUT_F32 false) or FP32 NCHW.
-template <int S, bool OUT_F32>
-__global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__ CUtensorMap tin,
-                                                         const float *__restrict__ bias_g,
-                                                         const uint32_t *__restrict__ wpack, void *__restrict__ out,
-                                                         int Ho, int tiles_x, int tiles_y, int n_tiles,
-                                                         int *__restrict__ err)
+// The epilogue's store of one output pixel's NR channels v (bias added): as
+// planar BF16 (32 channels) after ReLU, or FP32 NCHW (ReLU if RELU).
+template <int NR, bool RELU, bool OUT_F32>
+__device__ __forceinline__ void store_pixel(void *out, float *v, const float *bias, int b, int Ho, int oy, int ox)
+{
+#pragma unroll
+    for (int o = 0; o < NR; o++) {
+        v[o] += bias[o];
+        if (RELU) v[o] = fmaxf(v[o], 0.f);
+    }
+    if (OUT_F32) {
+        float *o32 = reinterpret_cast<float *>(out);
+        const int64_t o0 = ((int64_t)b * NR * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
+#pragma unroll
+        for (int o = 0; o < NR; o++) o32[o0 + o * plane] = v[o];
+    } else {
+        static_assert(OUT_F32 || NR == UC, "planar output has 32 channels");
+        uint4 *o16 = reinterpret_cast<uint4 *>(out);
+#pragma unroll
+        for (int cg = 0; cg < NR / 8; cg++) {
+            const float *q = v + 8 * cg;
+            o16[((int64_t)(4 * b + cg) * Ho + oy) * Ho + ox] =
+                make_uint4(pack2(q[0], q[1]), pack2(q[2], q[3]), pack2(q[4], q[5]), pack2(q[6], q[7]));
+        }
+    }
+}
+
+// Forward of a layer with 32 input channels: input by TMA from the planar
+// BF16 activations (tensor map tin), N output rows of which NR are written
+// (bias, ReLU if RELU) as planar BF16 or FP32 NCHW.
+template <int S, int N, int NR, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(128) k_conv_umma_fwd(const __grid_constant__ CUtensorMap tin,
+                                                       const float *__restrict__ bias_g,
+                                                       const uint32_t *__restrict__ wpack, void *__restrict__ out,
+                                                       int Ho, int tiles_x, int tiles_y, int n_tiles,
+                                                       int *__restrict__ err)
 {
     using HL = Halo<S>;
-    using SM = Smem<S>;
+    using SM = FwdSmem<S, N>;
+    constexpr int COLS = tmem_cols<N>();
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_base = smem_u32(smem);
@@ -328,8 +441,8 @@ __global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__
         return;
     }
     const uint32_t bar_w = s_base + SM::bars, bar_full = bar_w + 8, bar_mma = bar_w + 24;
-    const float *bias = reinterpret_cast<const float *>(smem + SM::bias);
-    const uint32_t tmem = umma_setup<S>(smem, bias_g, wpack);
+    float *bias = reinterpret_cast<float *>(smem + SM::bias);
+    const uint32_t tmem = umma_setup<SM, COLS>(smem, bias_g, NR, wpack, Wts<N>::bytes);
 
     // TMA copy of a tile's halo into buffer hb (thread 0)
     auto load_tile = [&](int tile, int hb) {
@@ -356,8 +469,8 @@ __global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__
     int it = 0, prev = -1;
     for (int tile = blockIdx.x;; tile += gridDim.x, ++it) {
         const bool have = tile < n_tiles;
-        const int buf = it & 1;                       // accumulator and MMA barrier of this tile
-        const int hb = SM::nbuf == 2 ? buf : 0;       // halo buffer
+        const int buf = it & 1;                         // accumulator and MMA barrier of this tile
+        const int hb = SM::nbuf == 2 ? buf : 0;         // halo buffer
         const int huse = SM::nbuf == 2 ? it >> 1 : it;  // its use count
         // the accumulator is free: its last reader, the epilogue two tiles
         // back, finished before this barrier
@@ -367,7 +480,7 @@ __global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__
             bool ok = (it > 0 || mbar_wait(bar_w, 0)) && mbar_wait(bar_full + 8 * hb, huse & 1);
             if (ok) {
                 tc_fence_after();
-                issue_tile_mmas<S>(s_base + SM::halo + hb * HL::bytes, s_base + SM::w, tmem + buf * UC);
+                issue_tile_mmas<S, N>(s_base + SM::halo + hb * HL::bytes, s_base + SM::w, tmem + buf * N);
             }
             umma_commit(bar_mma + 8 * buf);
             const int next = tile + gridDim.x;
@@ -391,29 +504,12 @@ __global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__
             bad = __syncthreads_or(!ok || bad || fail);
             if (!bad) {
                 tc_fence_after();
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
+                float v[N];
+                tmem_ld<N>(tmem + ((uint32_t)(32 * warp) << 16) + pb * N, v);
                 int b, ty, tx;
                 tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
                 const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
-                if (oy < Ho && ox < Ho) {
-#pragma unroll
-                    for (int o = 0; o < UC; o++) v[o] = fmaxf(v[o] + bias[o], 0.f);
-                    if (OUT_F32) {
-                        float *o32 = reinterpret_cast<float *>(out);
-                        const int64_t o0 = ((int64_t)b * UC * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
-#pragma unroll
-                        for (int o = 0; o < UC; o++) o32[o0 + o * plane] = v[o];
-                    } else {
-                        uint4 *o16 = reinterpret_cast<uint4 *>(out);
-#pragma unroll
-                        for (int cg = 0; cg < 4; cg++) {
-                            const float *q = v + 8 * cg;
-                            o16[((int64_t)(4 * b + cg) * Ho + oy) * Ho + ox] =
-                                make_uint4(pack2(q[0], q[1]), pack2(q[2], q[3]), pack2(q[4], q[5]), pack2(q[6], q[7]));
-                        }
-                    }
-                }
+                if (oy < Ho && ox < Ho) store_pixel<NR, RELU, OUT_F32>(out, v, bias, b, Ho, oy, ox);
             }
         } else if (have) {
             bad = __syncthreads_or(bad || fail);
@@ -421,7 +517,7 @@ __global__ void __launch_bounds__(128) k_conv32_umma_fwd(const __grid_constant__
         if (!have || bad) break;
         prev = tile;
     }
-    umma_teardown(tmem);
+    umma_teardown<COLS>(tmem);
 }
 
 // Positive entries of a planar BF16 activation: 32 bits, one per channel.
@@ -442,47 +538,69 @@ __device__ __forceinline__ uint32_t positive_mask(const uint4 *act, int b, int H
     return m;
 }
 
-// Data gradient of a stride-1 layer: gz (FP32 NCHW, the gradient with respect
-// to the layer's pre-activation output) staged and rounded to BF16 by the
-// CTA's threads; gx (FP32 NCHW) = the GEMM with flipped, transposed weights,
-// where the planar BF16 activation below (mask) is positive, else 0.
-__global__ void __launch_bounds__(128) k_conv32_umma_dgrad(const float *__restrict__ gz, int H,
-                                                           const uint32_t *__restrict__ wpack,
-                                                           const uint4 *__restrict__ mask, float *__restrict__ gx,
-                                                           int tiles_x, int tiles_y, int n_tiles,
-                                                           int *__restrict__ err)
+// Kernels whose tiles the CTA's threads stage from FP32 NCHW input, rounded
+// to BF16 (the previous tile's MMAs waited on in the last epilogue):
+//   L0 false: the data gradient of a stride-1 32 -> 32 layer, gz (the
+//     gradient with respect to the layer's pre-activation output) in, gx =
+//     the GEMM with flipped and transposed weights where the planar BF16
+//     activation below (mask) is positive, else 0;
+//   L0 true: the first layer's forward (2 input channels, stride 2, padded to
+//     one group of 8), bias + ReLU out as planar BF16.
+template <bool L0>
+__global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restrict__ in, int H,
+                                                          const uint32_t *__restrict__ wpack,
+                                                          const float *__restrict__ bias_g,
+                                                          const uint4 *__restrict__ mask, void *__restrict__ out,
+                                                          int Ho, int tiles_x, int tiles_y, int n_tiles,
+                                                          int *__restrict__ err)
 {
-    using HL = Halo<1>;
-    using SM = Smem<1>;
+    constexpr int S = L0 ? 2 : 1, G = L0 ? 1 : 4;
+    using HL = Halo<S, G>;
+    using SM = std::conditional_t<L0, L0Smem, DgradSmem>;
+    constexpr int COLS = tmem_cols<UC>();
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_base = smem_u32(smem);
     const uint32_t bar_w = s_base + SM::bars, bar_mma = bar_w + 24;
-    const uint32_t tmem = umma_setup<1>(smem, nullptr, wpack);
+    const float *bias = reinterpret_cast<const float *>(smem + SM::bias);
+    const uint32_t tmem = umma_setup<SM, COLS>(smem, L0 ? bias_g : nullptr, UC, wpack, L0 ? L0_WBYTES : Wts<UC>::bytes);
     int bad = 0;
     int it = 0, prev = -1;
     for (int tile = blockIdx.x;; tile += gridDim.x, ++it) {
         const bool have = tile < n_tiles;
         const int buf = it & 1;
         if (have) {
-            // stage the tile with its halo into halo[buf] (the MMAs that last
-            // read it completed: waited on in the last iteration's epilogue)
             int b, ty, tx;
             tile_coords(tile, tiles_x, tiles_y, b, ty, tx);
-            const int iy0 = UTH * ty - 1, ix0 = UTW * tx - 1;
+            const int iy0 = S * UTH * ty - 1, ix0 = S * UTW * tx - 1;
             uint8_t *hbuf = smem + SM::halo + buf * HL::bytes;
-            const float *img = gz + (int64_t)b * UC * H * H;
+            constexpr int C = L0 ? 2 : UC;
+            const float *img = in + (int64_t)b * C * H * H;
             const int64_t plane = (int64_t)H * H;
-            for (int i = tid; i < 4 * HL::rows * HL::cols; i += 128) {
-                const int ix = i % HL::cols, r3 = i / HL::cols, iy = r3 % HL::rows, cg = r3 / HL::rows;
-                const int gy = iy0 + iy, gxx = ix0 + ix;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (gy >= 0 && gy < H && gxx >= 0 && gxx < H) {
-                    const float *p = img + (int64_t)(8 * cg) * plane + (int64_t)gy * H + gxx;
-                    v = make_uint4(pack2(p[0], p[plane]), pack2(p[2 * plane], p[3 * plane]),
-                                   pack2(p[4 * plane], p[5 * plane]), pack2(p[6 * plane], p[7 * plane]));
+            if (L0) {
+                // halo columns ix0 + 2 j (copy 0) and ix0 + 1 + 2 j (copy 1), j < 9
+                for (int i = tid; i < 2 * HL::rows * HL::cols; i += 128) {
+                    const int j = i % HL::cols, r3 = i / HL::cols, iy = r3 % HL::rows, par = r3 / HL::rows;
+                    const int gy = iy0 + iy, gxx = ix0 + par + 2 * j;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (gy >= 0 && gy < H && gxx >= 0 && gxx < H) {
+                        const float *p = img + (int64_t)gy * H + gxx;
+                        v.x = pack2(p[0], p[plane]);
+                    }
+                    *reinterpret_cast<uint4 *>(hbuf + par * HL::copy_stride + (iy * HL::cols + j) * 16) = v;
                 }
-                *reinterpret_cast<uint4 *>(hbuf + cg * HL::cg_bytes + (iy * HL::cols + ix) * 16) = v;
+            } else {
+                for (int i = tid; i < 4 * HL::rows * HL::cols; i += 128) {
+                    const int ix = i % HL::cols, r3 = i / HL::cols, iy = r3 % HL::rows, cg = r3 / HL::rows;
+                    const int gy = iy0 + iy, gxx = ix0 + ix;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (gy >= 0 && gy < H && gxx >= 0 && gxx < H) {
+                        const float *p = img + (int64_t)(8 * cg) * plane + (int64_t)gy * H + gxx;
+                        v = make_uint4(pack2(p[0], p[plane]), pack2(p[2 * plane], p[3 * plane]),
+                                       pack2(p[4 * plane], p[5 * plane]), pack2(p[6 * plane], p[7 * plane]));
+                    }
+                    *reinterpret_cast<uint4 *>(hbuf + cg * HL::cg_bytes + (iy * HL::cols + ix) * 16) = v;
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
@@ -490,8 +608,13 @@ __global__ void __launch_bounds__(128) k_conv32_umma_dgrad(const float *__restri
         __syncthreads();
         if (have && tid == 0 && !bad) {
             tc_fence_after();
-            if (it == 0 && !mbar_wait(bar_w, 0)) *reinterpret_cast<volatile int *>(err) = 1;
-            else issue_tile_mmas<1>(s_base + SM::halo + buf * HL::bytes, s_base + SM::w, tmem + buf * UC);
+            if (it == 0 && !mbar_wait(bar_w, 0)) {
+                *reinterpret_cast<volatile int *>(err) = 1;
+            } else {
+                const uint32_t hbase = s_base + SM::halo + buf * HL::bytes;
+                if (L0) issue_l0_mmas(hbase, s_base + SM::w, tmem + buf * UC);
+                else issue_tile_mmas<1, UC>(hbase, s_base + SM::w, tmem + buf * UC);
+            }
             umma_commit(bar_mma + 8 * buf);
         }
         if (prev >= 0) {
@@ -501,23 +624,28 @@ __global__ void __launch_bounds__(128) k_conv32_umma_dgrad(const float *__restri
             bad = __syncthreads_or(!ok || bad);
             if (!bad) {
                 tc_fence_after();
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
+                float v[UC];
+                tmem_ld<UC>(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
                 int b, ty, tx;
                 tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
                 const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
-                if (oy < H && ox < H) {
-                    const uint32_t pm = positive_mask(mask, b, H, oy, ox);
-                    const int64_t o0 = ((int64_t)b * UC * H + oy) * H + ox, plane = (int64_t)H * H;
+                if (oy < Ho && ox < Ho) {
+                    if (L0) {
+                        store_pixel<UC, true, false>(out, v, bias, b, Ho, oy, ox);
+                    } else {
+                        float *gx = reinterpret_cast<float *>(out);
+                        const uint32_t pm = positive_mask(mask, b, Ho, oy, ox);
+                        const int64_t o0 = ((int64_t)b * UC * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
 #pragma unroll
-                    for (int o = 0; o < UC; o++) gx[o0 + o * plane] = ((pm >> o) & 1u) ? v[o] : 0.f;
+                        for (int o = 0; o < UC; o++) gx[o0 + o * plane] = ((pm >> o) & 1u) ? v[o] : 0.f;
+                    }
                 }
             }
         }
         if (!have || bad) break;
         prev = tile;
     }
-    umma_teardown(tmem);
+    umma_teardown<COLS>(tmem);
 }
 
 // cuTensorMapEncodeTiled from the driver, found once.
@@ -566,10 +694,10 @@ bool encode_input_map(CUtensorMap *map, const void *act, int H, int B, int S)
 }
 
 // Launch shape: one CTA per tile up to the resident CTAs of every SM (by
-// shared memory, at most 8: 8 x 64 TMEM columns fill the 512 columns of an
-// SM, so an allocation never waits on another CTA).
+// shared memory, and at most 512 / cols so that the TMEM allocations of the
+// resident CTAs fit the SM's 512 columns and never wait on one another).
 template <typename K>
-bool grid_for(K kern, int bytes, int n_tiles, int &grid)
+bool grid_for(K kern, int bytes, int cols, int n_tiles, int &grid)
 {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
@@ -581,56 +709,83 @@ bool grid_for(K kern, int bytes, int n_tiles, int &grid)
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
         return false;
-    const int per_sm = std::max(1, std::min(512 / U_TMEM_COLS, smem_sm / (bytes + smem_rsv)));
+    const int per_sm = std::max(1, std::min(std::min(512 / cols, 16), smem_sm / (bytes + smem_rsv)));
     grid = std::min(n_tiles, nsm * per_sm);
     return true;
 }
 
-template <int S, bool OUT_F32>
+template <int S, int N, int NR, bool RELU, bool OUT_F32>
 reg_status launch_fwd(const uint16_t *in, int H, const float *theta, void *out, int B, cudaStream_t st,
-                      uint32_t *wpack, int *err)
+                      uint32_t *wpack, bool pack, int *err)
 {
     CUtensorMap map;
     if (!encode_input_map(&map, in, H, B, S))
         return reg_internal_fail(REG_ECUDA, "tcgen05 convolution: tensor map of the input");
-    k_pack_w32_umma<false><<<(UW_BYTES / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    if (pack) k_pack_umma<false, N, NR><<<(Wts<N>::bytes / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
     const int Ho = (H + 2 - 3) / S + 1;
     const int tx = (Ho + UTW - 1) / UTW, ty = (Ho + UTH - 1) / UTH, nt = B * tx * ty;
-    auto kern = k_conv32_umma_fwd<S, OUT_F32>;
+    auto kern = k_conv_umma_fwd<S, N, NR, RELU, OUT_F32>;
+    constexpr int bytes = FwdSmem<S, N>::bytes;
     int grid = 0;
-    if (!grid_for(kern, Smem<S>::bytes, nt, grid))
+    if (!grid_for(kern, bytes, tmem_cols<N>(), nt, grid))
         return reg_internal_fail(REG_ECUDA, "tcgen05 convolution: launch attributes");
-    kern<<<grid, 128, Smem<S>::bytes, st>>>(map, theta + UC * UC * 9, wpack, out, Ho, tx, ty, nt, err);
+    kern<<<grid, 128, bytes, st>>>(map, theta + NR * UC * 9, wpack, out, Ho, tx, ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 convolution launch");
     return REG_OK;
 }
 
 }  // namespace
 
-int cnn_conv32_umma_words() { return UW_BYTES / 4; }
+int cnn_conv32_umma_words() { return Wts<UC>::bytes / 4; }
 
 reg_status cnn_conv32_umma(const uint16_t *in, int H, const float *theta, void *out, bool out_f32, int B, int S,
-                           cudaStream_t st, uint32_t *wpack, int *err)
+                           cudaStream_t st, uint32_t *wpack, bool pack, int *err)
 {
     if (S == 1)
-        return out_f32 ? launch_fwd<1, true>(in, H, theta, out, B, st, wpack, err)
-                       : launch_fwd<1, false>(in, H, theta, out, B, st, wpack, err);
+        return out_f32 ? launch_fwd<1, UC, UC, true, true>(in, H, theta, out, B, st, wpack, pack, err)
+                       : launch_fwd<1, UC, UC, true, false>(in, H, theta, out, B, st, wpack, pack, err);
     if (S == 2)
-        return out_f32 ? launch_fwd<2, true>(in, H, theta, out, B, st, wpack, err)
-                       : launch_fwd<2, false>(in, H, theta, out, B, st, wpack, err);
+        return out_f32 ? launch_fwd<2, UC, UC, true, true>(in, H, theta, out, B, st, wpack, pack, err)
+                       : launch_fwd<2, UC, UC, true, false>(in, H, theta, out, B, st, wpack, pack, err);
     return reg_internal_fail(REG_EINVAL, "tcgen05 convolution: stride must be 1 or 2");
 }
 
-reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
-                            cudaStream_t st, uint32_t *wpack, int *err)
+reg_status cnn_last_umma(const uint16_t *in, int H, const float *theta, float *out, int B, cudaStream_t st,
+                         uint32_t *wpack, bool pack, int *err)
 {
-    k_pack_w32_umma<true><<<(UW_BYTES / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    return launch_fwd<1, 16, 2, false, true>(in, H, theta, out, B, st, wpack, pack, err);
+}
+
+reg_status cnn_first_umma(const float *x, int H, const float *theta, uint16_t *out, int B, cudaStream_t st,
+                          uint32_t *wpack, bool pack, int *err)
+{
+    if (H % 2) return reg_internal_fail(REG_EINVAL, "tcgen05 first layer: odd input side");
+    if (pack) k_pack_l0<<<(L0_WBYTES / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    const int Ho = (H + 2 - 3) / 2 + 1;
+    const int tx = (Ho + UTW - 1) / UTW, ty = (Ho + UTH - 1) / UTH, nt = B * tx * ty;
+    int grid = 0;
+    if (!grid_for(k_conv_umma_staged<true>, L0Smem::bytes, tmem_cols<UC>(), nt, grid))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 first layer: launch attributes");
+    k_conv_umma_staged<true><<<grid, 128, L0Smem::bytes, st>>>(x, H, wpack, theta + UC * 2 * 9, nullptr, out, Ho, tx,
+                                                               ty, nt, err);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 first layer launch");
+    return REG_OK;
+}
+
+reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
+                            cudaStream_t st, uint32_t *wpack, bool pack, int *err)
+{
+    if (pack) k_pack_umma<true, UC, UC><<<(Wts<UC>::bytes / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
     const int tx = (H + UTW - 1) / UTW, ty = (H + UTH - 1) / UTH, nt = B * tx * ty;
     int grid = 0;
-    if (!grid_for(k_conv32_umma_dgrad, Smem<1>::bytes, nt, grid))
+    if (!grid_for(k_conv_umma_staged<false>, DgradSmem::bytes, tmem_cols<UC>(), nt, grid))
         return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient: launch attributes");
-    k_conv32_umma_dgrad<<<grid, 128, Smem<1>::bytes, st>>>(gz, H, wpack, reinterpret_cast<const uint4 *>(mask), gx,
-                                                            tx, ty, nt, err);
+    k_conv_umma_staged<false><<<grid, 128, DgradSmem::bytes, st>>>(gz, H, wpack, nullptr,
+                                                                   reinterpret_cast<const uint4 *>(mask), gx, H, tx,
+                                                                   ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient launch");
     return REG_OK;
 }
+
+int cnn_last_umma_words() { return Wts<16>::bytes / 4; }
+int cnn_first_umma_words() { return L0_WBYTES / 4; }

@@ -7,6 +7,13 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
+# the tensor-core forward takes BF16 operands in all six layers; its training
+# pass also in the data gradients of the stride-1 32-channel layers and the
+# weight gradients of the 32-channel layers, and the last layer's weight
+# gradient takes its BF16-stored input
+TC_LAYERS = (0, 1, 2, 3, 4, 5)
+TC_TRAIN = dict(bf16_layers=TC_LAYERS, bf16_data=(2, 3, 4), bf16_weights=(1, 2, 3, 4), bf16_stored=(5,))
+
 
 @pytest.fixture(scope="module")
 def reg():
@@ -63,7 +70,7 @@ def test_tensor_core_forward_matches_the_bf16_operand_oracle(reg, side, batch):
         y_f32 = net.forward(xd).cpu().numpy().astype(np.float64)
     th, x64 = theta.astype(np.float64), x.astype(np.float64)
     y_exact = ocnn.forward(th, x64)
-    y_bf16 = ocnn.forward(th, x64, bf16_layers=(1, 2, 3, 4))
+    y_bf16 = ocnn.forward(th, x64, bf16_layers=TC_LAYERS)
     scale = np.abs(y_exact).max()
     assert np.abs(y_tc - y_bf16).max() <= 2e-3 * scale
     assert np.median(np.abs(y_tc - y_bf16)) <= 1e-5 * scale
@@ -133,7 +140,7 @@ def test_learned_start_matches_the_oracle(reg, orc, syn, tensor_cores):
     fr = syn.series(31, 2, 256, **learned.TRAIN_SERIES)
     theta = synth.cnn_params(7)
     y = ocnn.forward(theta.astype(np.float64), _oracle_inputs(orc, fr),
-                     bf16_layers=(1, 2, 3, 4) if tensor_cores else ())
+                     bf16_layers=TC_LAYERS if tensor_cores else ())
     u0 = ocnn.upsample(y[0], 256)
     p = reg.default_params(n_levels=3, init_levels=2, iter_max=50, lam=10.0, learned_fallback_px=0.0)
     g0, g1 = orc.embed(fr[0]), orc.embed(fr[1])
@@ -240,14 +247,12 @@ def test_tensor_core_training_gradients_match_the_bf16_operand_oracle(reg, side,
         loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), want_grad=True,
                                 tensor_cores=True)
     th, x64, t64 = theta.astype(np.float64), x.astype(np.float64), t.astype(np.float64)
-    lb, gb = ocnn.loss_and_grad(th, x64, t64, bf16_layers=(1, 2, 3, 4), bf16_data=(2, 3, 4),
-                                bf16_weights=(1, 2, 3, 4))
+    lb, gb = ocnn.loss_and_grad(th, x64, t64, **TC_TRAIN)
     le, ge = ocnn.loss_and_grad(th, x64, t64)
     spread = np.zeros_like(gb)
     for seed in (7, 8):
         xp = x64 * (1.0 + 2.0 ** -24 * np.random.default_rng(seed).standard_normal(x.shape))
-        spread = np.maximum(spread, np.abs(ocnn.loss_and_grad(th, xp, t64, bf16_layers=(1, 2, 3, 4),
-                                                              bf16_data=(2, 3, 4), bf16_weights=(1, 2, 3, 4))[1] - gb))
+        spread = np.maximum(spread, np.abs(ocnn.loss_and_grad(th, xp, t64, **TC_TRAIN)[1] - gb))
     assert abs(loss - lb) <= 1e-4 * lb, (loss, lb, le)
     worst_b, worst_e = 0.0, 0.0
     for k, ((gw, gbias), (bw, bb), (ew, eb), (sw, _)) in enumerate(zip(ocnn.unpack(g.astype(np.float64)),

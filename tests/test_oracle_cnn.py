@@ -175,3 +175,29 @@ def test_bf16_operand_gradients_reduce_to_the_exact_ones_on_bf16_values():
     rel = np.abs(g2 - g0).max() / np.abs(g0).max()
     assert 1e-5 < rel < 0.1, rel
     assert abs(l2 - l0) < 0.05 * l0
+
+
+def test_bf16_stored_input_changes_only_that_layers_weight_gradient():
+    """A layer whose input is stored in BF16 (bf16_stored) differs from the
+    exact gradient only in its own weight gradient, and there by no more than
+    the input's rounding allows: each product moves by at most 2^-8 of its
+    size, so gW by at most 2^-8 sum |g| |a|."""
+    from oracle import cnn as ocnn
+    import synth
+    rng = np.random.default_rng(6)
+    theta = synth.cnn_params(3).astype(np.float64)
+    x = rng.standard_normal((2, 2, 32, 32))
+    t = rng.standard_normal((2, 2, 8, 8))
+    l0, g0 = ocnn.loss_and_grad(theta, x, t)
+    l1, g1 = ocnn.loss_and_grad(theta, x, t, bf16_stored=(5,))
+    assert l0 == l1
+    parts0, parts1 = ocnn.unpack(g0), ocnn.unpack(g1)
+    for k in range(5):
+        assert np.array_equal(parts0[k][0], parts1[k][0]) and np.array_equal(parts0[k][1], parts1[k][1]), k
+    assert np.array_equal(parts0[5][1], parts1[5][1])  # bias gradient: the unrounded output gradient
+    y, cache = ocnn.forward(theta, x, keep=True)
+    a = cache[5][0]
+    g = 2.0 * (y - t) / y.size
+    bound = ocnn.conv_backward(np.abs(a), np.abs(ocnn.unpack(theta)[5][0]), 1, np.abs(g))[1] * 2.0 ** -8
+    d = np.abs(parts1[5][0] - parts0[5][0])
+    assert np.all(d <= bound * (1 + 1e-12)) and d.max() > 0
