@@ -56,12 +56,16 @@ def _args():
     return ap.parse_args()
 
 
-# DRAM bytes (read + written) per algorithmic byte of the step kernels from an
-# ncu capture, for the kernel source it was taken on (a hash of kernels.cu);
-# another source reports no traffic.  No ratio is recorded for the current
-# source: the per-launch captures in profiles/ give DRAM bytes per launch, but
-# not the algorithmic bytes of that one launch.
-TRAFFIC_CAPTURE = {"kernels_cu_sha1": None}
+# DRAM traffic per launch, estimated from one ncu capture per kernel (a bulk
+# launch of 16 operators at the finest level, 1025^2 nodes each; the bench's
+# own launches are too many to capture): its dram__bytes_read.sum +
+# dram__bytes_write.sum over its library bytes (the kernel statistics' count:
+# 36 B per node for a trial pass, 60 B for a gradient pass, FP32 images),
+# times a bench launch's library bytes.  Recorded for one kernels.cu source;
+# any other source reports no traffic.
+TRAFFIC_CAPTURE = {"kernels_cu_sha1": "307efa368145ed15508fc77a27ac7763a6ba454e",
+                   "trial": (416.177664 + 4.737536) / (16 * 1025 * 1025 * 36 / 1e6),
+                   "grad": (505.841408 + 340.754688) / (16 * 1025 * 1025 * 60 / 1e6)}
 
 
 def _traffic(family, algo_bytes_per_launch):
@@ -129,8 +133,9 @@ def roofline_of(stats, cfg, bf16=False):
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "bytes_model": "40 B/node per gradient pass + 24 B/node per sequential Armijo trial + 16 B/node per "
                            "level-start pass (FP32 storage)",
-            "traffic": _traffic(dom, dk["bytes"] / launches), "traffic_note": "estimated: committed DRAM/library-byte "
-                       "ratio of an ncu capture times this launch's library bytes (null if the kernel source changed)",
+            "traffic": _traffic(dom, dk["bytes"] / launches), "traffic_note": "estimated: DRAM/library-byte ratio of one ncu "
+                       "capture (a 16-operator launch at the finest level) times this launch's library bytes (null "
+                       "if the kernel source changed)",
             "bytes_per_launch": mb / launches, "library_bytes_per_launch": dk["bytes"] / launches,
             "achieved_library_bytes": round(lib_achieved, 1), "frac_library_bytes": round(lib_achieved / peak, 4),
             "ms_per_launch": dk["ms"] / launches, "sequential_trials_per_trial_pass": round(seq_per_pass, 3),
