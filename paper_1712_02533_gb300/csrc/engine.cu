@@ -1145,7 +1145,10 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
         s->grid_S = s->nsm * 8;
     }
     // Pyramid construction in chunks of frames: raw level L, restriction chain,
-    // per-level FE mean/sigma, normalisation into the stored pyramid.
+    // per-level FE mean/sigma, normalisation into the stored pyramid.  The
+    // staging buffers alternate across the chunks of all series (nc counts
+    // them), so that each copy waits for the kernels that last read its buffer.
+    int nc = 0;
     for (int i = 0; i < n_series; i++) {
         SeriesInfo &si = s->S[i];
         int nL = si.side + 1;
@@ -1165,7 +1168,6 @@ reg_status reg_create_series(const float *frames, int32_t n_series, const int32_
             return cleanup(st);
         size_t stage_bytes = (size_t)chunk * frame_bytes;
         if (!frames_on_device && !staged && (st = dalloc(s, &stage, stage_bytes)) != REG_OK) return cleanup(st);
-        int nc = 0;
         for (int f0 = 0; f0 < si.n_frames; f0 += chunk, nc++) {
             int nf = std::min(chunk, si.n_frames - f0);
             const int b = nc & 1;

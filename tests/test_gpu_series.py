@@ -83,3 +83,24 @@ def test_host_transfers_match_device_transfers(reg, syn):
     assert np.array_equal(u_host, u_dev.cpu().numpy())
     assert np.array_equal(u_host, u_ref.cpu().numpy())
     assert np.abs(u_host[1:]).max() > 0.1  # the frames did move
+
+
+def test_host_upload_of_mixed_series_matches_device_upload(reg, syn):
+    """Several series of different sizes in one handle from host memory: the
+    staging buffers alternate over the chunks of all series, and each copy
+    waits for the kernels that read its buffer last, so every series gives
+    exactly what it gives alone from device memory (each operator's sums are
+    its own, so batching series together changes no result), checked through
+    the deformations of a short scan, which read every level of every frame."""
+    import torch
+    series = [syn.series(31, 18, 256, spacing=8.0, sigma=1.5, peak=20.0, drift_sd=0.5, dist_amp=1.0),
+              syn.series(32, 20, 1024, spacing=16.0, sigma=2.0, peak=10.0, drift_sd=0.5, dist_amp=1.0),
+              syn.series(33, 3, 512, spacing=12.0, sigma=2.0, peak=10.0, drift_sd=0.5, dist_amp=1.0)]
+    p = reg.default_params(n_levels=4, iter_max=2, lam=10.0)
+    with reg.Series(series, p) as s:
+        s.prefix_scan(reg.SKLANSKY)
+        mixed = [s.get_deformations(k) for k in range(len(series))]
+    for f, got in zip(series, mixed):
+        with reg.Series([torch.from_numpy(f).cuda()], p) as s:
+            s.prefix_scan(reg.SKLANSKY)
+            assert np.array_equal(got, s.get_deformations())
