@@ -39,19 +39,19 @@
 //     k-step of 16 takes two taps, whose core matrices the descriptor's
 //     K-stride joins (the ninth tap pairs with zero weights), 5 MMAs a tile.
 //
-// One thread issues the tile's copy and MMAs, committed to an mbarrier; each
-// warp then reads its 32 TMEM lanes (= tile rows 32 w .. 32 w + 31) with
-// tcgen05.ld and writes the result: bias + ReLU as planar BF16, or FP32 NCHW
-// (the 32-channel layer before the last, for its data gradient's mask and the
-// last layer, and the last layer's two channels).  CTAs loop over tiles with
-// two accumulators, so that the MMAs of a tile run while the previous one is
-// written, and (stride 1) two halo buffers, so that the next tile's copy is
-// in flight meanwhile too.  The data gradient of a stride-1 layer runs the
-// same GEMM on the output gradient (FP32 NCHW, staged and rounded by the
-// CTA's threads) with flipped and transposed weights, times the ReLU mask of
-// the layer below.  Every wait on an mbarrier is bounded (one second of the
-// global timer); a wait that runs out sets the error word, the CTA stops
-// issuing work, frees its TMEM and returns.
+// The TMA-fed layers split each CTA into a copy warp, an MMA warp and four
+// epilogue warps that hand tiles on through mbarriers (NS halo stages, two
+// TMEM accumulators); each epilogue warp reads its 32 TMEM lanes (= tile rows
+// 32 w .. 32 w + 31) with tcgen05.ld and writes bias + ReLU as planar BF16, or
+// the last layer's two channels as FP32 NCHW.  The kernels whose threads stage
+// their tiles (the first layer; the data gradient of a stride-1 layer, which
+// runs the same GEMM on the output gradient, FP32 NCHW, with flipped and
+// transposed weights, times the ReLU mask of the layer below) keep one thread
+// issuing the MMAs, two halo buffers and two accumulators, so that a tile's
+// MMAs run while the next is staged and the previous one is written.  Every
+// wait on an mbarrier is bounded (one second of the global timer); a wait that
+// runs out sets the error word, the CTA stops issuing work, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -116,12 +116,26 @@ struct Smem {
     static constexpr int bytes = bias + UC * 4;
     static_assert(halo % 128 == 0 && HB % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
-// the 32-channel (and last) layers' forward: stride 1 keeps two halo buffers,
-// the stride-2 halo is four times larger, so it keeps one and more CTAs
-template <int S, int N>
-using FwdSmem = Smem<Wts<N>::bytes, Halo<S>::bytes, S == 1 ? 2 : 1>;
 using DgradSmem = Smem<Wts<UC>::bytes, Halo<1>::bytes, 2>;
 using L0Smem = Smem<L0_WBYTES, Halo<2, 1>::bytes, 2>;
+
+// The warp-specialised forward: [weights][NS halo stages][mbarriers: weights,
+// full[NS], empty[NS], accumulator full[2], accumulator empty[2]][TMEM
+// address][abort flag][bias].  Stride 1 keeps four stages (three CTAs per
+// SM), stride 2 two.
+template <int S, int N>
+struct WsSmem {
+    static constexpr int ns = S == 1 ? 4 : 2;
+    static constexpr int w = 0;
+    static constexpr int halo = (Wts<N>::bytes + 127) / 128 * 128;
+    static constexpr int bars = halo + ns * Halo<S>::bytes;
+    static constexpr int nbars = 1 + 2 * ns + 4;
+    static constexpr int taddr = bars + nbars * 8;
+    static constexpr int abort = taddr + 4;
+    static constexpr int bias = taddr + 8;
+    static constexpr int bytes = bias + UC * 4;
+    static_assert(halo % 128 == 0 && Halo<S>::bytes % 128 == 0, "TMA destinations must be 128-byte aligned");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -161,6 +175,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
         if (global_ns() - t0 > U_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// mbar_wait that also gives up when another role of the CTA set the abort flag.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag || global_ns() - t0 > U_WAIT_NS) return false;
+    }
     return true;
 }
 
@@ -422,17 +452,25 @@ __device__ __forceinline__ void store_pixel(void *out, float *v, const float *bi
 
 // Forward of a layer with 32 input channels: input by TMA from the planar
 // BF16 activations (tensor map tin), N output rows of which NR are written
-// (bias, ReLU if RELU) as planar BF16 or FP32 NCHW.
+// (bias, ReLU if RELU) as planar BF16 or FP32 NCHW.  The CTA's roles are split
+// over six warps, each waiting on its own mbarriers: warp 4 (one lane) issues
+// the weights' bulk copy and the tiles' TMA copies into NS stages, warp 5 (one
+// lane) issues each tile's 18 MMAs into one of two TMEM accumulators once its
+// stage is full and the accumulator has been read, and commits them to the
+// stage's "empty" and the accumulator's "full" barriers; warps 0..3 read the
+// accumulator (their 32 TMEM lanes each), hand it back (one arrival per warp)
+// and store the tile.  A wait that runs out (one second) or sees another
+// role's abort sets the error word and the abort flag and ends that role.
 template <int S, int N, int NR, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(128) k_conv_umma_fwd(const __grid_constant__ CUtensorMap tin,
-                                                       const float *__restrict__ bias_g,
-                                                       const uint32_t *__restrict__ wpack, void *__restrict__ out,
-                                                       int Ho, int tiles_x, int tiles_y, int n_tiles,
-                                                       int *__restrict__ err)
+__global__ void __launch_bounds__(192) k_conv_umma_ws(const __grid_constant__ CUtensorMap tin,
+                                                      const float *__restrict__ bias_g,
+                                                      const uint32_t *__restrict__ wpack, void *__restrict__ out,
+                                                      int Ho, int tiles_x, int tiles_y, int n_tiles,
+                                                      int *__restrict__ err)
 {
     using HL = Halo<S>;
-    using SM = FwdSmem<S, N>;
-    constexpr int COLS = tmem_cols<N>();
+    using SM = WsSmem<S, N>;
+    constexpr int NS = SM::ns, COLS = tmem_cols<N>();
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_base = smem_u32(smem);
@@ -440,84 +478,118 @@ __global__ void __launch_bounds__(128) k_conv_umma_fwd(const __grid_constant__ C
         if (tid == 0) *reinterpret_cast<volatile int *>(err) = 3;
         return;
     }
-    const uint32_t bar_w = s_base + SM::bars, bar_full = bar_w + 8, bar_mma = bar_w + 24;
+    const uint32_t bar_w = s_base + SM::bars, bar_full = bar_w + 8, bar_empty = bar_full + 8 * NS;
+    const uint32_t bar_accf = bar_empty + 8 * NS, bar_acce = bar_accf + 16;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::abort);
     float *bias = reinterpret_cast<float *>(smem + SM::bias);
-    const uint32_t tmem = umma_setup<SM, COLS>(smem, bias_g, NR, wpack, Wts<N>::bytes);
-
-    // TMA copy of a tile's halo into buffer hb (thread 0)
-    auto load_tile = [&](int tile, int hb) {
-        int b, ty, tx;
-        tile_coords(tile, tiles_x, tiles_y, b, ty, tx);
-        const int iy0 = S * UTH * ty - 1;
-        const uint32_t dst = s_base + SM::halo + hb * HL::bytes, bar = bar_full + 8 * hb;
-        mbar_expect_tx(bar, S * HL::copy_bytes);
-        if (S == 1) {
-            tma_load_4d(dst, &tin, 0, UTW * tx - 1, iy0, 4 * b, bar);
-        } else {
-            // columns 16 tx - 1 + 2 j (odd: parity 1, half index 8 tx - 1 + j),
-            // then 16 tx + 2 j (parity 0, half index 8 tx + j)
-            tma_load_5d(dst, &tin, 0, 1, UTW * tx - 1, iy0, 4 * b, bar);
-            tma_load_5d(dst + HL::copy_stride, &tin, 0, 0, UTW * tx, iy0, 4 * b, bar);
-        }
-    };
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + SM::taddr),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     if (tid == 0) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
-        if ((int)blockIdx.x < n_tiles) load_tile(blockIdx.x, 0);
-    }
-
-    int bad = 0, fail = 0;
-    int it = 0, prev = -1;
-    for (int tile = blockIdx.x;; tile += gridDim.x, ++it) {
-        const bool have = tile < n_tiles;
-        const int buf = it & 1;                         // accumulator and MMA barrier of this tile
-        const int hb = SM::nbuf == 2 ? buf : 0;         // halo buffer
-        const int huse = SM::nbuf == 2 ? it >> 1 : it;  // its use count
-        // the accumulator is free: its last reader, the epilogue two tiles
-        // back, finished before this barrier
-        tc_fence_before();
-        __syncthreads();
-        if (have && tid == 0 && !bad) {
-            bool ok = (it > 0 || mbar_wait(bar_w, 0)) && mbar_wait(bar_full + 8 * hb, huse & 1);
-            if (ok) {
-                tc_fence_after();
-                issue_tile_mmas<S, N>(s_base + SM::halo + hb * HL::bytes, s_base + SM::w, tmem + buf * N);
-            }
-            umma_commit(bar_mma + 8 * buf);
-            const int next = tile + gridDim.x;
-            if (ok && next < n_tiles) {
-                // the next tile's buffer must no longer be read: by the MMAs of
-                // the last tile (two buffers) or of this one (one buffer)
-                if (SM::nbuf == 2) ok = it == 0 || mbar_wait(bar_mma + 8 * (buf ^ 1), ((it - 1) >> 1) & 1);
-                else ok = mbar_wait(bar_mma + 8 * buf, (it >> 1) & 1);
-                if (ok) load_tile(next, SM::nbuf == 2 ? hb ^ 1 : 0);
-            }
-            if (!ok) {
-                fail = 1;
-                *reinterpret_cast<volatile int *>(err) = 1;
-            }
+        mbar_init(bar_w, 1);
+        for (int i = 0; i < NS; i++) {
+            mbar_init(bar_full + 8 * i, 1);
+            mbar_init(bar_empty + 8 * i, 1);
         }
-        // epilogue of the previous tile
-        if (prev >= 0) {
-            const int pb = buf ^ 1;
-            const bool ok = bad ? true : mbar_wait(bar_mma + 8 * pb, ((it - 1) >> 1) & 1);
-            if (!ok) *reinterpret_cast<volatile int *>(err) = 2;
-            bad = __syncthreads_or(!ok || bad || fail);
-            if (!bad) {
-                tc_fence_after();
-                float v[N];
-                tmem_ld<N>(tmem + ((uint32_t)(32 * warp) << 16) + pb * N, v);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(bar_accf + 8 * i, 1);
+            mbar_init(bar_acce + 8 * i, 4);  // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < UC) bias[tid] = tid < NR ? bias_g[tid] : 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + SM::taddr);
+    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto fail = [&](int code) {
+        *reinterpret_cast<volatile int *>(err) = code;
+        *abort_flag = 1;
+    };
+    if (warp == 4) {
+        if (lane == 0) {
+            mbar_expect_tx(bar_w, Wts<N>::bytes);
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        s_base + SM::w + h * (Wts<N>::bytes / 2)),
+                    "l"(reinterpret_cast<const uint8_t *>(wpack) + h * (Wts<N>::bytes / 2)),
+                    "r"(Wts<N>::bytes / 2), "r"(bar_w)
+                    : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
+            for (int i = 0; i < my_tiles; i++) {
+                const int st = i % NS;
+                // the stage's last tile (i - NS) has been multiplied
+                if (i >= NS && !mbar_wait_ab(bar_empty + 8 * st, ((i / NS) - 1) & 1, abort_flag)) {
+                    fail(1);
+                    break;
+                }
                 int b, ty, tx;
-                tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
-                const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
-                if (oy < Ho && ox < Ho) store_pixel<NR, RELU, OUT_F32>(out, v, bias, b, Ho, oy, ox);
+                tile_coords(blockIdx.x + i * gridDim.x, tiles_x, tiles_y, b, ty, tx);
+                const int iy0 = S * UTH * ty - 1;
+                const uint32_t dst = s_base + SM::halo + st * HL::bytes, bar = bar_full + 8 * st;
+                mbar_expect_tx(bar, S * HL::copy_bytes);
+                if (S == 1) {
+                    tma_load_4d(dst, &tin, 0, UTW * tx - 1, iy0, 4 * b, bar);
+                } else {
+                    tma_load_5d(dst, &tin, 0, 1, UTW * tx - 1, iy0, 4 * b, bar);
+                    tma_load_5d(dst + HL::copy_stride, &tin, 0, 0, UTW * tx, iy0, 4 * b, bar);
+                }
             }
-        } else if (have) {
-            bad = __syncthreads_or(bad || fail);
         }
-        if (!have || bad) break;
-        prev = tile;
+    } else if (warp == 5) {
+        if (lane == 0) {
+            bool ok = my_tiles == 0 || mbar_wait_ab(bar_w, 0, abort_flag);
+            if (!ok) fail(1);
+            for (int i = 0; ok && i < my_tiles; i++) {
+                const int st = i % NS, a = i & 1;
+                if (!mbar_wait_ab(bar_full + 8 * st, (i / NS) & 1, abort_flag)) {
+                    fail(1);
+                    break;
+                }
+                // the accumulator's last tile (i - 2) has been read
+                if (i >= 2 && !mbar_wait_ab(bar_acce + 8 * a, ((i >> 1) - 1) & 1, abort_flag)) {
+                    fail(2);
+                    break;
+                }
+                tc_fence_after();
+                issue_tile_mmas<S, N>(s_base + SM::halo + st * HL::bytes, s_base + SM::w, tmem + a * N);
+                umma_commit(bar_empty + 8 * st);
+                umma_commit(bar_accf + 8 * a);
+            }
+        }
+    } else {
+        for (int i = 0; i < my_tiles; i++) {
+            const int a = i & 1;
+            const bool ok = mbar_wait_ab(bar_accf + 8 * a, (i >> 1) & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) fail(2);
+                break;
+            }
+            tc_fence_after();
+            float v[N];
+            tmem_ld<N>(tmem + ((uint32_t)(32 * warp) << 16) + a * N, v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_acce + 8 * a);
+            int b, ty, tx;
+            tile_coords(blockIdx.x + i * gridDim.x, tiles_x, tiles_y, b, ty, tx);
+            const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
+            if (oy < Ho && ox < Ho) store_pixel<NR, RELU, OUT_F32>(out, v, bias, b, Ho, oy, ox);
+        }
     }
-    umma_teardown<COLS>(tmem);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
 }
 
 // Positive entries of a planar BF16 activation: 32 bits, one per channel.
@@ -724,12 +796,12 @@ reg_status launch_fwd(const uint16_t *in, int H, const float *theta, void *out, 
     if (pack) k_pack_umma<false, N, NR><<<(Wts<N>::bytes / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
     const int Ho = (H + 2 - 3) / S + 1;
     const int tx = (Ho + UTW - 1) / UTW, ty = (Ho + UTH - 1) / UTH, nt = B * tx * ty;
-    auto kern = k_conv_umma_fwd<S, N, NR, RELU, OUT_F32>;
-    constexpr int bytes = FwdSmem<S, N>::bytes;
+    auto kern = k_conv_umma_ws<S, N, NR, RELU, OUT_F32>;
+    constexpr int bytes = WsSmem<S, N>::bytes;
     int grid = 0;
     if (!grid_for(kern, bytes, tmem_cols<N>(), nt, grid))
         return reg_internal_fail(REG_ECUDA, "tcgen05 convolution: launch attributes");
-    kern<<<grid, 128, bytes, st>>>(map, theta + NR * UC * 9, wpack, out, Ho, tx, ty, nt, err);
+    kern<<<grid, 192, bytes, st>>>(map, theta + NR * UC * 9, wpack, out, Ho, tx, ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 convolution launch");
     return REG_OK;
 }
