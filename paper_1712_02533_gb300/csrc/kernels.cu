@@ -1561,7 +1561,8 @@ __device__ void control_op(const BatchDev &b, OpState &s, const OpDesc &op, int 
 
 __global__ void __launch_bounds__(256) k_control(BatchDev b)
 {
-    __shared__ double red[8][PT_STRIDE + 2];
+    __shared__ double red[8][2];
+    __shared__ double redT[9][PT_STRIDE];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int n_ops = b.ctr[0];
     // grid-stride over ops: one block per op, the block reduces the op's tile
@@ -1589,15 +1590,17 @@ __global__ void __launch_bounds__(256) k_control(BatchDev b)
         __syncthreads();
         continue;
     }
-    // reduce the T partials (and G slope partials) of this op over the block
-    double S[PT_STRIDE];
-#pragma unroll
-    for (int k = 0; k < PT_STRIDE; k++) S[k] = 0.0;
+    // reduce the T partials (and G slope partials) of this op over the block:
+    // thread t < 9 PT_STRIDE sums entry t % PT_STRIDE of every ninth record
+    // from t / PT_STRIDE on, so that a warp's loads are consecutive doubles;
+    // thread 0 then adds the nine partial sums of each entry in order
+    // (deterministic)
     const int tb = s.t_begin, te = s.t_end;
-    for (int it = tb + threadIdx.x; it < te; it += blockDim.x) {
-        const double *p = b.partT + (int64_t)it * PT_STRIDE;
-#pragma unroll
-        for (int k = 0; k < PT_STRIDE; k++) S[k] += p[k];
+    if (threadIdx.x < 9 * PT_STRIDE) {
+        const int kk = threadIdx.x % PT_STRIDE, g = threadIdx.x / PT_STRIDE;
+        double acc = 0.0;
+        for (int it = tb + g; it < te; it += 9) acc += b.partT[(int64_t)it * PT_STRIDE + kk];
+        redT[g][kk] = acc;
     }
     double slope = 0.0, qud = 0.0;
     if (ph == PH_GRAD) {
@@ -1606,26 +1609,25 @@ __global__ void __launch_bounds__(256) k_control(BatchDev b)
             qud += b.partG[(int64_t)it * PG_STRIDE + 1];
         }
     }
-#pragma unroll
-    for (int k = 0; k < PT_STRIDE; k++) {
-        double v = warp_sum_d(S[k]);
-        if (lane == 0) red[wid][k] = v;
-    }
     slope = warp_sum_d(slope);
     qud = warp_sum_d(qud);
     if (lane == 0) {
-        red[wid][PT_STRIDE] = slope;
-        red[wid][PT_STRIDE + 1] = qud;
+        red[wid][0] = slope;
+        red[wid][1] = qud;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < PT_STRIDE + 2; k++) {
+        double S[PT_STRIDE];
+        for (int k = 0; k < PT_STRIDE; k++) {
             double v = 0.0;
-            for (int w = 0; w < 8; w++) v += red[w][k];
-            if (k < PT_STRIDE) S[k] = v;
-            else if (k == PT_STRIDE) slope = v;
-            else qud = v;
+            for (int g = 0; g < 9; g++) v += redT[g][k];
+            S[k] = v;
+        }
+        slope = 0.0;
+        qud = 0.0;
+        for (int w = 0; w < 8; w++) {
+            slope += red[w][0];
+            qud += red[w][1];
         }
         control_op(b, s, op, o, ph, S, slope, qud);
     }
