@@ -187,7 +187,7 @@ __global__ void k_restrict_img(const float *__restrict__ fine, int64_t fstride, 
 }
 
 // Per image: FE mean (w^T F) and FE standard deviation ((F-mean)^T M (F-mean))^1/2,
-// two passes over the cells in double.  Each image's cell rows are cut into
+// two passes over the cells, summed in double.  Each image's cell rows are cut into
 // STATS_SPLIT parts, one block each (grid: parts, images); the parts' sums
 // go to `part` and are added in order by k_image_stats_fin (deterministic).
 constexpr int STATS_SPLIT = 32;
@@ -212,20 +212,31 @@ __global__ void k_image_stats_part(const float *__restrict__ img, int64_t stride
     __shared__ double red[32];
     const int rows = n - 1, per = (rows + STATS_SPLIT - 1) / STATS_SPLIT;
     const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
-    const double m = pass ? stats[2 * blockIdx.y] : 0.0;
+    // each cell's term in FP32, their sum in FP64 (GB300's FP64 rate is a
+    // small fraction of its FP32 rate).  Pass 1 centres on the FP64 mean
+    // rounded to FP32: the cell form's linear term in that offset sums to
+    // zero (M 1 = w and sum w (F - mean) = 0), so only its square, ~1e-14 of
+    // the variance, remains.
+    // (a thread adds its few cells of a row in FP32, then the row's share in
+    // FP64)
+    const float mf = pass ? (float)stats[2 * blockIdx.y] : 0.f;
     double s = 0.0;
-    for (int k = threadIdx.x; k < (r1 - r0) * (n - 1); k += blockDim.x) {
-        const int r = r0 + k / (n - 1), c = k % (n - 1);
-        const float *p = F + (int64_t)r * pitch + c;
-        if (!pass) {
-            s += 0.25 * ((double)p[0] + p[1] + p[pitch] + p[pitch + 1]);
-        } else {
-            const double a = p[0] - m, b = p[1] - m, cc = p[pitch + 1] - m, d = p[pitch] - m;  // cyclic a b c d
-            s += (4.0 * (a * a + b * b + cc * cc + d * d) + 4.0 * (a * b + b * cc + cc * d + d * a) +
-                  2.0 * (a * cc + b * d)) / 36.0;
+    for (int r = r0; r < r1; r++) {
+        const float *row = F + (int64_t)r * pitch;
+        float rs = 0.f;
+        for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
+            const float *p = row + c;
+            if (!pass) {
+                rs += 0.25f * ((p[0] + p[1]) + (p[pitch] + p[pitch + 1]));
+            } else {
+                const float a = p[0] - mf, b = p[1] - mf, cc = p[pitch + 1] - mf, d = p[pitch] - mf;  // cyclic
+                rs += 4.f * (a * a + b * b + cc * cc + d * d) + 4.f * (a * b + b * cc + cc * d + d * a) +
+                      2.f * (a * cc + b * d);
+            }
         }
+        s += (double)rs;
     }
-    const double t = block_sum_d(s, red);
+    const double t = block_sum_d(s, red) * (pass ? 1.0 / 36.0 : 1.0);
     if (threadIdx.x == 0) part[(int64_t)blockIdx.y * STATS_SPLIT + blockIdx.x] = t;
 }
 
