@@ -474,17 +474,25 @@ def main():
         e2e_steps = max(1, a.steps)
         barrier()
         t = time.time()
+        phases = []  # per step: wall ms of creation (upload + pyramid), scan, download, release
         for _ in range(e2e_steps):
+            t_a = time.time()
             with reg.Series([host], p2) as s2:
                 for lv in (tiles or {}).get("levels", []):  # the tuned table, as a user reuses it
                     s2.set_tile_rows(lv["level"], lv["grad_rows"], lv["trial_rows"])
+                t_b = time.time()
                 r2 = s2.prefix_scan(kind, a.chunks, reg.KOGGE_STONE)
+                t_c = time.time()
                 s2.get_deformations(out=out)
+                t_d = time.time()
+            t_e = time.time()
+            phases.append([round((y - x) * 1e3, 1) for x, y in ((t_a, t_b), (t_b, t_c), (t_c, t_d), (t_d, t_e))])
         barrier()
         e2e_s = max_over_ranks((time.time() - t) / e2e_steps, world, dev)
         e2e = {"value": job_rate(world, r2["ops"], e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(out.numel() * 4),
-               "ms_per_step": round(e2e_s * 1e3, 2)}
+               "ms_per_step": round(e2e_s * 1e3, 2),
+               "phases_ms": {"order": ["create", "scan", "download", "release"], "steps": phases}}
     s.close()
 
     if rank == 0:

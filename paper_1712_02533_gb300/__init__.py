@@ -466,9 +466,12 @@ class Series:
                     o += n * s
         else:
             torch = _torch()
-            frames = torch.cat([f.reshape(-1, f.shape[-1]) for f in series_frames]) if len(set(self.sides)) == 1 else None
-            if frames is None:
+            if len(set(self.sides)) != 1:
                 raise ValueError("mixed sides need host frames")
+            # one tensor passes through as a view (a pinned host tensor stays
+            # pinned, so the upload is a direct DMA); several are concatenated
+            flat = [f.reshape(-1, f.shape[-1]) for f in series_frames]
+            frames = flat[0] if len(flat) == 1 else torch.cat(flat)
         self.h, self.params = create_series(frames, self.counts, self.sides, params, stream, use_torch_allocator)
 
     def apply_operator_batch(self, ops):
