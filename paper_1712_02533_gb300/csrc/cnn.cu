@@ -275,6 +275,254 @@ __global__ void k_bwd_weight_sum(const float *__restrict__ part, int split, floa
     else if (c == 0) grad[O * C * 9 + o] = t;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradients of the 2 -> 32 (stride 2) and 32 -> 2 layers.  Their
+// arithmetic intensity is a few FLOPs per byte (two input channels, or two
+// output channels), so they stay on the CUDA cores in FP32, but each input
+// element is read from global memory once: a block stages a tile of the output
+// gradient and the input window the tile needs, and its threads form all the
+// layer's weight and bias sums from shared memory.  Each block works through a
+// fixed sequence of tiles (tile = block + k grid) and writes one partial
+// record; k_wgrad_parts_sum adds the records in block order, so the result is
+// deterministic for a given grid.
+// ---------------------------------------------------------------------------
+constexpr int WF_TR = 2, WF_TW = 64, WF_NP = WF_TR * WF_TW;  // first layer: 2 output rows x 64 columns
+constexpr int WF_XR = 2 * WF_TR + 1, WF_XC = 2 * WF_TW + 1;  // its input window: 5 x 129
+constexpr int WF_GS = WF_NP + 1;                              // row stride of the staged gradient
+constexpr int WF_REC = 32 * 2 * 9 + 32;                       // weights (o, c, tap), then biases
+
+// First layer: gW[o][c][dy][dx] = sum gz[b][o][y][x] x[b][c][2 y + dy - 1][2 x + dx - 1],
+// gb[o] = sum gz[b][o][y][x]; x FP32 NCHW (B x 2 x H x H), gz FP32 NCHW (B x
+// 32 x Ho x Ho).  Thread (og, ps) = (t % 8, t / 8) sums output channels
+// 4 og .. 4 og + 3 over the tile pixels ps + 32 k.
+__global__ void __launch_bounds__(256, 2) k_wgrad_first(const float *__restrict__ x, int H,
+                                                     const float *__restrict__ gz, int Ho, int B,
+                                                     float *__restrict__ part)
+{
+    __shared__ float xs[2][WF_XR][WF_XC];
+    __shared__ float gs[32 * WF_GS];  // [o][pixel]
+    __shared__ float red[8][8][4 * 19];
+    const int t = threadIdx.x, og = t & 7, ps = t >> 3;
+    float acc[4][19];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 19; j++) acc[i][j] = 0.f;
+    const int tx_n = (Ho + WF_TW - 1) / WF_TW, ty_n = (Ho + WF_TR - 1) / WF_TR, nt = B * tx_n * ty_n;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const int b = tile / (tx_n * ty_n), r = tile % (tx_n * ty_n);
+        const int y0 = (r / tx_n) * WF_TR, x0 = (r % tx_n) * WF_TW;
+        __syncthreads();  // the previous tile's reads are done
+        // a thread's loads are issued in groups before their stores: the
+        // input window (up to 6), then the gradient in two groups of 8
+        constexpr int NG = 32 * WF_NP / 256 / 2, NX = (2 * WF_XR * WF_XC + 255) / 256;
+        {
+            float xv[NX];
+#pragma unroll
+            for (int k = 0; k < NX; k++) {
+                const int i = t + 256 * k, c = i / (WF_XR * WF_XC), rr = (i / WF_XC) % WF_XR, cc = i % WF_XC;
+                const int iy = 2 * y0 - 1 + rr, ix = 2 * x0 - 1 + cc;
+                xv[k] = (i < 2 * WF_XR * WF_XC && iy >= 0 && iy < H && ix >= 0 && ix < H)
+                            ? x[(((int64_t)b * 2 + c) * H + iy) * H + ix] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < NX; k++) {
+                const int i = t + 256 * k;
+                if (i < 2 * WF_XR * WF_XC) (&xs[0][0][0])[i] = xv[k];
+            }
+        }
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            float gv[NG];
+#pragma unroll
+            for (int k = 0; k < NG; k++) {
+                const int i = t + 256 * (NG * half + k), o = i / WF_NP, p = i % WF_NP;
+                const int y = y0 + p / WF_TW, xx = x0 + p % WF_TW;
+                gv[k] = (y < Ho && xx < Ho) ? gz[(((int64_t)b * 32 + o) * Ho + y) * Ho + xx] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < NG; k++) {
+                const int i = t + 256 * (NG * half + k);
+                gs[(i / WF_NP) * WF_GS + i % WF_NP] = gv[k];
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k = 0; k < WF_NP / 32; k++) {
+            const int p = ps + 32 * k, py = p / WF_TW, px = p % WF_TW;
+            float gv[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) gv[i] = gs[(4 * og + i) * WF_GS + p];
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+                    for (int dx = 0; dx < 3; dx++) {
+                        const float v = xs[c][2 * py + dy][2 * px + dx];
+#pragma unroll
+                        for (int i = 0; i < 4; i++) acc[i][c * 9 + dy * 3 + dx] = fmaf(gv[i], v, acc[i][c * 9 + dy * 3 + dx]);
+                    }
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[i][18] += gv[i];
+        }
+    }
+    // the lanes l, l ^ 8, l ^ 16, l ^ 24 of a warp share og; then the 8 warps
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 19; j++) {
+            float v = acc[i][j];
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (lane < 8) red[w][lane][i * 19 + j] = v;
+        }
+    __syncthreads();
+    for (int e = t; e < WF_REC; e += 256) {
+        // weights (o, c, tap) at (2 o + c) 9 + tap, then the biases
+        const int o = e < 576 ? e / 18 : e - 576, j = e < 576 ? e % 18 : 18;
+        float sum = 0.f;
+        for (int w2 = 0; w2 < 8; w2++) sum += red[w2][o >> 2][(o & 3) * 19 + j];
+        part[(int64_t)blockIdx.x * WF_REC + e] = sum;
+    }
+}
+
+constexpr int WL_TR = 4, WL_TW = 32, WL_NP = WL_TR * WL_TW;  // last layer: 4 output rows x 32 columns
+constexpr int WL_AR = WL_TR + 2, WL_AC = WL_TW + 2;          // its input window: 6 x 34
+constexpr int WL_CS = WL_AR * WL_AC + 1;                     // channel stride (odd: no bank conflicts)
+constexpr int WL_REC = 2 * 32 * 9 + 2;
+
+// Last layer: gW[o][c][dy][dx] = sum gz[b][o][y][x] a[b][c][y + dy - 1][x + dx - 1],
+// gb[o] = sum gz[b][o][y][x]; a the planar BF16 input (B x 32 x H x H), gz FP32
+// NCHW (B x 2 x H x H).  Thread (c, seg) = (t % 32, t / 32) walks 16 pixels of
+// tile row seg / 2 with a sliding 3 x 3 window of channel c.
+__global__ void __launch_bounds__(256) k_wgrad_last(const uint4 *__restrict__ a, int H, const float *__restrict__ gz,
+                                                    int B, float *__restrict__ part)
+{
+    __shared__ float as[32 * WL_CS];
+    __shared__ float gs[2][WL_NP];
+    __shared__ float red[8][32][18];
+    __shared__ float redb[8][2];
+    const int t = threadIdx.x, c = t & 31, seg = t >> 5, r = seg >> 1, xs0 = (seg & 1) * 16;
+    float acc[18], gb0 = 0.f, gb1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 18; j++) acc[j] = 0.f;
+    const int tx_n = (H + WL_TW - 1) / WL_TW, ty_n = (H + WL_TR - 1) / WL_TR, nt = B * tx_n * ty_n;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const int b = tile / (tx_n * ty_n), rr0 = tile % (tx_n * ty_n);
+        const int y0 = (rr0 / tx_n) * WL_TR, x0 = (rr0 % tx_n) * WL_TW;
+        __syncthreads();
+        // all of a thread's loads are issued before its stores
+        constexpr int NA = (4 * WL_AR * WL_AC + 255) / 256;
+        float g[2];
+        uint4 qa[NA];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int i = t + 256 * k, o = i / WL_NP, p = i % WL_NP, y = y0 + p / WL_TW, xx = x0 + p % WL_TW;
+            g[k] = (y < H && xx < H) ? gz[(((int64_t)b * 2 + o) * H + y) * H + xx] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < NA; k++) {
+            const int i = t + 256 * k, cg = i / (WL_AR * WL_AC), rr = (i / WL_AC) % WL_AR, cc = i % WL_AC;
+            const int iy = y0 - 1 + rr, ix = x0 - 1 + cc;
+            qa[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < 4 * WL_AR * WL_AC && iy >= 0 && iy < H && ix >= 0 && ix < H)
+                qa[k] = a[((int64_t)(4 * b + cg) * H + iy) * H + ix];
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) (&gs[0][0])[t + 256 * k] = g[k];
+#pragma unroll
+        for (int k = 0; k < NA; k++) {
+            const int i = t + 256 * k, cg = i / (WL_AR * WL_AC), rr = (i / WL_AC) % WL_AR, cc = i % WL_AC;
+            if (i >= 4 * WL_AR * WL_AC) continue;
+            const uint32_t wv[4] = {qa[k].x, qa[k].y, qa[k].z, qa[k].w};
+            float *dst = as + (8 * cg) * WL_CS + rr * WL_AC + cc;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                dst[(2 * j) * WL_CS] = __uint_as_float(wv[j] << 16);
+                dst[(2 * j + 1) * WL_CS] = __uint_as_float(wv[j] & 0xFFFF0000u);
+            }
+        }
+        __syncthreads();
+        const float *ac = as + c * WL_CS + r * WL_AC + xs0;
+        float win[3][3];
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++) {
+            win[dy][0] = ac[dy * WL_AC];
+            win[dy][1] = ac[dy * WL_AC + 1];
+        }
+#pragma unroll 4
+        for (int px = 0; px < 16; px++) {
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++) win[dy][2] = ac[dy * WL_AC + px + 2];
+            const int p = r * WL_TW + xs0 + px;
+            const float g0 = gs[0][p], g1 = gs[1][p];
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 3; dx++) {
+                    acc[dy * 3 + dx] = fmaf(g0, win[dy][dx], acc[dy * 3 + dx]);
+                    acc[9 + dy * 3 + dx] = fmaf(g1, win[dy][dx], acc[9 + dy * 3 + dx]);
+                }
+            gb0 += g0;
+            gb1 += g1;
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++) {
+                win[dy][0] = win[dy][1];
+                win[dy][1] = win[dy][2];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 18; j++) red[seg][c][j] = acc[j];
+    if (c == 0) {
+        redb[seg][0] = gb0;
+        redb[seg][1] = gb1;
+    }
+    __syncthreads();
+    for (int e = t; e < WL_REC; e += 256) {
+        // weights (o, c, tap) at (32 o + c) 9 + tap, then the biases
+        float sum = 0.f;
+        if (e < 576) {
+            const int o = e / 288, cc = (e % 288) / 9, tap = e % 9;
+            for (int w2 = 0; w2 < 8; w2++) sum += red[w2][cc][o * 9 + tap];
+        } else {
+            for (int w2 = 0; w2 < 8; w2++) sum += redb[w2][e - 576];
+        }
+        part[(int64_t)blockIdx.x * WL_REC + e] = sum;
+    }
+}
+
+// grad[e] = sum over blocks of part[block][e], e < rec: one block per entry,
+// a fixed-order tree.
+__global__ void __launch_bounds__(256) k_wgrad_parts_sum(const float *__restrict__ part, int nblk, int rec,
+                                                         float *__restrict__ grad)
+{
+    __shared__ float red[8];
+    const int e = blockIdx.x, t = threadIdx.x;
+    float s = 0.f;
+    for (int k = t; k < nblk; k += 256) s += part[(int64_t)k * rec + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((t & 31) == 0) red[t >> 5] = s;
+    __syncthreads();
+    if (t == 0) {
+        float tot = 0.f;
+        for (int w = 0; w < 8; w++) tot += red[w];
+        grad[e] = tot;
+    }
+}
+
+// Grid of the two kernels above: two blocks per SM, at most one per tile.
+int wgrad_small_grid(int n_tiles)
+{
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 152;
+    return std::max(1, std::min(n_tiles, 2 * nsm));
+}
+
 // Mean squared error: per-block partial sums (double), then one block adds them
 // in order; gy = 2 (y - t) / N.
 __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, int64_t n, float *__restrict__ gy,
@@ -298,12 +546,22 @@ __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, 
     }
 }
 
-__global__ void k_sum_partials(const double *partial, int n, double scale, double *out)
+__global__ void __launch_bounds__(256) k_sum_partials(const double *partial, int n, double scale, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; i++) s += partial[i];
-        *out = s * scale;
+    // fixed order: thread t adds entries t, t + 256, ...; then the warps' sums
+    // by shuffles and the eight warp totals in order
+    __shared__ double red[8];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int i = t; i < n; i += 256) s += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((t & 31) == 0) red[t >> 5] = s;
+    __syncthreads();
+    if (t == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += red[w];
+        *out = tot * scale;
     }
 }
 
@@ -547,10 +805,11 @@ reg_status reg_cnn_loss_grad_tc(reg_cnn_t h, const float *x, const float *target
     return loss_grad(h, x, target, batch, loss, grad_out, true);
 }
 
-// Loss and gradient; tc: the four 32 -> 32 layers' forward and weight
-// gradients and the three stride-1 layers' data gradients on the tensor cores
-// (BF16 operands, FP32 accumulation); the 2 -> 32 and 32 -> 2 layers and the
-// stride-2 32 -> 32 layer's data gradient on the CUDA cores in FP32.
+// Loss and gradient; tc: the forward of all six layers, the four 32 -> 32
+// layers' weight and data gradients on the tensor cores (BF16 operands, FP32
+// accumulation); the weight gradients of the 2 -> 32 and 32 -> 2 layers
+// (k_wgrad_first, k_wgrad_last) and the last layer's data gradient on the CUDA
+// cores in FP32.
 static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, int32_t batch, double *loss,
                             float *grad_out, bool tc)
 {
@@ -562,7 +821,7 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
     const int64_t ny = act_elems(NL - 1, S) * B;
     const int nb = (int)std::min<int64_t>(1024, (ny + 255) / 256);
     k_mse<<<nb, 256, 0, st>>>(h->act[NL - 1], target, ny, h->gy, h->partial);
-    k_sum_partials<<<1, 32, 0, st>>>(h->partial, nb, 1.0 / (double)ny, h->loss);
+    k_sum_partials<<<1, 256, 0, st>>>(h->partial, nb, 1.0 / (double)ny, h->loss);
     const float *gz = h->gy;
     float *bufs[2] = {h->g0, h->g1};
     for (int k = NL - 1; k >= 0; k--) {
@@ -577,24 +836,31 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
             const uint16_t *inb = h->actb[k - 1];
             rs = cnn_wgrad32_tc(inb, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
             if (rs != REG_OK) return rs;
-            if (LAYERS[k].S == 1) {
-                const bool pack = h->packed_dgrad[k - 1] != h->version;
-                rs = cnn_dgrad32_umma(gz, H, th, inb, gx, B, st, h->wpack_d + (k - 1) * cnn_conv32_umma_words(), pack,
-                                      h->uerr);
-                if (rs != REG_OK) return rs;
-                h->packed_dgrad[k - 1] = h->version;
-            } else {
-                const int Ho = (H + 2 - 3) / LAYERS[k].S + 1, total = B * H * H;
-                k_conv_bwd_data<32, 32, 2, true><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, th, inb, gx, H, total);
-            }
+            const bool pack = h->packed_dgrad[k - 1] != h->version;
+            uint32_t *wp = h->wpack_d + (k - 1) * cnn_conv32_umma_words();
+            if (LAYERS[k].S == 1) rs = cnn_dgrad32_umma(gz, H, th, inb, gx, B, st, wp, pack, h->uerr);
+            else rs = cnn_dgrad32s2_umma(gz, H / 2, th, inb, gx, B, st, wp, pack, h->uerr);
+            if (rs != REG_OK) return rs;
+            h->packed_dgrad[k - 1] = h->version;
             gz = gx;
             continue;
         }
         if (tc && k == NL - 1) {
             // the last layer's input (and the mask below) is the planar BF16
             // output of layer 4
-            bwd<32, 2, 1, true>(h->actb[k - 1], H, gz, th, h->actb[k - 1], gx, gr, B, st, h->wpart);
+            const int nt = B * ((H + WL_TW - 1) / WL_TW) * ((H + WL_TR - 1) / WL_TR), grid = wgrad_small_grid(nt);
+            k_wgrad_last<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4 *>(h->actb[k - 1]), H, gz, B, h->wpart);
+            k_wgrad_parts_sum<<<WL_REC, 256, 0, st>>>(h->wpart, grid, WL_REC, gr);
+            const int total = B * H * H;
+            k_conv_bwd_data<32, 2, 1, true><<<(total + 127) / 128, 128, 0, st>>>(gz, H, th, h->actb[k - 1], gx, H, total);
             gz = gx;
+            continue;
+        }
+        if (tc && k == 0) {
+            const int Ho = H / 2, nt = B * ((Ho + WF_TW - 1) / WF_TW) * ((Ho + WF_TR - 1) / WF_TR);
+            const int grid = wgrad_small_grid(nt);
+            k_wgrad_first<<<grid, 256, 0, st>>>(x, H, gz, Ho, B, h->wpart);
+            k_wgrad_parts_sum<<<WF_REC, 256, 0, st>>>(h->wpart, grid, WF_REC, gr);
             continue;
         }
         switch (k) {

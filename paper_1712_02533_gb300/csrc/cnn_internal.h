@@ -41,6 +41,13 @@ reg_status cnn_conv32_umma(const uint16_t *in, int H, const float *theta, void *
 // mask the activation below (planar).
 reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const uint16_t *mask, float *gx, int B,
                             cudaStream_t st, uint32_t *wpack, bool pack, int *err);
+// Data gradient of a stride-2 32 -> 32 layer on the tensor cores: gz (FP32
+// NCHW, B x 32 x Hg x Hg) the gradient with respect to the layer's
+// pre-activation output, gx (FP32 NCHW, B x 32 x 2Hg x 2Hg) = (mask > 0) *
+// the transposed convolution, mask the activation below (planar, side 2 Hg);
+// wpack as cnn_dgrad32_umma's (the same packing).
+reg_status cnn_dgrad32s2_umma(const float *gz, int Hg, const float *theta, const uint16_t *mask, float *gx, int B,
+                              cudaStream_t st, uint32_t *wpack, bool pack, int *err);
 int cnn_conv32_umma_words();
 // The last layer (32 -> 2, stride 1, no ReLU) on the same kernel with N = 16
 // (output rows 2..15 zero): in planar (B x 32 x H x H), out FP32 NCHW (B x 2 x

@@ -3,7 +3,8 @@
 // FP32 accumulation.  All six layers of the tensor-core forward run here: the
 // four 32 -> 32 layers and the last layer (32 -> 2) from TMA-loaded tiles,
 // the first layer (2 -> 32) from tiles the CTA's threads stage; and the data
-// gradients of the three stride-1 32 -> 32 layers.
+// gradients of the four 32 -> 32 layers (stride 1, and stride 2 as four
+// parity classes of stride-1 GEMMs).
 //
 // Implicit GEMM per output tile of 16 rows x 8 columns of one image:
 //   D[m][o] = sum_k A[m][k] W[o][k],   m = 8 (tile row) + (tile column),
@@ -44,7 +45,7 @@
 // TMEM accumulators); each epilogue warp reads its 32 TMEM lanes (= tile rows
 // 32 w .. 32 w + 31) with tcgen05.ld and writes bias + ReLU as planar BF16, or
 // the last layer's two channels as FP32 NCHW.  The kernels whose threads stage
-// their tiles (the first layer; the data gradient of a stride-1 layer, which
+// their tiles (the first layer; the data gradient of a 32 -> 32 layer, which
 // runs the same GEMM on the output gradient, FP32 NCHW, with flipped and
 // transposed weights, times the ReLU mask of the layer below) keep one thread
 // issuing the MMAs, two halo buffers and two accumulators, so that a tile's
@@ -366,6 +367,40 @@ __device__ __forceinline__ void issue_l0_mmas(uint32_t hbase, uint32_t wbase, ui
     }
 }
 
+// The 18 MMAs of one tile of the data gradient of a stride-2 32 -> 32 layer.
+// An input pixel (2 i + py, 2 j + px) takes the taps dy with 2 i + py + 1 - dy
+// even: dy = 1 (output row i) for py = 0, dy = 0 (row i + 1) and dy = 2 (row i)
+// for py = 1, and likewise along x.  Each parity class q = 2 py + px is then a
+// stride-1 GEMM over the output gradient on the class grid (i, j), with 1, 2, 2
+// or 4 taps at offsets 0 and +1: in the halo of the stride-1 data gradient
+// (origin one row and column before the tile) offset delta is tap row or column
+// 1 + delta.  The weights are those of the stride-1 packing (flipped: packed
+// tap p holds W[.][.][8 - p]), so tap (dy, dx) reads packed tap 8 - (3 dy + dx).
+// Class q accumulates into columns d + 32 q.
+__device__ __forceinline__ void issue_dgrad2_mmas(uint32_t hbase, uint32_t wbase, uint32_t d)
+{
+    using HL = Halo<1>;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int py = q >> 1, px = q & 1;
+        int first = 1;
+#pragma unroll
+        for (int ty = 0; ty < 1 + py; ty++) {
+            const int dy = py ? 2 * ty : 1, hy = dy == 0 ? 2 : 1;
+#pragma unroll
+            for (int tx = 0; tx < 1 + px; tx++) {
+                const int dx = px ? 2 * tx : 1, hx = dx == 0 ? 2 : 1, p = 8 - (3 * dy + dx);
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    umma_bf16<UC>(d + 32 * q, sdesc(hbase + HL::tap_offset(hy, hx, 2 * h), HL::cg_bytes, HL::sbo),
+                                  sdesc(wbase + (4 * p + 2 * h) * UC * 16, UC * 16, 128), first ? 0u : 1u);
+                    first = 0;
+                }
+            }
+        }
+    }
+}
+
 // Common setup: TMEM columns, mbarriers, bias (nb entries), and the weights'
 // bulk copy (wbytes, a multiple of 32).
 template <class SM, int COLS>
@@ -612,13 +647,24 @@ __device__ __forceinline__ uint32_t positive_mask(const uint4 *act, int b, int H
 
 // Kernels whose tiles the CTA's threads stage from FP32 NCHW input, rounded
 // to BF16 (the previous tile's MMAs waited on in the last epilogue):
-//   L0 false: the data gradient of a stride-1 32 -> 32 layer, gz (the
+//   ST_DGRAD1: the data gradient of a stride-1 32 -> 32 layer, gz (the
 //     gradient with respect to the layer's pre-activation output) in, gx =
 //     the GEMM with flipped and transposed weights where the planar BF16
 //     activation below (mask) is positive, else 0;
-//   L0 true: the first layer's forward (2 input channels, stride 2, padded to
-//     one group of 8), bias + ReLU out as planar BF16.
-template <bool L0>
+//   ST_FIRST: the first layer's forward (2 input channels, stride 2, padded to
+//     one group of 8), bias + ReLU out as planar BF16;
+//   ST_DGRAD2: the data gradient of a stride-2 32 -> 32 layer: tiles of the
+//     class grid (side H, the output gradient's), the four parity classes of
+//     a tile in four accumulators (issue_dgrad2_mmas), gx of side Ho = 2 H
+//     written as pairs of adjacent columns (px = 0, 1), masked as ST_DGRAD1.
+constexpr int ST_DGRAD1 = 0, ST_FIRST = 1, ST_DGRAD2 = 2;
+template <int MODE>
+__host__ __device__ constexpr int staged_cols()
+{
+    return MODE == ST_DGRAD2 ? 2 * 4 * UC : tmem_cols<UC>();
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restrict__ in, int H,
                                                           const uint32_t *__restrict__ wpack,
                                                           const float *__restrict__ bias_g,
@@ -626,10 +672,11 @@ __global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restric
                                                           int Ho, int tiles_x, int tiles_y, int n_tiles,
                                                           int *__restrict__ err)
 {
+    constexpr bool L0 = MODE == ST_FIRST;
     constexpr int S = L0 ? 2 : 1, G = L0 ? 1 : 4;
     using HL = Halo<S, G>;
     using SM = std::conditional_t<L0, L0Smem, DgradSmem>;
-    constexpr int COLS = tmem_cols<UC>();
+    constexpr int COLS = staged_cols<MODE>(), ACC = COLS / 2;  // two accumulators of ACC columns
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_base = smem_u32(smem);
@@ -684,8 +731,9 @@ __global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restric
                 *reinterpret_cast<volatile int *>(err) = 1;
             } else {
                 const uint32_t hbase = s_base + SM::halo + buf * HL::bytes;
-                if (L0) issue_l0_mmas(hbase, s_base + SM::w, tmem + buf * UC);
-                else issue_tile_mmas<1, UC>(hbase, s_base + SM::w, tmem + buf * UC);
+                if (MODE == ST_FIRST) issue_l0_mmas(hbase, s_base + SM::w, tmem + buf * ACC);
+                else if (MODE == ST_DGRAD2) issue_dgrad2_mmas(hbase, s_base + SM::w, tmem + buf * ACC);
+                else issue_tile_mmas<1, UC>(hbase, s_base + SM::w, tmem + buf * ACC);
             }
             umma_commit(bar_mma + 8 * buf);
         }
@@ -696,20 +744,45 @@ __global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restric
             bad = __syncthreads_or(!ok || bad);
             if (!bad) {
                 tc_fence_after();
-                float v[UC];
-                tmem_ld<UC>(tmem + ((uint32_t)(32 * warp) << 16) + pb * UC, v);
                 int b, ty, tx;
                 tile_coords(prev, tiles_x, tiles_y, b, ty, tx);
-                const int m = 32 * warp + lane, oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
-                if (oy < Ho && ox < Ho) {
-                    if (L0) {
-                        store_pixel<UC, true, false>(out, v, bias, b, Ho, oy, ox);
-                    } else {
-                        float *gx = reinterpret_cast<float *>(out);
-                        const uint32_t pm = positive_mask(mask, b, Ho, oy, ox);
-                        const int64_t o0 = ((int64_t)b * UC * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
+                const int m = 32 * warp + lane;
+                const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+                if (MODE == ST_DGRAD2) {
+                    // class grid pixel (i, j) -> input pixels (2 i + py, 2 j + px)
+                    const int i = ty * UTH + (m >> 3), j = tx * UTW + (m & 7);
+                    float *gx = reinterpret_cast<float *>(out);
+                    const int64_t plane = (int64_t)Ho * Ho;
+#pragma unroll 1
+                    for (int py = 0; py < 2; py++) {
+                        float v0[UC], v1[UC];
+                        tmem_ld<UC>(tmem + lanes + pb * ACC + 32 * (2 * py), v0);
+                        tmem_ld<UC>(tmem + lanes + pb * ACC + 32 * (2 * py + 1), v1);
+                        if (i < H && j < H) {
+                            const int iy = 2 * i + py, ix = 2 * j;
+                            const uint32_t m0 = positive_mask(mask, b, Ho, iy, ix);
+                            const uint32_t m1 = positive_mask(mask, b, Ho, iy, ix + 1);
+                            float2 *o2 = reinterpret_cast<float2 *>(gx + ((int64_t)b * UC * Ho + iy) * Ho + ix);
 #pragma unroll
-                        for (int o = 0; o < UC; o++) gx[o0 + o * plane] = ((pm >> o) & 1u) ? v[o] : 0.f;
+                            for (int o = 0; o < UC; o++)
+                                o2[o * (plane / 2)] = make_float2(((m0 >> o) & 1u) ? v0[o] : 0.f,
+                                                                  ((m1 >> o) & 1u) ? v1[o] : 0.f);
+                        }
+                    }
+                } else {
+                    float v[UC];
+                    tmem_ld<UC>(tmem + lanes + pb * ACC, v);
+                    const int oy = ty * UTH + (m >> 3), ox = tx * UTW + (m & 7);
+                    if (oy < Ho && ox < Ho) {
+                        if (L0) {
+                            store_pixel<UC, true, false>(out, v, bias, b, Ho, oy, ox);
+                        } else {
+                            float *gx = reinterpret_cast<float *>(out);
+                            const uint32_t pm = positive_mask(mask, b, Ho, oy, ox);
+                            const int64_t o0 = ((int64_t)b * UC * Ho + oy) * Ho + ox, plane = (int64_t)Ho * Ho;
+#pragma unroll
+                            for (int o = 0; o < UC; o++) gx[o0 + o * plane] = ((pm >> o) & 1u) ? v[o] : 0.f;
+                        }
                     }
                 }
             }
@@ -836,9 +909,9 @@ reg_status cnn_first_umma(const float *x, int H, const float *theta, uint16_t *o
     const int Ho = (H + 2 - 3) / 2 + 1;
     const int tx = (Ho + UTW - 1) / UTW, ty = (Ho + UTH - 1) / UTH, nt = B * tx * ty;
     int grid = 0;
-    if (!grid_for(k_conv_umma_staged<true>, L0Smem::bytes, tmem_cols<UC>(), nt, grid))
+    if (!grid_for(k_conv_umma_staged<ST_FIRST>, L0Smem::bytes, staged_cols<ST_FIRST>(), nt, grid))
         return reg_internal_fail(REG_ECUDA, "tcgen05 first layer: launch attributes");
-    k_conv_umma_staged<true><<<grid, 128, L0Smem::bytes, st>>>(x, H, wpack, theta + UC * 2 * 9, nullptr, out, Ho, tx,
+    k_conv_umma_staged<ST_FIRST><<<grid, 128, L0Smem::bytes, st>>>(x, H, wpack, theta + UC * 2 * 9, nullptr, out, Ho, tx,
                                                                ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 first layer launch");
     return REG_OK;
@@ -850,12 +923,27 @@ reg_status cnn_dgrad32_umma(const float *gz, int H, const float *theta, const ui
     if (pack) k_pack_umma<true, UC, UC><<<(Wts<UC>::bytes / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
     const int tx = (H + UTW - 1) / UTW, ty = (H + UTH - 1) / UTH, nt = B * tx * ty;
     int grid = 0;
-    if (!grid_for(k_conv_umma_staged<false>, DgradSmem::bytes, tmem_cols<UC>(), nt, grid))
+    if (!grid_for(k_conv_umma_staged<ST_DGRAD1>, DgradSmem::bytes, staged_cols<ST_DGRAD1>(), nt, grid))
         return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient: launch attributes");
-    k_conv_umma_staged<false><<<grid, 128, DgradSmem::bytes, st>>>(gz, H, wpack, nullptr,
+    k_conv_umma_staged<ST_DGRAD1><<<grid, 128, DgradSmem::bytes, st>>>(gz, H, wpack, nullptr,
                                                                    reinterpret_cast<const uint4 *>(mask), gx, H, tx,
                                                                    ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 data gradient launch");
+    return REG_OK;
+}
+
+reg_status cnn_dgrad32s2_umma(const float *gz, int Hg, const float *theta, const uint16_t *mask, float *gx, int B,
+                              cudaStream_t st, uint32_t *wpack, bool pack, int *err)
+{
+    if (pack) k_pack_umma<true, UC, UC><<<(Wts<UC>::bytes / 4 + 255) / 256, 256, 0, st>>>(theta, wpack);
+    const int tx = (Hg + UTW - 1) / UTW, ty = (Hg + UTH - 1) / UTH, nt = B * tx * ty;
+    int grid = 0;
+    if (!grid_for(k_conv_umma_staged<ST_DGRAD2>, DgradSmem::bytes, staged_cols<ST_DGRAD2>(), nt, grid))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 stride-2 data gradient: launch attributes");
+    k_conv_umma_staged<ST_DGRAD2><<<grid, 128, DgradSmem::bytes, st>>>(gz, Hg, wpack, nullptr,
+                                                                     reinterpret_cast<const uint4 *>(mask), gx,
+                                                                     2 * Hg, tx, ty, nt, err);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 stride-2 data gradient launch");
     return REG_OK;
 }
 
