@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libreg.so")
 
-SOURCES = ["kernels.cu", "engine.cu", "schedule.cpp", "noalloc.cu", "cnn.cu", "cnn_tc.cu", "cnn_umma.cu"]
+SOURCES = ["kernels.cu", "engine.cu", "schedule.cpp", "noalloc.cu", "cnn.cu", "cnn_umma.cu"]
 HEADERS = ["reg_common.cuh", "schedule.h", "cnn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -11,12 +11,12 @@
 //
 // Layout: the FP32 path keeps activations NCHW in float, one buffer per layer,
 // on the CUDA cores.  The tensor-core path runs with BF16 operands and FP32
-// accumulation: the forward of all six layers and the stride-1 data gradients
-// on tcgen05 with TMEM accumulators, the 32 -> 32 weight gradients by
-// mma.sync; the outputs of layers 0..4 are then BF16 in a channel-group
-// planar layout [b][c / 8][y][x][c % 8], the operand layout of those kernels.
-// The remaining gradients (first and last layers' weights, the stride-2 and
-// last layers' data) run on the CUDA cores in FP32.
+// accumulation: the forward of all six layers and the data and weight
+// gradients of the four 32 -> 32 layers on tcgen05 with TMEM accumulators;
+// the outputs of layers 0..4 are then BF16 in a channel-group planar layout
+// [b][c / 8][y][x][c % 8], the operand layout of those kernels.  The remaining
+// gradients (the first and last layers' weights, whose few channels make them
+// bandwidth work, and the last layer's data) run on the CUDA cores in FP32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -742,7 +742,7 @@ reg_status reg_cnn_create(int32_t side, int32_t max_batch, void *cuda_stream, re
          alloc((void **)&h->wpack_last, sizeof(uint32_t) * cnn_last_umma_words()) &&
          cudaHostAlloc((void **)&h->uerr_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostGetDevicePointer((void **)&h->uerr, h->uerr_host, 0) == cudaSuccess &&
-         alloc((void **)&h->wpart, sizeof(float) * (size_t)(cnn_wgrad32_tc_blocks() + 1) * 32 * 288);
+         alloc((void **)&h->wpart, sizeof(float) * (size_t)std::max(cnn_wgrad32_umma_part_floats(), 2 * 1024 * 608));
     if (!ok) {
         reg_cnn_destroy(h);
         return cnn_fail(REG_ENOMEM, "device allocation failed");
@@ -834,7 +834,7 @@ static reg_status loss_grad(reg_cnn_t h, const float *x, const float *target, in
         if (tc && k >= 1 && k <= 4) {
             // the layer's input and the mask below: BF16 planar
             const uint16_t *inb = h->actb[k - 1];
-            rs = cnn_wgrad32_tc(inb, H, gz, B, LAYERS[k].S, gr, h->wpart, st);
+            rs = cnn_wgrad32_umma(inb, H, gz, B, LAYERS[k].S, gr, h->wpart, st, h->uerr);
             if (rs != REG_OK) return rs;
             const bool pack = h->packed_dgrad[k - 1] != h->version;
             uint32_t *wp = h->wpack_d + (k - 1) * cnn_conv32_umma_words();

@@ -18,12 +18,12 @@ int cnn_max_batch(const reg_cnn *h);
 // channels): "planar" below.
 //
 // Weight and bias gradient of a 32 -> 32 layer of stride S on the tensor cores
-// into grad (the layer's W then b): in the layer's input (planar, B x 32 x H
-// x H), gz the output gradient (FP32 NCHW); part: device scratch of
-// (cnn_wgrad32_tc_blocks() + 1) x 32 x 288 floats.
-reg_status cnn_wgrad32_tc(const uint16_t *in, int H, const float *gz, int B, int S, float *grad, float *part,
-                          cudaStream_t st);
-int cnn_wgrad32_tc_blocks();
+// (tcgen05) into grad (the layer's W then b): in the layer's input (planar, B
+// x 32 x H x H), gz the output gradient (FP32 NCHW); part: device scratch of
+// cnn_wgrad32_umma_part_floats() floats; err: the tcgen05 error word.
+reg_status cnn_wgrad32_umma(const uint16_t *in, int H, const float *gz, int B, int S, float *grad, float *part,
+                            cudaStream_t st, int *err);
+int cnn_wgrad32_umma_part_floats();
 // 32 -> 32 channel 3x3 convolution (zero padding 1, stride S = 1 or 2) with
 // bias and ReLU on the fifth-generation tensor cores (tcgen05.mma, accumulator
 // in TMEM, BF16 operands, FP32 accumulation): in (planar, B x 32 x H x H, read

@@ -2,9 +2,10 @@
 // tcgen05.mma with the accumulator in tensor memory (TMEM), BF16 operands,
 // FP32 accumulation.  All six layers of the tensor-core forward run here: the
 // four 32 -> 32 layers and the last layer (32 -> 2) from TMA-loaded tiles,
-// the first layer (2 -> 32) from tiles the CTA's threads stage; and the data
+// the first layer (2 -> 32) from tiles the CTA's threads stage; the data
 // gradients of the four 32 -> 32 layers (stride 1, and stride 2 as four
-// parity classes of stride-1 GEMMs).
+// parity classes of stride-1 GEMMs); and their weight gradients, GEMMs whose
+// reduction runs over the batch's pixels (k_wgrad32_umma).
 //
 // Implicit GEMM per output tile of 16 rows x 8 columns of one image:
 //   D[m][o] = sum_k A[m][k] W[o][k],   m = 8 (tile row) + (tile column),
@@ -793,6 +794,214 @@ __global__ void __launch_bounds__(128) k_conv_umma_staged(const float *__restric
     umma_teardown<COLS>(tmem);
 }
 
+// Weight gradient of a 32 -> 32 layer (stride S) on the tensor cores:
+//   gW[o][c][dy][dx] = sum_p gz[o][p] in_pad[c][S y + dy][S x + dx],
+// the sum over all output pixels p = (y, x) of the batch, as GEMMs with the
+// pixels as the reduction: for every output row y of a tile of WG_TH x WG_TW
+// pixels and every dy, one MMA with K = the row's 16 pixels,
+//   D_dy[o][(dx, c)] += A[o][k] B_dy[(dx, c)][k],   M = 128, N = 96,
+// A = the output gradient (BF16; rows 32..127 read padding, so lanes 32..127
+// of D are unused), B_dy = the input row S y + dy at the columns S x + dx - 1.
+// Both operands are K-major core matrices staged by the CTA's threads:
+//   A: [tile row][k half][8-channel group of o][8 o x 8 pixels], 1536 B of
+//      padding after it for the unused rows;
+//   B: [dx, 8-channel group of c][input row of the tile][k half][8 c x 8
+//      pixels], one copy per dx (so that every MMA reads 16-byte aligned core
+//      matrices), from the planar BF16 input.
+// The three accumulators D_0, D_1, D_2 take TMEM columns 0, 96 and 192, so
+// column 32 (3 dy + dx) + c holds tap (dy, dx) of channel c.  The CTA walks
+// its tiles (tile = block + k grid) with two staging buffers, so that the MMAs
+// of one tile run while the next is staged; the bias sums (of the unrounded
+// FP32 gradient) are formed from the staging registers.  Each CTA writes one
+// record in the parameter layout ((o 32 + c) 9 + tap, then the 32 biases);
+// k_wgrad_umma_reduce adds the records in block order.
+constexpr int WG_TH = 8, WG_TW = 16, WG_N = 96, WG_COLS = 512;
+constexpr int WG_REC = UC * UC * 9 + UC;
+
+template <int S>
+struct WgSmem {
+    static constexpr int ir = S * (WG_TH - 1) + 3;      // input rows of a tile
+    static constexpr int a_bytes = WG_TH * 1024 + 1536;  // 8 rows x 2 halves x 4 groups x 128 B + padding
+    static constexpr int b_bytes = 12 * ir * 256;        // 12 groups x rows x 2 halves x 128 B
+    static constexpr int a0 = 0, b0 = 2 * a_bytes;
+    static constexpr int bars = b0 + 2 * b_bytes;        // MMA done, per buffer
+    static constexpr int taddr = bars + 16;
+    static constexpr int red = taddr + 16;               // bias sums: [warp][8 o][4 groups]
+    static constexpr int bytes = red + 8 * 8 * 4 * 4;
+    static_assert(a_bytes % 128 == 0 && b_bytes % 128 == 0, "core matrices 16-byte aligned");
+};
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) k_wgrad32_umma(const uint4 *__restrict__ in, int H,
+                                                         const float *__restrict__ gz, int Ho, int tiles_x,
+                                                         int tiles_y, int n_tiles, float *__restrict__ part,
+                                                         int *__restrict__ err)
+{
+    using SM = WgSmem<S>;
+    constexpr int IR = SM::ir, NB = (96 * IR + 255) / 256;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t s_base = smem_u32(smem), bar_mma = s_base + SM::bars;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + SM::taddr),
+                     "r"(WG_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_mma + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + SM::taddr);
+    // A items: jp = pixel pair, r = o % 8 (consecutive lanes: conflict-free
+    // stores), then k half, tile row and group og = o / 8 (= slot k / 2)
+    const int a_jp = tid & 3, a_r = (tid >> 2) & 7;
+    float bsum[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0, it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        int b, ty, tx;
+        tile_coords(tile, tiles_x, tiles_y, b, ty, tx);
+        const int oy0 = ty * WG_TH, ox0 = tx * WG_TW;
+        // the gradient's and the input's values of this tile, loaded before
+        // the buffer is free
+        float2 av[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int item = tid + 256 * k, kap = (item >> 5) & 1, y = (item >> 6) & 7, o = 8 * (item >> 9) + a_r;
+            const int oy = oy0 + y, ox = ox0 + 8 * kap + 2 * a_jp;
+            float2 v = make_float2(0.f, 0.f);
+            if (oy < Ho) {
+                const float *row = gz + (((int64_t)b * UC + o) * Ho + oy) * Ho;
+                if (ox < Ho) v.x = row[ox];
+                if (ox + 1 < Ho) v.y = row[ox + 1];
+            }
+            av[k] = v;
+        }
+        uint4 q0[NB], q1[NB];
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            const int item = tid + 256 * k, jp = item & 3, kap = (item >> 2) & 1, r2 = item >> 3;
+            const int ir = r2 % IR, g = r2 / IR, dx = g >> 2, cg = g & 3;
+            const int iy = S * oy0 - 1 + ir, x = ox0 + 8 * kap + 2 * jp;
+            const int ix0 = S * x + dx - 1, ix1 = S * (x + 1) + dx - 1;
+            q0[k] = q1[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (item < 96 * IR && iy >= 0 && iy < H) {
+                const uint4 *row = in + ((int64_t)(4 * b + cg) * H + iy) * H;
+                if (ix0 >= 0 && ix0 < H) q0[k] = row[ix0];
+                if (ix1 >= 0 && ix1 < H) q1[k] = row[ix1];
+            }
+        }
+        if (it >= 2) {
+            // the MMAs of tile it - 2 have read this buffer
+            const bool ok = bad ? true : mbar_wait(bar_mma + 8 * buf, ((it - 2) >> 1) & 1);
+            if (!ok) *reinterpret_cast<volatile int *>(err) = 3;
+            bad = __syncthreads_or(!ok || bad);
+            if (bad) break;
+        }
+        uint8_t *abuf = smem + SM::a0 + buf * SM::a_bytes;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int item = tid + 256 * k, kap = (item >> 5) & 1, y = (item >> 6) & 7, og = item >> 9;
+            bsum[k >> 1] += av[k].x + av[k].y;
+            *reinterpret_cast<uint32_t *>(abuf + ((y * 2 + kap) * 4 + og) * 128 + a_r * 16 + a_jp * 4) =
+                pack2(av[k].x, av[k].y);
+        }
+        uint8_t *bbuf = smem + SM::b0 + buf * SM::b_bytes;
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            const int item = tid + 256 * k, jp = item & 3, kap = (item >> 2) & 1, r2 = item >> 3;
+            if (item >= 96 * IR) continue;
+            const int ir = r2 % IR, g = r2 / IR;
+            uint8_t *cm = bbuf + ((g * IR + ir) * 2 + kap) * 128 + jp * 4;
+            const uint32_t w0[4] = {q0[k].x, q0[k].y, q0[k].z, q0[k].w}, w1[4] = {q1[k].x, q1[k].y, q1[k].z, q1[k].w};
+            // wd[c]: channel c of the two pixels (row c of the core matrix)
+            uint32_t wd[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) wd[c] = __byte_perm(w0[c >> 1], w1[c >> 1], (c & 1) ? 0x7632 : 0x5410);
+            // rotated by the lane group (rot = lane / 4), so that the 8 lane
+            // groups of a store instruction write 8 different rows: 32 banks
+            const int rot = lane >> 2;
+#pragma unroll
+            for (int sh = 1; sh < 8; sh <<= 1) {
+                uint32_t t[8];
+#pragma unroll
+                for (int i = 0; i < 8; i++) t[i] = (rot & sh) ? wd[(i + sh) & 7] : wd[i];
+#pragma unroll
+                for (int i = 0; i < 8; i++) wd[i] = t[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) *reinterpret_cast<uint32_t *>(cm + ((i + rot) & 7) * 16) = wd[i];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t abase = s_base + SM::a0 + buf * SM::a_bytes, bbase = s_base + SM::b0 + buf * SM::b_bytes;
+#pragma unroll 1
+            for (int y = 0; y < WG_TH; y++)
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++)
+                    umma_bf16<WG_N>(tmem + WG_N * dy, sdesc(abase + y * 1024, 512, 128),
+                                    sdesc(bbase + (S * y + dy) * 256, 128, IR * 256), (it > 0 || y > 0) ? 1u : 0u);
+            umma_commit(bar_mma + 8 * buf);
+        }
+    }
+    // the last tile's MMAs (and so all of them) are done
+    if (!bad && it > 0) {
+        const int last = it - 1;
+        const bool ok = mbar_wait(bar_mma + 8 * (last & 1), (last >> 1) & 1);
+        if (!ok) *reinterpret_cast<volatile int *>(err) = 3;
+        bad = __syncthreads_or(!ok);
+    }
+    float *rec = part + (int64_t)blockIdx.x * WG_REC;
+    if (warp == 0) {
+        // lane o of the accumulators: column 32 (3 dy + dx) + c = tap (dy, dx), channel c
+        tc_fence_after();
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            float v[UC];
+            if (!bad && it > 0) tmem_ld<UC>(tmem + 32 * tap, v);
+            else
+#pragma unroll
+                for (int c = 0; c < UC; c++) v[c] = 0.f;
+#pragma unroll
+            for (int c = 0; c < UC; c++) rec[(lane * UC + c) * 9 + tap] = v[c];
+        }
+    }
+    // bias: the four lanes of a pixel-pair group, then the eight warps
+    float *red = reinterpret_cast<float *>(smem + SM::red);
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+        float v = bsum[g];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (a_jp == 0) red[(warp * 8 + a_r) * 4 + g] = v;
+    }
+    __syncthreads();
+    if (tid < UC) {
+        float sum = 0.f;
+        for (int w = 0; w < 8; w++) sum += red[(w * 8 + (tid & 7)) * 4 + (tid >> 3)];
+        rec[UC * UC * 9 + tid] = sum;
+    }
+    umma_teardown<WG_COLS>(tmem);
+}
+
+// grad[e] = the records' sum in block order, one thread per entry.
+__global__ void k_wgrad_umma_reduce(const float *__restrict__ part, int nblk, float *__restrict__ grad)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= WG_REC) return;
+    float s = 0.f;
+    for (int k = 0; k < nblk; k++) s += part[(int64_t)k * WG_REC + e];
+    grad[e] = s;
+}
+
 // cuTensorMapEncodeTiled from the driver, found once.
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 {
@@ -945,6 +1154,42 @@ reg_status cnn_dgrad32s2_umma(const float *gz, int Hg, const float *theta, const
                                                                      2 * Hg, tx, ty, nt, err);
     if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 stride-2 data gradient launch");
     return REG_OK;
+}
+
+namespace {
+
+template <int S>
+reg_status launch_wgrad_umma(const uint16_t *in, int H, const float *gz, int B, float *grad, float *part,
+                             cudaStream_t st, int *err)
+{
+    const int Ho = (H + 2 - 3) / S + 1;
+    const int tx = (Ho + WG_TW - 1) / WG_TW, ty = (Ho + WG_TH - 1) / WG_TH, nt = B * tx * ty;
+    int grid = 0;
+    if (!grid_for(k_wgrad32_umma<S>, WgSmem<S>::bytes, WG_COLS, nt, grid))
+        return reg_internal_fail(REG_ECUDA, "tcgen05 weight gradient: launch attributes");
+    k_wgrad32_umma<S><<<grid, 256, WgSmem<S>::bytes, st>>>(reinterpret_cast<const uint4 *>(in), H, gz, Ho, tx, ty, nt,
+                                                          part, err);
+    k_wgrad_umma_reduce<<<(WG_REC + 255) / 256, 256, 0, st>>>(part, grid, grad);
+    if (cudaGetLastError() != cudaSuccess) return reg_internal_fail(REG_ECUDA, "tcgen05 weight gradient launch");
+    return REG_OK;
+}
+
+}  // namespace
+
+reg_status cnn_wgrad32_umma(const uint16_t *in, int H, const float *gz, int B, int S, float *grad, float *part,
+                            cudaStream_t st, int *err)
+{
+    if (S == 1) return launch_wgrad_umma<1>(in, H, gz, B, grad, part, st, err);
+    if (S == 2) return launch_wgrad_umma<2>(in, H, gz, B, grad, part, st, err);
+    return reg_internal_fail(REG_EINVAL, "tcgen05 weight gradient: stride must be 1 or 2");
+}
+
+int cnn_wgrad32_umma_part_floats()
+{
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 152;
+    return nsm * WG_REC;
 }
 
 int cnn_last_umma_words() { return Wts<16>::bytes / 4; }
