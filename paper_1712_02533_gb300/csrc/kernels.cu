@@ -1443,6 +1443,37 @@ __device__ __forceinline__ void steps_tile(const OpState &s, const LevelDesc &Lv
 template <int JM>
 __device__ __forceinline__ void write_partials(const BatchDev &b, int item, const float *v, int nused, int lane)
 {
+    const unsigned FULL = 0xffffffffu;
+    if constexpr (JM <= 4) {
+        // The (at most) 15 sums by one transpose-reduction: at each butterfly
+        // step (lane offsets 16, 8, 4, 2) a lane keeps half of its values and
+        // adds the partner's copy of them, so that after the last step (offset
+        // 1) lanes 2 k and 2 k + 1 hold sum k.  Every sum pairs the same lanes
+        // in the same order as warp_sum, so the totals are the same floats.
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 12; k++) x[k] = (k < 3 * JM && k < nused) ? v[k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) x[12 + k] = v[3 * REG_MAX_TRIALS + k];
+        x[15] = 0.f;
+#pragma unroll
+        for (int o = 16, h = 8; h >= 1; o >>= 1, h >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < h; i++) {
+                const float send = up ? x[i] : x[h + i], keep = up ? x[h + i] : x[i];
+                x[i] = keep + __shfl_xor_sync(FULL, send, o);
+            }
+        }
+        x[0] += __shfl_xor_sync(FULL, x[0], 1);
+        // entry e of the record: sums 0..11 from lanes 0, 2, .., 22; entries
+        // 3 MAXT .. 3 MAXT + 2 from lanes 24, 26, 28; the rest zero
+        const int src = lane < 12 ? 2 * lane : (lane >= 3 * REG_MAX_TRIALS ? 2 * (12 + lane - 3 * REG_MAX_TRIALS) : 0);
+        const float tot = __shfl_sync(FULL, x[0], src & 31);
+        const bool has = lane < 12 || (lane >= 3 * REG_MAX_TRIALS && lane < PT_STRIDE);
+        if (lane < PT_STRIDE) b.partT[(int64_t)item * PT_STRIDE + lane] = has ? (double)tot : 0.0;
+        return;
+    }
     double mine = 0.0;
 #pragma unroll
     for (int k = 0; k < PT_STRIDE; k++) {
