@@ -46,20 +46,13 @@ int64_t param_offset(int k)
 }
 int64_t total_params() { return param_offset(NL); }
 
-__device__ __forceinline__ uint32_t bf16x2(float lo, float hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
-}
 
 // ---------------------------------------------------------------------------
 // Forward: one thread per output pixel (b, y, x) computes all O channels.
 // ---------------------------------------------------------------------------
-// OUT_PLANAR: out is BF16 in the planar layout of the tensor-core layers,
-// [b][o / 8][y][x][o % 8] (O = 32), instead of FP32 NCHW.
-template <int C, int O, int S, bool RELU, bool OUT_PLANAR = false>
+template <int C, int O, int S, bool RELU>
 __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, int H, const float *__restrict__ theta,
-                                                  void *__restrict__ out, int Ho, int total)
+                                                  float *__restrict__ out, int Ho, int total)
 {
     // weights as [c][tap][o], so that one vector load brings the weights of
     // several output channels for an input value
@@ -113,20 +106,8 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const float *__restrict__ in, 
 #pragma unroll
     for (int o = 0; o < O; o++)
         if (RELU) acc[o] = fmaxf(acc[o], 0.f);
-    if (OUT_PLANAR) {
-        static_assert(!OUT_PLANAR || O == 32, "planar output has 32 channels");
-        uint4 *o16 = reinterpret_cast<uint4 *>(out);
 #pragma unroll
-        for (int g = 0; g < O / 8; g++) {
-            const float *q = acc + 8 * g;
-            o16[((int64_t)(4 * b + g) * Ho + y) * Ho + x] =
-                make_uint4(bf16x2(q[0], q[1]), bf16x2(q[2], q[3]), bf16x2(q[4], q[5]), bf16x2(q[6], q[7]));
-        }
-    } else {
-        float *o32 = reinterpret_cast<float *>(out);
-#pragma unroll
-        for (int o = 0; o < O; o++) o32[(((int64_t)b * O + o) * Ho + y) * Ho + x] = acc[o];
-    }
+    for (int o = 0; o < O; o++) out[(((int64_t)b * O + o) * Ho + y) * Ho + x] = acc[o];
 }
 
 // ---------------------------------------------------------------------------
@@ -210,9 +191,8 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float *__restrict__
 // each (grid O C split), and each block writes its 10 sums to part; the
 // layers with few (o, c) pairs (2 -> 32, 32 -> 2) keep the GPU busy that way,
 // and k_bwd_weight_sum adds the parts in order.
-// IN_PLANAR: in is BF16 in the planar layout of the tensor-core layers (C = 32).
-template <int C, int O, int S, bool IN_PLANAR = false>
-__global__ void __launch_bounds__(256) k_conv_bwd_weight(const void *__restrict__ in_, int H,
+template <int C, int O, int S>
+__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict__ in, int H,
                                                          const float *__restrict__ gz, int Ho, int B,
                                                          float *__restrict__ grad, int split,
                                                          float *__restrict__ part)
@@ -227,17 +207,14 @@ __global__ void __launch_bounds__(256) k_conv_bwd_weight(const void *__restrict_
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const int b = p / per, q = p % per, y = q / Ho, x = q % Ho;
         const float g = gz[((int64_t)b * O + o) * per + q];
-        const float *src = reinterpret_cast<const float *>(in_) + ((int64_t)b * C + c) * H * H;
-        const __nv_bfloat16 *srcb =
-            reinterpret_cast<const __nv_bfloat16 *>(in_) + ((int64_t)(4 * b + c / 8) * H * H) * 8 + (c & 7);
+        const float *src = in + ((int64_t)b * C + c) * H * H;
 #pragma unroll
         for (int dy = 0; dy < 3; dy++)
 #pragma unroll
             for (int dx = 0; dx < 3; dx++) {
                 const int iy = S * y + dy - 1, ix = S * x + dx - 1;
                 float v = 0.f;
-                if (iy >= 0 && iy < H && ix >= 0 && ix < H)
-                    v = IN_PLANAR ? __bfloat162float(srcb[(int64_t)(iy * H + ix) * 8]) : src[iy * H + ix];
+                if (iy >= 0 && iy < H && ix >= 0 && ix < H) v = src[iy * H + ix];
                 acc[dy * 3 + dx] = fmaf(g, v, acc[dy * 3 + dx]);
             }
         acc[9] += g;
@@ -579,26 +556,25 @@ __global__ void k_adam(float *__restrict__ theta, const float *__restrict__ g, f
     }
 }
 
-template <int C, int O, int S, bool RELU, bool OUT_PLANAR = false>
-void fwd(const float *in, int H, const float *theta, void *out, int B, cudaStream_t st)
+template <int C, int O, int S, bool RELU>
+void fwd(const float *in, int H, const float *theta, float *out, int B, cudaStream_t st)
 {
     const int Ho = (H + 2 - 3) / S + 1, total = B * Ho * Ho;
-    k_conv_fwd<C, O, S, RELU, OUT_PLANAR><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
+    k_conv_fwd<C, O, S, RELU><<<(total + 127) / 128, 128, 0, st>>>(in, H, theta, out, Ho, total);
 }
 
-// PLANAR: the layer's input and the activation below are BF16 planar.
-template <int C, int O, int S, bool PLANAR = false>
-void bwd(const void *in, int H, const float *gz, const float *theta, const void *a_below, float *gx, float *grad,
+template <int C, int O, int S>
+void bwd(const float *in, int H, const float *gz, const float *theta, const float *a_below, float *gx, float *grad,
          int B, cudaStream_t st, float *part)
 {
     const int Ho = (H + 2 - 3) / S + 1;
     // (o, c) pairs times parts of the pixel range: about a thousand blocks
     const int split = (O * C >= 512) ? 1 : std::min(64, 1024 / (O * C));
-    k_conv_bwd_weight<C, O, S, PLANAR><<<O * C * split, 256, 0, st>>>(in, H, gz, Ho, B, grad, split, part);
+    k_conv_bwd_weight<C, O, S><<<O * C * split, 256, 0, st>>>(in, H, gz, Ho, B, grad, split, part);
     if (split > 1) k_bwd_weight_sum<C, O><<<(O * C * 10 + 255) / 256, 256, 0, st>>>(part, split, grad);
     if (gx) {
         const int total = B * H * H;
-        k_conv_bwd_data<C, O, S, PLANAR><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
+        k_conv_bwd_data<C, O, S><<<(total + 127) / 128, 128, 0, st>>>(gz, Ho, theta, a_below, gx, H, total);
     }
 }
 
